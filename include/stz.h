@@ -1,0 +1,144 @@
+/*
+ * stz.h -- C ABI of the GB300 (sm_103a) implementation of the STZ streaming
+ * lossy compressor's hot path ("STZ: A High Quality and High Speed Streaming
+ * Lossy Compression Framework for Scientific Data", SC'25).
+ *
+ * Every step of compression and decompression runs in hand-written CUDA
+ * kernels on the device; the host only validates arguments, sizes launches
+ * and reads back a few bytes.  The library allocates no device memory:
+ * callers pass device buffers (typically from PyTorch) for the field, the
+ * output and a workspace, and a CUDA stream (cast to void*; NULL = legacy
+ * default stream).  All pointers named *_dev are device pointers.
+ *
+ * Layout conventions
+ *   - A field is a C-order array of float (STZ_F32) or double (STZ_F64).
+ *   - dims[] lists the extents slowest first: {nz, ny, nx} for ndim = 3,
+ *     {ny, nx} for ndim = 2 (dims[2] ignored).
+ *   - Boxes are half-open [lo, hi) in field coordinates, slowest first, in the
+ *     same order as dims (2D: only lo[0..1], hi[0..1] are read).
+ *   - Level l of L has stride s_l = 2^(L-l): level 1 is the coarsest grid,
+ *     level L the full field (Sec. 3.2, three-level partition; L = 3).
+ *
+ * Errors: every call returns STZ_OK (0) or a negative code; stz_strerror()
+ * names it.  Device-side checks (corrupt containers) are read back before a
+ * decompression call returns, so no call leaves a fault behind.
+ *
+ * Threading: calls on different workspaces may run concurrently on different
+ * streams.  A workspace must not be shared by two calls in flight.
+ */
+#ifndef STZ_H
+#define STZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { STZ_F32 = 0, STZ_F64 = 1 } stz_dtype;
+
+/* STZ_EB_ABS: |x - x'| <= eb.  STZ_EB_REL: |x - x'| <= eb * (max - min) over
+ * the finite values (a zero range falls back to eb as an absolute bound). */
+typedef enum { STZ_EB_ABS = 0, STZ_EB_REL = 1 } stz_eb_mode;
+
+enum {
+  STZ_OK = 0,
+  STZ_ERR_ARG = -1,       /* invalid argument or unsupported container option */
+  STZ_ERR_CAPACITY = -2,  /* output or workspace too small; needed size returned */
+  STZ_ERR_CORRUPT = -3,   /* container fails validation */
+  STZ_ERR_CUDA = -4,      /* a CUDA runtime call failed */
+  STZ_ERR_TIMEOUT = -5,   /* a bounded device wait ran out */
+  STZ_ERR_NOMEM = -6      /* host allocation failed */
+};
+
+/* Name of an error code (static string). */
+const char* stz_strerror(int code);
+
+/* Library version string, e.g. "stz-gb300 1.0 (sm_103a)". */
+const char* stz_version(void);
+
+/*
+ * Worst-case container size for a field of these dims and dtype (all points
+ * outliers, longest codes).  0 on invalid arguments.
+ */
+size_t stz_compress_bound(const int64_t* dims, int ndim, stz_dtype dtype);
+
+/*
+ * Workspace bytes that suffice for stz_compress and for every decompression
+ * call on a container of a field with these dims and dtype.
+ */
+size_t stz_workspace_size(const int64_t* dims, int ndim, stz_dtype dtype);
+
+/*
+ * Compress (Sec. 3.1-3.2: hierarchical partition into L = 3 levels, SZ3-style
+ * interpolation of level 1, multi-dimensional cubic prediction of levels 2
+ * and 3 (Eqs. 6-8) with the adaptive bound eb_l = eb_{l+1} / 2.5
+ * (Sec. 3.1 opt. 5), linear-scale quantization with outliers, and Huffman
+ * coding of each sub-block's codes in independently decodable chunks).
+ *
+ *   field_dev     input field (device), ndim/dims/dtype as above
+ *   eb_mode, eb   error bound (eb > 0, finite)
+ *   out_dev       output container (device), capacity out_cap bytes;
+ *                 stz_compress_bound() always suffices
+ *   out_bytes     receives the container size (also on STZ_ERR_CAPACITY:
+ *                 the size that would have been needed)
+ *   ws_dev        workspace (device), ws_bytes >= stz_workspace_size()
+ *   stream        cudaStream_t
+ *
+ * Blocks the calling thread once, at the end, to read the size back.
+ * The container is bit-identical to the CPU oracle's for the same input.
+ */
+int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype dtype,
+                 stz_eb_mode eb_mode, double eb, void* out_dev, size_t out_cap,
+                 size_t* out_bytes, void* ws_dev, size_t ws_bytes, void* stream);
+
+/* Header of a container (host or device memory; comp_on_device selects). */
+typedef struct {
+  stz_dtype dtype;
+  int ndim;
+  int64_t dims[3];   /* slowest first; 2D: {ny, nx, 1} */
+  int levels;        /* L */
+  double eb;         /* bound given to stz_compress */
+  stz_eb_mode eb_mode;
+  double eb_abs;     /* absolute bound of the finest level */
+  uint64_t total_bytes;
+} stz_info_t;
+
+int stz_info(const void* comp, size_t comp_bytes, int comp_on_device, stz_info_t* info);
+
+/*
+ * Full decompression: the whole field at full resolution, out_cap >= number
+ * of points times the element size.  Each level is reconstructed from the
+ * coarser one (Sec. 3.3; "L2 pre./rec." of Table 5 fused into one pass).
+ */
+int stz_decompress_full(const void* comp_dev, size_t comp_bytes, void* out_dev, size_t out_cap,
+                        void* ws_dev, size_t ws_bytes, void* stream);
+
+/*
+ * Progressive decompression to level `level` (1..L; Sec. 3.3): only levels
+ * 1..level are decoded; the output is the stride-2^(L-level) grid, out_dims
+ * = ceil(dims / 2^(L-level)) (slowest first; 2D: out_dims[2] = 1).
+ */
+int stz_decompress_progressive(const void* comp_dev, size_t comp_bytes, int level,
+                               void* out_dev, size_t out_cap, int64_t* out_dims, void* ws_dev,
+                               size_t ws_bytes, void* stream);
+
+/*
+ * Random-access decompression of the box [lo, hi) at level `level`
+ * (Sec. 3.3, Fig. 5): level 1 is decoded whole; at each finer level only the
+ * chunks and predictions the box needs (its points plus the interpolation
+ * support) are decoded.  The output is the box's points whose coordinates are
+ * multiples of 2^(L-level), C order; out_dims receives its shape.  The values
+ * are bitwise those of the full decode.  The box must be non-empty and inside
+ * the field (STZ_ERR_ARG otherwise); it may contain no lattice point, then
+ * out_dims has a zero.
+ */
+int stz_decompress_region(const void* comp_dev, size_t comp_bytes, const int64_t* lo,
+                          const int64_t* hi, int level, void* out_dev, size_t out_cap,
+                          int64_t* out_dims, void* ws_dev, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,707 @@
+// stz_api.cu -- the C ABI (include/stz.h): argument checks, workspace
+// planning, container header parsing and launch sequencing.  Every step of
+// the method runs in the kernels of the other translation units.
+#include <stdio.h>
+#include <string.h>
+
+#include "stz_kernels.cuh"
+
+namespace stz {
+
+void make_geo(const int64_t n[3], int ndim, int dtype, int L, const int b[3], Geo* g) {
+  memset(g, 0, sizeof(*g));
+  for (int a = 0; a < 3; a++) {
+    g->n[a] = n[a];
+    g->b[a] = b[a];
+  }
+  g->L = L;
+  g->ndim = ndim;
+  g->dtype = dtype;
+  g->nstreams = 1 + 7 * (L - 1);
+  g->bvol = (int64_t)b[0] * b[1] * b[2];
+  int64_t chunk0 = 0;
+  for (int s = 0; s < g->nstreams; s++) {
+    StreamGeo& sg = g->s[s];
+    if (s == 0) {
+      sg.level = 1;
+      grid_extent(n, L, 1, sg.e);
+      sg.o[0] = sg.o[1] = sg.o[2] = 0;
+    } else {
+      const int l = 2 + (s - 1) / 7, k = 1 + (s - 1) % 7;
+      sg.level = l;
+      sg.o[0] = (k >> 2) & 1;
+      sg.o[1] = (k >> 1) & 1;
+      sg.o[2] = k & 1;
+      int64_t m[3];
+      grid_extent(n, L, l, m);
+      for (int a = 0; a < 3; a++) sg.e[a] = m[a] >= sg.o[a] ? (m[a] - sg.o[a] + 1) / 2 : 0;
+    }
+    sg.nsym = sg.e[0] * sg.e[1] * sg.e[2];
+    for (int a = 0; a < 3; a++) sg.nb[a] = sg.e[a] > 0 ? cdiv(sg.e[a], b[a]) : 0;
+    sg.nchunks = sg.nb[0] * sg.nb[1] * sg.nb[2];
+    sg.chunk0 = chunk0;
+    chunk0 += sg.nchunks;
+  }
+  g->total_chunks = chunk0;
+}
+
+static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+static int64_t vol(const int64_t e[3]) { return e[0] * e[1] * e[2]; }
+
+// Workspace plan; offsets in bytes from the workspace base.
+struct WsPlan {
+  size_t dp, grid[kMaxLevels + 1], codes, hist, chunk_out, chunk_words, word_off, out_off, enc,
+      books, lay, lut, total;
+};
+
+static WsPlan plan_compress(const Geo& g) {
+  WsPlan w;
+  memset(&w, 0, sizeof(w));
+  const size_t ps = g.dtype == STZ_F32 ? 4 : 8;
+  size_t o = 0;
+  w.dp = o;
+  o += al256(sizeof(DevParams));
+  for (int l = 1; l < g.L; l++) {
+    int64_t m[3];
+    grid_extent(g.n, g.L, l, m);
+    w.grid[l] = o;
+    o += al256(ps * (size_t)vol(m));
+  }
+  w.codes = o;
+  o += al256(2 * (size_t)(g.total_chunks * g.bvol));
+  w.hist = o;
+  o += al256(4 * (size_t)g.nstreams * kAlphabet);
+  w.chunk_out = o;
+  o += al256(4 * (size_t)g.total_chunks);
+  w.chunk_words = o;
+  o += al256(4 * (size_t)g.total_chunks);
+  w.word_off = o;
+  o += al256(8 * (size_t)(g.total_chunks + 1));
+  w.out_off = o;
+  o += al256(8 * (size_t)(g.total_chunks + 1));
+  w.enc = o;
+  o += al256(2 * (size_t)g.nstreams * kAlphabet);
+  w.books = o;
+  o += al256(sizeof(BookDev) * (size_t)g.nstreams);
+  w.lay = o;
+  o += al256(sizeof(LayoutDev));
+  w.lut = o;
+  o += al256(4 * (size_t)g.nstreams * kLutSize);
+  w.total = o;
+  return w;
+}
+
+static int dims3(const int64_t* dims, int ndim, int64_t n[3]) {
+  if (!dims || (ndim != 2 && ndim != 3)) return STZ_ERR_ARG;
+  if (ndim == 3) {
+    n[0] = dims[0];
+    n[1] = dims[1];
+    n[2] = dims[2];
+  } else {
+    n[0] = 1;
+    n[1] = dims[0];
+    n[2] = dims[1];
+  }
+  for (int a = 0; a < 3; a++)
+    if (n[a] < 1 || n[a] > ((int64_t)1 << 31)) return STZ_ERR_ARG;
+  if (n[0] * n[1] > ((int64_t)1 << 40) / n[2]) return STZ_ERR_ARG;
+  return STZ_OK;
+}
+
+static const int* default_brick(int ndim) { return ndim == 3 ? kBrick3D : kBrick2D; }
+
+static size_t bound_of(const Geo& g) {
+  const size_t ps = g.dtype == STZ_F32 ? 4 : 8;
+  size_t total = kHeaderBytes + (size_t)g.nstreams * kDirEntryBytes;
+  for (int s = 0; s < g.nstreams; s++) {
+    const StreamGeo& sg = g.s[s];
+    size_t nsym = (size_t)sg.nsym, nch = (size_t)sg.nchunks;
+    size_t nlive = nsym < (size_t)kAlphabet ? nsym : (size_t)kAlphabet;
+    size_t pw = (nsym * kMaxCodeLen + 31) / 32 + nch;
+    size_t sect = ((3 * nlive + 3) & ~(size_t)3) + 4 * nch + 4 * pw + 4 * nsym;
+    sect = ((sect + 7) & ~(size_t)7) + ps * nsym;
+    total += (sect + 7) & ~(size_t)7;
+  }
+  return total;
+}
+
+// ------------------------------------------------------------ header parsing
+struct Hdr {
+  int dtype, ndim, L, eb_mode, maxlen, R, ns;
+  int b[3];
+  int64_t n[3];
+  double eb, eb_abs, two_eb[kMaxLevels + 1];
+  uint64_t total;
+  struct {
+    uint64_t sect_off, nsym, pw, nout;
+    uint32_t nch, nlive;
+  } d[kMaxStreams];
+};
+
+static uint32_t rd32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+static uint64_t rd64(const uint8_t* p) { return (uint64_t)rd32(p) | ((uint64_t)rd32(p + 4) << 32); }
+static double rdf64(const uint8_t* p) {
+  uint64_t u = rd64(p);
+  double v;
+  memcpy(&v, &u, 8);
+  return v;
+}
+
+struct SectHost {
+  uint64_t off_syms, off_lens, off_chunks, off_payload, off_opos, off_oval, size;
+};
+static SectHost sect_host(uint64_t nlive, uint64_t nch, uint64_t pw, uint64_t nout, uint64_t ps) {
+  SectHost s;
+  s.off_syms = 0;
+  s.off_lens = 2 * nlive;
+  s.off_chunks = (3 * nlive + 3) & ~3ull;
+  s.off_payload = s.off_chunks + 4 * nch;
+  s.off_opos = s.off_payload + 4 * pw;
+  s.off_oval = (s.off_opos + 4 * nout + 7) & ~7ull;
+  s.size = (s.off_oval + ps * nout + 7) & ~7ull;
+  return s;
+}
+
+// Parse and check the header and directory (h holds `avail` bytes).
+// Returns STZ_OK, STZ_ERR_CORRUPT, or STZ_ERR_ARG for valid containers with
+// options this library does not decode (radius other than 1024, codes longer
+// than 12 bits, bricks whose tiles exceed shared memory).
+static int parse_hdr(const uint8_t* h, size_t avail, size_t comp_bytes, Hdr* H) {
+  memset(H, 0, sizeof(*H));
+  if (avail < (size_t)kHeaderBytes || memcmp(h, "STZ1", 4) != 0) return STZ_ERR_CORRUPT;
+  if ((h[4] | (h[5] << 8)) != 1) return STZ_ERR_CORRUPT;
+  H->dtype = h[6];
+  H->ndim = h[7];
+  H->L = h[8];
+  H->eb_mode = h[9];
+  H->maxlen = h[10];
+  H->R = (int)rd32(h + 12);
+  for (int a = 0; a < 3; a++) H->b[a] = (int)rd32(h + 16 + 4 * a);
+  H->ns = (int)rd32(h + 28);
+  for (int a = 0; a < 3; a++) H->n[a] = (int64_t)rd64(h + 32 + 8 * a);
+  H->eb = rdf64(h + 56);
+  H->eb_abs = rdf64(h + 64);
+  H->total = rd64(h + 88);
+  if (H->dtype != STZ_F32 && H->dtype != STZ_F64) return STZ_ERR_CORRUPT;
+  if (H->ndim != 2 && H->ndim != 3) return STZ_ERR_CORRUPT;
+  if (H->L < 1 || H->L > kMaxLevels) return STZ_ERR_CORRUPT;
+  if (H->eb_mode != STZ_EB_ABS && H->eb_mode != STZ_EB_REL) return STZ_ERR_CORRUPT;
+  if (H->maxlen < 1 || H->maxlen > 24) return STZ_ERR_CORRUPT;
+  if (H->R < 2 || H->R > 32768 || 2 * (int64_t)H->R > ((int64_t)1 << H->maxlen))
+    return STZ_ERR_CORRUPT;
+  for (int a = 0; a < 3; a++) {
+    if (H->b[a] < 1 || H->b[a] > 4096) return STZ_ERR_CORRUPT;
+    if (H->n[a] < 1 || H->n[a] > ((int64_t)1 << 31)) return STZ_ERR_CORRUPT;
+  }
+  if ((int64_t)H->b[0] * H->b[1] * H->b[2] > 65536) return STZ_ERR_CORRUPT;
+  if (H->n[0] * H->n[1] > ((int64_t)1 << 40) / H->n[2]) return STZ_ERR_CORRUPT;
+  if (H->ndim == 2 && H->n[0] != 1) return STZ_ERR_CORRUPT;
+  if (H->ns != 1 + 7 * (H->L - 1)) return STZ_ERR_CORRUPT;
+  if (H->total > comp_bytes) return STZ_ERR_CORRUPT;
+  const uint64_t dir_end = kHeaderBytes + (uint64_t)H->ns * kDirEntryBytes;
+  if (dir_end > H->total || avail < dir_end) return STZ_ERR_CORRUPT;
+  for (int l = 1; l <= H->L; l++) H->two_eb[l] = rdf64(h + 144 + 8 * (l - 1));
+  Geo g;
+  make_geo(H->n, H->ndim, H->dtype, H->L, H->b, &g);
+  const uint64_t ps = H->dtype == STZ_F32 ? 4 : 8;
+  for (int s = 0; s < H->ns; s++) {
+    const uint8_t* d = h + kHeaderBytes + (size_t)s * kDirEntryBytes;
+    H->d[s].sect_off = rd64(d);
+    H->d[s].nsym = rd64(d + 8);
+    H->d[s].nch = rd32(d + 16);
+    H->d[s].nlive = rd32(d + 20);
+    H->d[s].pw = rd64(d + 24);
+    H->d[s].nout = rd64(d + 32);
+    const auto& e = H->d[s];
+    if (e.nsym != (uint64_t)g.s[s].nsym || e.nch != (uint64_t)g.s[s].nchunks) return STZ_ERR_CORRUPT;
+    if (e.nlive > (uint64_t)2 * H->R || (e.nsym > 0 && e.nlive == 0)) return STZ_ERR_CORRUPT;
+    if (e.nout > e.nsym || e.pw > e.nsym * 24 + e.nch) return STZ_ERR_CORRUPT;
+    if (e.sect_off % 8 || e.sect_off < dir_end || e.sect_off > H->total) return STZ_ERR_CORRUPT;
+    SectHost sh = sect_host(e.nlive, e.nch, e.pw, e.nout, ps);
+    if (sh.size > H->total - e.sect_off) return STZ_ERR_CORRUPT;
+  }
+  if (H->R != kRadius || H->maxlen > kMaxCodeLen) return STZ_ERR_ARG;
+  {
+    int64_t tv = 1;
+    for (int a = 0; a < 3; a++) tv *= H->b[a] + 3;
+    if (tv * (int64_t)ps > 160 * 1024 || (int64_t)H->b[0] * H->b[1] * H->b[2] > 4096)
+      return STZ_ERR_ARG;
+  }
+  return STZ_OK;
+}
+
+static int read_hdr(const void* comp, size_t comp_bytes, int on_device, cudaStream_t st, Hdr* H) {
+  if (!comp || comp_bytes < (size_t)kHeaderBytes) return STZ_ERR_CORRUPT;
+  const size_t want = kHeaderBytes + (size_t)kMaxStreams * kDirEntryBytes;
+  const size_t n = comp_bytes < want ? comp_bytes : want;
+  uint8_t buf[kHeaderBytes + kMaxStreams * kDirEntryBytes];
+  if (on_device) {
+    if (cudaMemcpyAsync(buf, comp, n, cudaMemcpyDeviceToHost, st) != cudaSuccess) return STZ_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return STZ_ERR_CUDA;
+  } else {
+    memcpy(buf, comp, n);
+  }
+  return parse_hdr(buf, n, comp_bytes, H);
+}
+
+// Decode workspace plan for a region: level-1 grid, box grids of levels
+// 2..k-1, code slots of the needed chunks, decode tables.
+struct DecPlan {
+  int k;
+  int64_t OA[3], OB[3];                                // output box on G_k
+  int64_t A[kMaxLevels + 1][3], B[kMaxLevels + 1][3];  // boxes on G_j (G_1 whole)
+  int64_t tlo[kMaxLevels + 1][3], tcnt[kMaxLevels + 1][3];
+  SlotMap sm[kMaxStreams];
+  int64_t nslots;
+  size_t dp, grid[kMaxLevels + 1], codes, lut, total;
+};
+
+static void plan_decode(const Geo& g, int k, const int64_t lo[3], const int64_t hi[3], DecPlan* P) {
+  memset(P, 0, sizeof(*P));
+  P->k = k;
+  const int64_t sk = level_stride(g.L, k);
+  for (int a = 0; a < 3; a++) {
+    P->OA[a] = P->A[k][a] = cdiv(lo[a], sk);
+    P->OB[a] = P->B[k][a] = cdiv(hi[a], sk);
+  }
+  for (int j = k; j >= 2; j--) {
+    int64_t M[3];
+    grid_extent(g.n, g.L, j - 1, M);
+    for (int a = 0; a < 3; a++) {
+      P->A[j - 1][a] = imax(0, P->A[j][a] / 2 - 1);
+      P->B[j - 1][a] = imin(M[a], P->B[j][a] / 2 + 2);
+    }
+  }
+  {
+    int64_t m1[3];
+    grid_extent(g.n, g.L, 1, m1);
+    for (int a = 0; a < 3; a++) {
+      P->A[1][a] = 0;
+      P->B[1][a] = m1[a];
+    }
+  }
+  // slots: level 1 whole, then for each level the bricks over the needed cells
+  int64_t nslots = 0;
+  const StreamGeo& s0 = g.s[0];
+  for (int a = 0; a < 3; a++) {
+    P->sm[0].lo[a] = 0;
+    P->sm[0].cnt[a] = s0.nb[a];
+  }
+  P->sm[0].base = 0;
+  nslots += s0.nchunks;
+  for (int j = 2; j <= k; j++) {
+    for (int a = 0; a < 3; a++) {
+      const int64_t clo = P->A[j][a] / 2, chi = cdiv(P->B[j][a], 2);
+      P->tlo[j][a] = clo / g.b[a];
+      P->tcnt[j][a] = imax(0, cdiv(chi, g.b[a]) - P->tlo[j][a]);
+    }
+    for (int K = 1; K <= 7; K++) {
+      const int sid = 1 + 7 * (j - 2) + (K - 1);
+      const StreamGeo& sg = g.s[sid];
+      SlotMap& sm = P->sm[sid];
+      int64_t c = 1;
+      for (int a = 0; a < 3; a++) {
+        sm.lo[a] = P->tlo[j][a];
+        sm.cnt[a] = imax(0, imin(P->tlo[j][a] + P->tcnt[j][a], sg.nb[a]) - P->tlo[j][a]);
+        c *= sm.cnt[a];
+      }
+      sm.base = nslots;
+      nslots += c;
+    }
+  }
+  P->nslots = nslots;
+  const size_t ps = g.dtype == STZ_F32 ? 4 : 8;
+  size_t o = 0;
+  P->dp = o;
+  o += al256(sizeof(DevParams));
+  for (int j = 1; j < (k > 1 ? k : 2); j++) {
+    P->grid[j] = o;
+    int64_t e[3] = {P->B[j][0] - P->A[j][0], P->B[j][1] - P->A[j][1], P->B[j][2] - P->A[j][2]};
+    o += al256(ps * (size_t)vol(e));
+  }
+  P->codes = o;
+  o += al256(2 * (size_t)(nslots * g.bvol));
+  P->lut = o;
+  o += al256(4 * (size_t)g.nstreams * kLutSize);
+  P->total = o;
+}
+
+}  // namespace stz
+
+using namespace stz;
+
+// ------------------------------------------------------------------ kernels
+// copy a box of the level-1 grid to the output (progressive/region at level 1)
+template <typename T>
+__global__ void k_copy_box(const T* __restrict__ src, T* __restrict__ dst, int64_t a0, int64_t a1,
+                           int64_t a2, int64_t e0, int64_t e1, int64_t e2, int64_t m1,
+                           int64_t m2) {
+  const int64_t n = e0 * e1 * e2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t x = i % e2, y = (i / e2) % e1, z = i / (e1 * e2);
+    dst[i] = src[((z + a0) * m1 + (y + a1)) * m2 + (x + a2)];
+  }
+}
+
+extern "C" {
+
+const char* stz_strerror(int code) {
+  switch (code) {
+    case STZ_OK: return "ok";
+    case STZ_ERR_ARG: return "invalid argument or unsupported option";
+    case STZ_ERR_CAPACITY: return "buffer too small";
+    case STZ_ERR_CORRUPT: return "corrupt container";
+    case STZ_ERR_CUDA: return "CUDA runtime error";
+    case STZ_ERR_TIMEOUT: return "device wait timed out";
+    case STZ_ERR_NOMEM: return "host allocation failed";
+    default: return "unknown error";
+  }
+}
+
+const char* stz_version(void) { return "stz-gb300 1.0 (sm_103a)"; }
+
+size_t stz_compress_bound(const int64_t* dims, int ndim, stz_dtype dtype) {
+  int64_t n[3];
+  if (dims3(dims, ndim, n) != STZ_OK || (dtype != STZ_F32 && dtype != STZ_F64)) return 0;
+  Geo g;
+  make_geo(n, ndim, dtype, kLevels, default_brick(ndim), &g);
+  return bound_of(g);
+}
+
+size_t stz_workspace_size(const int64_t* dims, int ndim, stz_dtype dtype) {
+  int64_t n[3];
+  if (dims3(dims, ndim, n) != STZ_OK || (dtype != STZ_F32 && dtype != STZ_F64)) return 0;
+  Geo g;
+  make_geo(n, ndim, dtype, kLevels, default_brick(ndim), &g);
+  WsPlan w = plan_compress(g);
+  DecPlan P;
+  int64_t lo[3] = {0, 0, 0};
+  plan_decode(g, g.L, lo, g.n, &P);
+  return w.total > P.total ? w.total : P.total;
+}
+
+int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype dtype,
+                 stz_eb_mode eb_mode, double eb, void* out_dev, size_t out_cap,
+                 size_t* out_bytes, void* ws_dev, size_t ws_bytes, void* stream) {
+  int64_t n[3];
+  if (dims3(dims, ndim, n) != STZ_OK) return STZ_ERR_ARG;
+  if (dtype != STZ_F32 && dtype != STZ_F64) return STZ_ERR_ARG;
+  if (eb_mode != STZ_EB_ABS && eb_mode != STZ_EB_REL) return STZ_ERR_ARG;
+  if (!(eb > 0.0) || !isfinite(eb)) return STZ_ERR_ARG;
+  if (!field_dev || !out_dev || !ws_dev || !out_bytes) return STZ_ERR_ARG;
+  const size_t ps = dtype == STZ_F32 ? 4 : 8;
+  if (((uintptr_t)field_dev % 16) || ((uintptr_t)out_dev % 8) || ((uintptr_t)ws_dev % 256))
+    return STZ_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Geo g;
+  make_geo(n, ndim, dtype, kLevels, default_brick(ndim), &g);
+  WsPlan w = plan_compress(g);
+  if (ws_bytes < w.total) return STZ_ERR_CAPACITY;
+  uint8_t* ws = (uint8_t*)ws_dev;
+  DevParams* dp = (DevParams*)(ws + w.dp);
+  uint16_t* codes = (uint16_t*)(ws + w.codes);
+  uint32_t* hist = (uint32_t*)(ws + w.hist);
+  uint32_t* chunk_out = (uint32_t*)(ws + w.chunk_out);
+  uint32_t* chunk_words = (uint32_t*)(ws + w.chunk_words);
+  unsigned long long* word_off = (unsigned long long*)(ws + w.word_off);
+  unsigned long long* out_off = (unsigned long long*)(ws + w.out_off);
+  uint16_t* enc = (uint16_t*)(ws + w.enc);
+  BookDev* books = (BookDev*)(ws + w.books);
+  LayoutDev* lay = (LayoutDev*)(ws + w.lay);
+  uint8_t* out = (uint8_t*)out_dev;
+  int rc = STZ_OK;
+#define STZ_TRY(x)          \
+  do {                      \
+    rc = (x);               \
+    if (rc != STZ_OK) return rc; \
+  } while (0)
+  STZ_TRY(cuda_ok(cudaMemsetAsync(hist, 0, 4 * (size_t)g.nstreams * kAlphabet, st)));
+  STZ_TRY(cuda_ok(cudaMemsetAsync(chunk_out, 0, 4 * (size_t)g.total_chunks, st)));
+  STZ_TRY(launch_params_init(dp, st));
+  if (eb_mode == STZ_EB_REL) STZ_TRY(launch_range(field_dev, dtype, vol(n), dp, st));
+  STZ_TRY(launch_params(dp, dtype, eb_mode, eb, g.L, kRadius, st));
+  {
+    BaseArgs a;
+    memset(&a, 0, sizeof(a));
+    a.geo = g;
+    a.dp = dp;
+    a.field = field_dev;
+    a.g1 = ws + w.grid[1];
+    a.codes = codes;
+    a.chunk_outliers = chunk_out;
+    for (int d = 0; d < 3; d++) {
+      a.sm.lo[d] = 0;
+      a.sm.cnt[d] = g.s[0].nb[d];
+    }
+    a.sm.base = g.s[0].chunk0;
+    STZ_TRY(launch_base(a, false, st));
+  }
+  STZ_TRY(launch_stream_hist(g, 0, codes, hist, st));
+  for (int l = 2; l <= g.L; l++) {
+    LevelArgs a;
+    memset(&a, 0, sizeof(a));
+    a.geo = g;
+    a.level = l;
+    a.dp = dp;
+    a.field = field_dev;
+    int64_t M[3], m[3];
+    grid_extent(g.n, g.L, l - 1, M);
+    grid_extent(g.n, g.L, l, m);
+    a.coarse = ws + w.grid[l - 1];
+    a.fine = l < g.L ? (void*)(ws + w.grid[l]) : nullptr;
+    for (int d = 0; d < 3; d++) {
+      a.clo[d] = 0;
+      a.chi[d] = M[d];
+      a.flo[d] = 0;
+      a.fhi[d] = m[d];
+      a.tlo[d] = 0;
+      a.tcnt[d] = cdiv(M[d], g.b[d]);
+    }
+    a.codes = codes;
+    a.chunk_outliers = chunk_out;
+    a.hist = hist;
+    for (int K = 1; K <= 7; K++) {
+      const StreamGeo& sg = g.s[1 + 7 * (l - 2) + K - 1];
+      for (int d = 0; d < 3; d++) {
+        a.sm[K].lo[d] = 0;
+        a.sm[K].cnt[d] = sg.nb[d];
+      }
+      a.sm[K].base = sg.chunk0;
+    }
+    STZ_TRY(launch_level(a, false, st));
+  }
+  STZ_TRY(launch_codebook(g, hist, enc, books, st));
+  STZ_TRY(launch_chunk_words(g, codes, enc, chunk_words, st));
+  STZ_TRY(launch_scan(chunk_words, word_off, g.total_chunks, st));
+  STZ_TRY(launch_scan(chunk_out, out_off, g.total_chunks, st));
+  STZ_TRY(launch_layout(g, dp, eb_mode, word_off, out_off, books, lay, out, out_cap, st));
+  STZ_TRY(launch_sections(g, lay, books, word_off, dp, out, st));
+  STZ_TRY(launch_pack(g, codes, enc, word_off, lay->s, out, dp, st));
+  STZ_TRY(launch_outliers(g, codes, field_dev, chunk_out, out_off, lay, dp, out, st));
+  unsigned long long total = 0;
+  uint32_t status = 0;
+  STZ_TRY(cuda_ok(cudaMemcpyAsync(&total, &lay->total, 8, cudaMemcpyDeviceToHost, st)));
+  STZ_TRY(cuda_ok(cudaMemcpyAsync(&status, &dp->status, 4, cudaMemcpyDeviceToHost, st)));
+  STZ_TRY(cuda_ok(cudaStreamSynchronize(st)));
+#undef STZ_TRY
+  *out_bytes = (size_t)total;
+  (void)ps;
+  if (status & kStatCapacity) return STZ_ERR_CAPACITY;
+  return STZ_OK;
+}
+
+int stz_info(const void* comp, size_t comp_bytes, int comp_on_device, stz_info_t* info) {
+  if (!info) return STZ_ERR_ARG;
+  Hdr H;
+  int rc = read_hdr(comp, comp_bytes, comp_on_device, (cudaStream_t)0, &H);
+  if (rc == STZ_ERR_CUDA || rc == STZ_ERR_CORRUPT) return rc;
+  memset(info, 0, sizeof(*info));
+  info->dtype = (stz_dtype)H.dtype;
+  info->ndim = H.ndim;
+  if (H.ndim == 3) {
+    for (int a = 0; a < 3; a++) info->dims[a] = H.n[a];
+  } else {
+    info->dims[0] = H.n[1];
+    info->dims[1] = H.n[2];
+    info->dims[2] = 1;
+  }
+  info->levels = H.L;
+  info->eb = H.eb;
+  info->eb_mode = (stz_eb_mode)H.eb_mode;
+  info->eb_abs = H.eb_abs;
+  info->total_bytes = H.total;
+  return rc;
+}
+
+static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* lo_in,
+                       const int64_t* hi_in, int level, int whole, void* out_dev, size_t out_cap,
+                       int64_t* out_dims, void* ws_dev, size_t ws_bytes, cudaStream_t st) {
+  if (!comp_dev || !out_dev || !ws_dev) return STZ_ERR_ARG;
+  if (((uintptr_t)comp_dev % 8) || ((uintptr_t)ws_dev % 256)) return STZ_ERR_ARG;
+  Hdr H;
+  int rc = read_hdr(comp_dev, comp_bytes, 1, st, &H);
+  if (rc != STZ_OK) return rc;
+  if (level == 0) level = H.L;
+  if (level < 1 || level > H.L) return STZ_ERR_ARG;
+  const size_t ps = H.dtype == STZ_F32 ? 4 : 8;
+  if ((uintptr_t)out_dev % ps) return STZ_ERR_ARG;
+  Geo g;
+  make_geo(H.n, H.ndim, H.dtype, H.L, H.b, &g);
+  int64_t lo[3] = {0, 0, 0}, hi[3] = {g.n[0], g.n[1], g.n[2]};
+  if (!whole) {
+    if (!lo_in || !hi_in) return STZ_ERR_ARG;
+    if (H.ndim == 3) {
+      for (int a = 0; a < 3; a++) {
+        lo[a] = lo_in[a];
+        hi[a] = hi_in[a];
+      }
+    } else {
+      lo[1] = lo_in[0];
+      hi[1] = hi_in[0];
+      lo[2] = lo_in[1];
+      hi[2] = hi_in[1];
+    }
+    for (int a = 0; a < 3; a++)
+      if (lo[a] < 0 || hi[a] > g.n[a] || lo[a] >= hi[a]) return STZ_ERR_ARG;
+  }
+  DecPlan P;
+  plan_decode(g, level, lo, hi, &P);
+  int64_t od[3];
+  for (int a = 0; a < 3; a++) od[a] = imax(0, P.OB[a] - P.OA[a]);
+  if (out_dims) {
+    if (H.ndim == 3) {
+      for (int a = 0; a < 3; a++) out_dims[a] = od[a];
+    } else {
+      out_dims[0] = od[1];
+      out_dims[1] = od[2];
+      out_dims[2] = 1;
+    }
+  }
+  const int64_t npts = od[0] * od[1] * od[2];
+  if (npts == 0) return STZ_OK;
+  if ((size_t)npts * ps > out_cap) return STZ_ERR_CAPACITY;
+  if (P.total > ws_bytes) return STZ_ERR_CAPACITY;
+  uint8_t* ws = (uint8_t*)ws_dev;
+  DevParams* dp = (DevParams*)(ws + P.dp);
+  uint16_t* codes = (uint16_t*)(ws + P.codes);
+  uint32_t* lut = (uint32_t*)(ws + P.lut);
+  uint32_t* status = &dp->status;
+  const uint8_t* comp = (const uint8_t*)comp_dev;
+  // decode tables
+  DecTables tb;
+  memset(&tb, 0, sizeof(tb));
+  for (int s = 0; s < H.ns; s++) {
+    DecStream& d = tb.ds[s];
+    SectHost sh = sect_host(H.d[s].nlive, H.d[s].nch, H.d[s].pw, H.d[s].nout, ps);
+    d.sect = comp + H.d[s].sect_off;
+    d.nlive = H.d[s].nlive;
+    d.nchunks = H.d[s].nch;
+    d.pw = H.d[s].pw;
+    d.off_syms = sh.off_syms;
+    d.off_lens = sh.off_lens;
+    d.off_chunks = sh.off_chunks;
+    d.off_payload = sh.off_payload;
+  }
+  const int ns_needed = 1 + 7 * (level - 1);
+  int64_t nblocks = 0;
+  for (int s = 0; s < ns_needed; s++) {
+    if (g.s[s].nsym == 0) continue;
+    tb.lut_sid[tb.nlut++] = s;
+    const SlotMap& sm = P.sm[s];
+    const int64_t c = sm.cnt[0] * sm.cnt[1] * sm.cnt[2];
+    if (c == 0) continue;
+    DecChunkJob& jb = tb.jobs[tb.njobs++];
+    jb.sid = s;
+    for (int a = 0; a < 3; a++) {
+      jb.lo[a] = sm.lo[a];
+      jb.cnt[a] = sm.cnt[a];
+    }
+    jb.slot_base = sm.base;
+    jb.nchunks_job = c;
+    jb.block0 = nblocks;
+    nblocks += cdiv(c, 128);
+  }
+  tb.nblocks = nblocks;
+#define STZ_TRY(x)               \
+  do {                           \
+    rc = (x);                    \
+    if (rc != STZ_OK) return rc; \
+  } while (0)
+  STZ_TRY(cuda_ok(cudaMemsetAsync(dp, 0, sizeof(DevParams), st)));
+  STZ_TRY(launch_lut(tb, lut, status, st));
+  STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, st));
+  const uint8_t* sec0 = comp + H.d[0].sect_off;
+  SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps);
+  uint8_t* g1buf = ws + P.grid[1];
+  {
+    BaseArgs a;
+    memset(&a, 0, sizeof(a));
+    a.geo = g;
+    a.dp = dp;
+    a.g1 = g1buf;
+    a.codes = codes;
+    a.sm = P.sm[0];
+    a.opos = (const uint32_t*)(sec0 + sh0.off_opos);
+    a.oval = sec0 + sh0.off_oval;
+    a.nout = (int64_t)H.d[0].nout;
+    a.two_eb = H.two_eb[1];
+    a.status = status;
+    STZ_TRY(launch_base(a, true, st));
+  }
+  if (level == 1) {
+    int64_t m1[3];
+    grid_extent(g.n, g.L, 1, m1);
+    const int blocks = (int)imin(cdiv(npts, 256), 4096);
+    if (ps == 4)
+      k_copy_box<float><<<blocks, 256, 0, st>>>((const float*)g1buf, (float*)out_dev, P.OA[0],
+                                                P.OA[1], P.OA[2], od[0], od[1], od[2], m1[1],
+                                                m1[2]);
+    else
+      k_copy_box<double><<<blocks, 256, 0, st>>>((const double*)g1buf, (double*)out_dev, P.OA[0],
+                                                 P.OA[1], P.OA[2], od[0], od[1], od[2], m1[1],
+                                                 m1[2]);
+    STZ_TRY(cuda_ok(cudaGetLastError()));
+  }
+  for (int j = 2; j <= level; j++) {
+    LevelArgs a;
+    memset(&a, 0, sizeof(a));
+    a.geo = g;
+    a.level = j;
+    a.dp = dp;
+    a.coarse = (j == 2) ? (const void*)g1buf : (const void*)(ws + P.grid[j - 1]);
+    a.fine = (j == level) ? out_dev : (void*)(ws + P.grid[j]);
+    for (int d = 0; d < 3; d++) {
+      a.clo[d] = P.A[j - 1][d];
+      a.chi[d] = P.B[j - 1][d];
+      a.flo[d] = P.A[j][d];
+      a.fhi[d] = P.B[j][d];
+      a.tlo[d] = P.tlo[j][d];
+      a.tcnt[d] = P.tcnt[j][d];
+    }
+    a.codes = codes;
+    for (int K = 1; K <= 7; K++) {
+      const int sid = 1 + 7 * (j - 2) + K - 1;
+      a.sm[K] = P.sm[sid];
+      const uint8_t* sec = comp + H.d[sid].sect_off;
+      SectHost sh = sect_host(H.d[sid].nlive, H.d[sid].nch, H.d[sid].pw, H.d[sid].nout, ps);
+      a.opos[K] = (const uint32_t*)(sec + sh.off_opos);
+      a.oval[K] = sec + sh.off_oval;
+      a.nout[K] = (int64_t)H.d[sid].nout;
+    }
+    a.two_eb = H.two_eb[j];
+    a.status = status;
+    STZ_TRY(launch_level(a, true, st));
+  }
+  uint32_t hstat = 0;
+  STZ_TRY(cuda_ok(cudaMemcpyAsync(&hstat, status, 4, cudaMemcpyDeviceToHost, st)));
+  STZ_TRY(cuda_ok(cudaStreamSynchronize(st)));
+#undef STZ_TRY
+  return (hstat & kStatCorrupt) ? STZ_ERR_CORRUPT : STZ_OK;
+}
+
+int stz_decompress_full(const void* comp_dev, size_t comp_bytes, void* out_dev, size_t out_cap,
+                        void* ws_dev, size_t ws_bytes, void* stream) {
+  return decode_impl(comp_dev, comp_bytes, nullptr, nullptr, 0, 1, out_dev, out_cap, nullptr,
+                     ws_dev, ws_bytes, (cudaStream_t)stream);
+}
+
+int stz_decompress_progressive(const void* comp_dev, size_t comp_bytes, int level,
+                               void* out_dev, size_t out_cap, int64_t* out_dims, void* ws_dev,
+                               size_t ws_bytes, void* stream) {
+  if (level < 1) return STZ_ERR_ARG;
+  return decode_impl(comp_dev, comp_bytes, nullptr, nullptr, level, 1, out_dev, out_cap,
+                     out_dims, ws_dev, ws_bytes, (cudaStream_t)stream);
+}
+
+int stz_decompress_region(const void* comp_dev, size_t comp_bytes, const int64_t* lo,
+                          const int64_t* hi, int level, void* out_dev, size_t out_cap,
+                          int64_t* out_dims, void* ws_dev, size_t ws_bytes, void* stream) {
+  if (level < 1) return STZ_ERR_ARG;
+  return decode_impl(comp_dev, comp_bytes, lo, hi, level, 0, out_dev, out_cap, out_dims, ws_dev,
+                     ws_bytes, (cudaStream_t)stream);
+}
+
+}  // extern "C"

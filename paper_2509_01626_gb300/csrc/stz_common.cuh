@@ -1,0 +1,221 @@
+// stz_common.cuh -- shared definitions of the STZ CUDA library (sm_103a).
+//
+// Geometry of the hierarchical partition (Sec. 3.1 Fig. 3, Sec. 3.2 three
+// levels): level l of L has stride s_l = 2^(L-l); G_l is the grid of points
+// whose coordinates are multiples of s_l.  Level 1 is G_1.  Level l >= 2 is
+// G_l minus G_{l-1}, split into 7 sub-blocks by which G_l coordinates are odd
+// (k = 4*(z odd) + 2*(y odd) + (x odd)); in 2D (nz = 1) the sub-blocks with
+// an odd z are empty.  Sub-block k holds the points 2c + o_k of G_l, with c
+// its "cell" (a point of G_{l-1}).
+//
+// Each stream (level 1, then level l sub-block k at index 1 + 7(l-2) + k-1)
+// is stored brick-major: bricks of (bz, by, bx) cells in raster order, each
+// brick one independently decodable chunk.  On the device a chunk's symbols
+// live in a "slot" of bvol = bz*by*bx entries of the code buffer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "stz.h"
+
+namespace stz {
+
+constexpr int kMaxLevels = 6;
+constexpr int kMaxStreams = 1 + 7 * (kMaxLevels - 1);
+constexpr int kLevels = 3;              // L used by stz_compress
+constexpr int kRadius = 1024;           // quantization radius R
+constexpr int kAlphabet = 2 * kRadius;  // symbols 0 (outlier) .. 2R-1
+constexpr int kMaxCodeLen = 12;         // Huffman length limit = decode table index bits
+constexpr int kLutSize = 1 << kMaxCodeLen;
+constexpr int kHeaderBytes = 256;
+constexpr int kDirEntryBytes = 48;
+constexpr int kBrick3D[3] = {8, 16, 16};
+constexpr int kBrick2D[3] = {1, 32, 64};
+
+// status bits written by kernels into DevParams::status
+constexpr uint32_t kStatCorrupt = 1u;
+constexpr uint32_t kStatCapacity = 2u;
+
+#define STZ_HD __host__ __device__ __forceinline__
+
+STZ_HD int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+STZ_HD int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
+STZ_HD int64_t imax(int64_t a, int64_t b) { return a > b ? a : b; }
+
+struct StreamGeo {
+  int64_t e[3];   // sub-block extent in cells
+  int64_t nb[3];  // bricks per axis
+  int64_t nsym;
+  int64_t nchunks;
+  int64_t chunk0;  // index of its first chunk among all streams' chunks
+  int32_t o[3];    // odd offsets of the sub-block (0 for level 1)
+  int32_t level;
+};
+
+struct Geo {
+  int64_t n[3];  // field dims (z, y, x)
+  int32_t b[3];  // brick
+  int32_t L, ndim, dtype, nstreams;
+  int64_t bvol;          // cells per brick = symbols per chunk slot
+  int64_t total_chunks;  // over all streams
+  StreamGeo s[kMaxStreams];
+};
+
+STZ_HD int64_t level_stride(int L, int l) { return (int64_t)1 << (L - l); }
+
+STZ_HD void grid_extent(const int64_t n[3], int L, int l, int64_t m[3]) {
+  int64_t s = level_stride(L, l);
+  for (int a = 0; a < 3; a++) m[a] = cdiv(n[a], s);
+}
+
+// Which bricks of a stream a kernel touches, and where their slots start in
+// the code buffer: ordinal of brick B = ((B0-lo0)*cnt1 + (B1-lo1))*cnt2 +
+// (B2-lo2); slot of chunk = base + ordinal.
+struct SlotMap {
+  int64_t lo[3];
+  int64_t cnt[3];
+  int64_t base;
+};
+
+// Position of cell c in the stream (brick-major order), its local index in
+// the brick and its slot entry in the code buffer.
+struct CellAddr {
+  int64_t pos;    // stream position (outlier indices refer to it)
+  int64_t slot;   // code buffer entry
+  int64_t chunk;  // chunk index within the stream
+};
+
+STZ_HD CellAddr cell_addr(const StreamGeo& sg, const int32_t b[3], int64_t bvol,
+                          const SlotMap& sm, int64_t c0, int64_t c1, int64_t c2) {
+  int64_t B0 = c0 / b[0], B1 = c1 / b[1], B2 = c2 / b[2];
+  int64_t l0 = imin(b[0], sg.e[0] - B0 * b[0]);
+  int64_t l1 = imin(b[1], sg.e[1] - B1 * b[1]);
+  int64_t l2 = imin(b[2], sg.e[2] - B2 * b[2]);
+  int64_t local = ((c0 - B0 * b[0]) * l1 + (c1 - B1 * b[1])) * l2 + (c2 - B2 * b[2]);
+  CellAddr r;
+  r.pos = B0 * b[0] * sg.e[1] * sg.e[2] + B1 * b[1] * l0 * sg.e[2] + B2 * b[2] * l0 * l1 + local;
+  r.chunk = (B0 * sg.nb[1] + B1) * sg.nb[2] + B2;
+  int64_t ord = ((B0 - sm.lo[0]) * sm.cnt[1] + (B1 - sm.lo[1])) * sm.cnt[2] + (B2 - sm.lo[2]);
+  r.slot = (sm.base + ord) * bvol + local;
+  return r;
+}
+
+// Chunk j of a stream: brick coordinates, clipped extent, first position.
+STZ_HD void chunk_brick(const StreamGeo& sg, const int32_t b[3], int64_t j, int64_t B[3],
+                        int64_t l[3], int64_t* start) {
+  B[0] = j / (sg.nb[1] * sg.nb[2]);
+  B[1] = (j / sg.nb[2]) % sg.nb[1];
+  B[2] = j % sg.nb[2];
+  for (int a = 0; a < 3; a++) l[a] = imin(b[a], sg.e[a] - B[a] * b[a]);
+  *start = B[0] * b[0] * sg.e[1] * sg.e[2] + B[1] * b[1] * l[0] * sg.e[2] + B[2] * b[2] * l[0] * l[1];
+}
+
+// Error-bound constants, computed on the device from the value range (or the
+// absolute bound) so that no host round trip is needed.
+struct DevParams {
+  double eb;          // as given
+  double eb_abs;      // finest-level bound
+  double vmin, vmax;  // range of finite values (relative mode), else 0
+  double eb_level[kMaxLevels + 1];  // index 1..L
+  double two_eb_d[kMaxLevels + 1];  // 2 eb_l rounded to the field precision, as double
+  float inv2eb_f[kMaxLevels + 1], two_eb_f[kMaxLevels + 1], ebc_f[kMaxLevels + 1];
+  double inv2eb_d[kMaxLevels + 1], two_eb_dd[kMaxLevels + 1], ebc_d[kMaxLevels + 1];
+  unsigned long long range_lo, range_hi;  // order-preserving keys of min / max
+  uint32_t status;
+  uint32_t pad;
+};
+
+// ---- correctly rounded single operations (no contraction into FMA) ----
+__device__ __forceinline__ float op_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float op_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float op_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float op_abs(float a) { return fabsf(a); }
+__device__ __forceinline__ double op_abs(double a) { return fabs(a); }
+__device__ __forceinline__ int to_int_rn(float v) { return __float2int_rn(v); }
+__device__ __forceinline__ int to_int_rn(double v) { return __double2int_rn(v); }
+__device__ __forceinline__ float from_int(int v, float) { return __int2float_rn(v); }
+__device__ __forceinline__ double from_int(int v, double) { return (double)v; }
+
+template <typename T> struct QConst;
+template <> struct QConst<float> {
+  float inv2eb, two_eb, ebc, rlim;
+  __device__ __forceinline__ void load(const DevParams* p, int l, int R) {
+    inv2eb = p->inv2eb_f[l];
+    two_eb = p->two_eb_f[l];
+    ebc = p->ebc_f[l];
+    rlim = (float)R - 0.5f;
+  }
+};
+template <> struct QConst<double> {
+  double inv2eb, two_eb, ebc, rlim;
+  __device__ __forceinline__ void load(const DevParams* p, int l, int R) {
+    inv2eb = p->inv2eb_d[l];
+    two_eb = p->two_eb_dd[l];
+    ebc = p->ebc_d[l];
+    rlim = (double)R - 0.5;
+  }
+};
+
+// Linear-scale quantization: q = round-half-even(d / 2eb) when |q| < R - 0.5,
+// reconstruction pred + q * 2eb accepted when within ebc of x (ebc is below
+// eb_l by at least one ulp, so the rounded test implies the exact bound).
+// Returns the symbol q + R, or 0 (outlier, reconstruction = x).
+template <typename T>
+__device__ __forceinline__ int quantize(T x, T pred, const QConst<T>& q, int R, T& xr) {
+  T d = op_sub(x, pred);
+  T qf = op_mul(d, q.inv2eb);
+  if (!(op_abs(qf) < q.rlim)) {
+    xr = x;
+    return 0;
+  }
+  int qi = to_int_rn(qf);
+  T rec = op_add(pred, op_mul(from_int(qi, T()), q.two_eb));
+  T e = op_sub(rec, x);
+  if (!(op_abs(e) <= q.ebc)) {
+    xr = x;
+    return 0;
+  }
+  xr = rec;
+  return qi + R;
+}
+
+template <typename T>
+__device__ __forceinline__ T dequantize(int sym, T pred, T two_eb, int R) {
+  return op_add(pred, op_mul(from_int(sym - R, T()), two_eb));
+}
+
+// Outlier value at stream position pos: binary search in the ascending list.
+template <typename T>
+__device__ __forceinline__ bool find_outlier(const uint32_t* pos, const T* val, int64_t n,
+                                             int64_t p, T& out) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)pos[mid] < p) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo < n && (int64_t)pos[lo] == p) {
+    out = val[lo];
+    return true;
+  }
+  return false;
+}
+
+// Per-stream decode-side pointers into a container on the device.
+template <typename T>
+struct StreamIn {
+  const uint32_t* opos;  // outlier positions
+  const T* oval;         // outlier values
+  int64_t nout;
+};
+
+// ---- host helpers (stz_api.cu) ----
+void make_geo(const int64_t n[3], int ndim, int dtype, int L, const int b[3], Geo* g);
+
+inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? STZ_OK : STZ_ERR_CUDA; }
+
+}  // namespace stz

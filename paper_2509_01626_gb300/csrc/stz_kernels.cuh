@@ -1,0 +1,125 @@
+// stz_kernels.cuh -- host-side launchers of the STZ kernels (one .cu each).
+#pragma once
+
+#include "stz_common.cuh"
+
+namespace stz {
+
+// ---- stz_range.cu: value range and error-bound constants ----
+int launch_params_init(DevParams* dp, cudaStream_t s);
+// min / max over the finite values of the field into dp->range_lo/hi
+int launch_range(const void* field, int dtype, int64_t n, DevParams* dp, cudaStream_t s);
+// eb_abs, per-level bounds and quantizer constants (one thread)
+int launch_params(DevParams* dp, int dtype, int eb_mode, double eb, int L, int R, cudaStream_t s);
+
+// ---- stz_base.cu: level 1 (SZ3-style axis passes) ----
+struct BaseArgs {
+  Geo geo;
+  const DevParams* dp;
+  const void* field;          // compress: the input field
+  void* g1;                   // level-1 grid (compact), reconstruction
+  uint16_t* codes;            // code buffer (slots)
+  uint32_t* chunk_outliers;   // compress: outliers per chunk (global chunk index)
+  SlotMap sm;                 // slots of stream 0
+  const uint32_t* opos;       // decode: outliers of stream 0
+  const void* oval;
+  int64_t nout;
+  double two_eb;              // decode: 2 eb_1 in the field precision
+  uint32_t* status;           // decode: corrupt flag
+};
+int launch_base(const BaseArgs& a, bool decode, cudaStream_t s);
+
+// ---- stz_level.cu: levels 2..L (multi-dimensional cubic prediction) ----
+struct LevelArgs {
+  Geo geo;
+  int level;                  // l >= 2
+  const DevParams* dp;
+  const void* field;          // compress: input field
+  const void* coarse;         // G_{l-1} reconstruction, box [clo, chi)
+  int64_t clo[3], chi[3];
+  void* fine;                 // G_l output, box [flo, fhi); may be null (compress, l = L)
+  int64_t flo[3], fhi[3];
+  uint16_t* codes;
+  uint32_t* chunk_outliers;   // compress
+  uint32_t* hist;             // compress: histograms of the 7 streams (2R bins each)
+  SlotMap sm[8];              // index = sub-block 1..7
+  const uint32_t* opos[8];    // decode: outliers per sub-block stream
+  const void* oval[8];
+  int64_t nout[8];
+  double two_eb;              // decode
+  uint32_t* status;
+  int64_t tlo[3], tcnt[3];    // tiles (bricks of cells) to process
+};
+int launch_level(const LevelArgs& a, bool decode, cudaStream_t s);
+
+// ---- stz_huffman.cu: histograms, codebooks, chunk coding ----
+// histogram of stream 0 from its slots
+int launch_stream_hist(const Geo& g, int sid, const uint16_t* codes, uint32_t* hist,
+                       cudaStream_t s);
+// codebook per stream: enc[s][sym] = code << 4 | len; book = nlive, syms, lens
+struct BookDev {
+  uint32_t nlive;
+  uint16_t sym[kAlphabet];
+  uint8_t len[kAlphabet];
+};
+int launch_codebook(const Geo& g, const uint32_t* hist, uint16_t* enc, BookDev* books,
+                    cudaStream_t s);
+// bits per chunk -> words per chunk
+int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc,
+                       uint32_t* chunk_words, cudaStream_t s);
+// exclusive scan of n u32 into n+1 u64 (single block)
+int launch_scan(const uint32_t* in, unsigned long long* out, int64_t n, cudaStream_t s);
+// pack every chunk's codes into the container payload
+struct SectDev;  // stz_container.cu
+int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
+                const unsigned long long* word_off, const SectDev* sect, uint8_t* out,
+                const DevParams* dp, cudaStream_t s);
+
+// decode tables: lut[s][i] = sym << 8 | len for the top-12-bit index i
+struct DecStream {
+  const uint8_t* sect;        // section start in the container
+  uint64_t nlive, nchunks, pw;
+  uint64_t off_syms, off_lens, off_chunks, off_payload;
+};
+// entropy-decode the chunks of bricks [lo, lo+cnt) of each stream into slots
+struct DecChunkJob {
+  int sid;                    // stream
+  int64_t lo[3], cnt[3];      // brick range
+  int64_t slot_base;          // slot index of the first brick
+  int64_t nchunks_job;        // cnt0*cnt1*cnt2
+  int64_t block0;             // first thread block of this job
+};
+struct DecTables {
+  DecStream ds[kMaxStreams];  // indexed by stream
+  int lut_sid[kMaxStreams];   // streams whose decode table is built
+  int nlut;
+  DecChunkJob jobs[kMaxStreams];
+  int njobs;
+  int64_t nblocks;            // thread blocks of the chunk decoder
+};
+int launch_lut(const DecTables& tb, uint32_t* lut, uint32_t* status, cudaStream_t s);
+int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,
+                         uint16_t* codes, uint32_t* status, cudaStream_t s);
+
+// ---- stz_container.cu: layout, header, sections, outliers ----
+struct SectDev {
+  unsigned long long sect_off, off_syms, off_lens, off_chunks, off_payload, off_opos, off_oval,
+      size;
+  unsigned long long pw, nout, nlive, word0, out0;
+};
+struct LayoutDev {
+  unsigned long long total;
+  SectDev s[kMaxStreams];
+};
+int launch_layout(const Geo& g, const DevParams* dp, int eb_mode,
+                  const unsigned long long* word_off, const unsigned long long* out_off,
+                  const BookDev* books, LayoutDev* lay, uint8_t* out, size_t cap,
+                  cudaStream_t s);
+int launch_sections(const Geo& g, const LayoutDev* lay, const BookDev* books,
+                    const unsigned long long* word_off, const DevParams* dp, uint8_t* out,
+                    cudaStream_t s);
+int launch_outliers(const Geo& g, const uint16_t* codes, const void* field,
+                    const uint32_t* chunk_outliers, const unsigned long long* out_off,
+                    const LayoutDev* lay, const DevParams* dp, uint8_t* out, cudaStream_t s);
+
+}  // namespace stz

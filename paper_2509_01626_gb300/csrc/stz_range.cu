@@ -1,0 +1,167 @@
+// stz_range.cu -- value range of the finite values and the error-bound
+// constants (absolute or value-range-relative bound; per-level bounds
+// eb_l = eb_{l+1} / 2.5, Sec. 3.1 opt. 5, applied level by level as in the
+// three-level scheme of Sec. 3.2).
+#include "stz_kernels.cuh"
+
+namespace stz {
+
+// Order-preserving 64-bit keys: -0 sorts below +0, finite values only.
+__device__ __forceinline__ unsigned long long key_f32(uint32_t u) {
+  return (u & 0x80000000u) ? (unsigned long long)(~u) : (unsigned long long)(u | 0x80000000u);
+}
+__device__ __forceinline__ unsigned long long key_f64(unsigned long long u) {
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double val_f32(unsigned long long k) {
+  uint32_t u = (uint32_t)k;
+  u = (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+  return (double)__uint_as_float(u);
+}
+__device__ __forceinline__ double val_f64(unsigned long long k) {
+  unsigned long long u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double((long long)u);
+}
+
+__global__ void k_params_init(DevParams* dp) {
+  dp->range_lo = ~0ull;
+  dp->range_hi = 0ull;
+  dp->status = 0;
+}
+
+__device__ __forceinline__ void upd(unsigned long long k, unsigned long long& lo,
+                                    unsigned long long& hi) {
+  lo = k < lo ? k : lo;
+  hi = k > hi ? k : hi;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_range(const void* __restrict__ field, int64_t n,
+                                               DevParams* dp) {
+  unsigned long long lo = ~0ull, hi = 0ull;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  if (DT == STZ_F32) {
+    const uint32_t* f = (const uint32_t*)field;
+    const int64_t n4 = n >> 2;
+    const uint4* f4 = (const uint4*)field;
+    for (int64_t i = tid; i < n4; i += nth) {
+      uint4 v = __ldg(f4 + i);
+      if ((v.x & 0x7F800000u) != 0x7F800000u) upd(key_f32(v.x), lo, hi);
+      if ((v.y & 0x7F800000u) != 0x7F800000u) upd(key_f32(v.y), lo, hi);
+      if ((v.z & 0x7F800000u) != 0x7F800000u) upd(key_f32(v.z), lo, hi);
+      if ((v.w & 0x7F800000u) != 0x7F800000u) upd(key_f32(v.w), lo, hi);
+    }
+    for (int64_t i = (n4 << 2) + tid; i < n; i += nth) {
+      uint32_t u = f[i];
+      if ((u & 0x7F800000u) != 0x7F800000u) upd(key_f32(u), lo, hi);
+    }
+  } else {
+    const unsigned long long* f = (const unsigned long long*)field;
+    const int64_t n2 = n >> 1;
+    const ulonglong2* f2 = (const ulonglong2*)field;
+    const unsigned long long em = 0x7FF0000000000000ull;
+    for (int64_t i = tid; i < n2; i += nth) {
+      ulonglong2 v = __ldg(f2 + i);
+      if ((v.x & em) != em) upd(key_f64(v.x), lo, hi);
+      if ((v.y & em) != em) upd(key_f64(v.y), lo, hi);
+    }
+    for (int64_t i = (n2 << 1) + tid; i < n; i += nth) {
+      unsigned long long u = f[i];
+      if ((u & em) != em) upd(key_f64(u), lo, hi);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+    unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  __shared__ unsigned long long slo[8], shi[8];
+  int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    slo[w] = lo;
+    shi[w] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
+      lo = slo[i] < lo ? slo[i] : lo;
+      hi = shi[i] > hi ? shi[i] : hi;
+    }
+    if (lo != ~0ull) atomicMin(&dp->range_lo, lo);
+    if (hi != 0ull) atomicMax(&dp->range_hi, hi);
+  }
+}
+
+// largest float <= v (v > 0)
+__device__ __forceinline__ float rz_float(double v) { return __double2float_rz(v); }
+
+__global__ void k_params(DevParams* dp, int dtype, int eb_mode, double eb, int L, int R) {
+  double vmin = 0.0, vmax = 0.0;
+  bool any = false;
+  if (eb_mode == STZ_EB_REL && dp->range_lo != ~0ull) {
+    any = true;
+    vmin = dtype == STZ_F32 ? val_f32(dp->range_lo) : val_f64(dp->range_lo);
+    vmax = dtype == STZ_F32 ? val_f32(dp->range_hi) : val_f64(dp->range_hi);
+  }
+  double ea = eb;
+  if (eb_mode == STZ_EB_REL) {
+    double range = any ? __dsub_rn(vmax, vmin) : 0.0;
+    ea = __dmul_rn(eb, range);
+    if (!(ea > 0.0) || !isfinite(ea)) ea = eb;
+  }
+  dp->eb = eb;
+  dp->eb_abs = ea;
+  dp->vmin = vmin;
+  dp->vmax = vmax;
+  for (int l = 0; l <= kMaxLevels; l++) {
+    dp->eb_level[l] = dp->two_eb_d[l] = 0.0;
+    dp->inv2eb_f[l] = dp->two_eb_f[l] = dp->ebc_f[l] = 0.f;
+    dp->inv2eb_d[l] = dp->two_eb_dd[l] = dp->ebc_d[l] = 0.0;
+  }
+  for (int l = 1; l <= L; l++) {
+    double r = 1.0;
+    for (int k = 0; k < L - l; k++) r = __dmul_rn(r, 2.5);
+    double ebl = __ddiv_rn(ea, r);
+    dp->eb_level[l] = ebl;
+    double two = __dmul_rn(2.0, ebl);
+    double inv = __ddiv_rn(1.0, two);
+    if (dtype == STZ_F32) {
+      dp->two_eb_f[l] = __double2float_rn(two);
+      dp->inv2eb_f[l] = __double2float_rn(inv);
+      dp->ebc_f[l] = nextafterf(rz_float(ebl), 0.0f);
+      dp->two_eb_d[l] = (double)dp->two_eb_f[l];
+    } else {
+      dp->two_eb_dd[l] = two;
+      dp->inv2eb_d[l] = inv;
+      dp->ebc_d[l] = nextafter(ebl, 0.0);
+      dp->two_eb_d[l] = two;
+    }
+  }
+  (void)R;
+}
+
+int launch_params_init(DevParams* dp, cudaStream_t s) {
+  k_params_init<<<1, 1, 0, s>>>(dp);
+  return cuda_ok(cudaGetLastError());
+}
+
+int launch_range(const void* field, int dtype, int64_t n, DevParams* dp, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t per = dtype == STZ_F32 ? 4 : 2;
+  int64_t want = cdiv(cdiv(n, per), 256);
+  int blocks = (int)imin(imax(want, 1), (int64_t)sms * 8);
+  if (dtype == STZ_F32) k_range<STZ_F32><<<blocks, 256, 0, s>>>(field, n, dp);
+  else k_range<STZ_F64><<<blocks, 256, 0, s>>>(field, n, dp);
+  return cuda_ok(cudaGetLastError());
+}
+
+int launch_params(DevParams* dp, int dtype, int eb_mode, double eb, int L, int R, cudaStream_t s) {
+  k_params<<<1, 1, 0, s>>>(dp, dtype, eb_mode, eb, L, R);
+  return cuda_ok(cudaGetLastError());
+}
+
+}  // namespace stz

@@ -1,0 +1,228 @@
+"""Python binding of the C ABI in include/stz.h (libstz.so).
+
+Argument marshalling only: every step of compression and decompression runs
+in the library's CUDA kernels.  torch supplies device memory and the current
+CUDA stream.  If the library is not built, importing the functions raises
+-- there is no CPU fallback.
+
+Shapes are C order, slowest first: (nz, ny, nx) or (ny, nx).  Boxes are
+half-open [lo, hi) in the same axis order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libstz.so")
+
+F32, F64 = 0, 1
+EB_ABS, EB_REL = 0, 1
+OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
+
+
+class StzError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [
+        ("dtype", ctypes.c_int),
+        ("ndim", ctypes.c_int),
+        ("dims", ctypes.c_int64 * 3),
+        ("levels", ctypes.c_int),
+        ("eb", ctypes.c_double),
+        ("eb_mode", ctypes.c_int),
+        ("eb_abs", ctypes.c_double),
+        ("total_bytes", ctypes.c_uint64),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libstz.so (build it with paper_2509_01626_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libstz.so is not built ({LIB_PATH}); run "
+                              "`python -m paper_2509_01626_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz, i64p = ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)
+        L.stz_strerror.restype = ctypes.c_char_p
+        L.stz_strerror.argtypes = [ctypes.c_int]
+        L.stz_version.restype = ctypes.c_char_p
+        L.stz_compress_bound.restype = sz
+        L.stz_compress_bound.argtypes = [i64p, ctypes.c_int, ctypes.c_int]
+        L.stz_workspace_size.restype = sz
+        L.stz_workspace_size.argtypes = [i64p, ctypes.c_int, ctypes.c_int]
+        L.stz_compress.argtypes = [vp, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_double, vp, sz, ctypes.POINTER(sz), vp, sz, vp]
+        L.stz_info.argtypes = [vp, sz, ctypes.c_int, ctypes.POINTER(_Info)]
+        L.stz_decompress_full.argtypes = [vp, sz, vp, sz, vp, sz, vp]
+        L.stz_decompress_progressive.argtypes = [vp, sz, ctypes.c_int, vp, sz, i64p, vp, sz, vp]
+        L.stz_decompress_region.argtypes = [vp, sz, i64p, i64p, ctypes.c_int, vp, sz, i64p, vp,
+                                            sz, vp]
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().stz_strerror(int(code)).decode()
+    except ImportError:
+        return str(code)
+
+
+def version() -> str:
+    return lib().stz_version().decode()
+
+
+def _i64(vals):
+    vals = list(vals) + [0] * (3 - len(vals))
+    return (ctypes.c_int64 * 3)(*[int(v) for v in vals])
+
+
+def _dt(dtype) -> int:
+    if dtype in (torch.float32, "float32"):
+        return F32
+    if dtype in (torch.float64, "float64"):
+        return F64
+    raise TypeError(f"unsupported dtype {dtype}")
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise StzError(rc, what)
+
+
+def compress_bound(shape, dtype) -> int:
+    return int(lib().stz_compress_bound(_i64(shape), len(shape), _dt(dtype)))
+
+
+def workspace_size(shape, dtype) -> int:
+    return int(lib().stz_workspace_size(_i64(shape), len(shape), _dt(dtype)))
+
+
+def alloc_workspace(shape, dtype, device=None) -> torch.Tensor:
+    return torch.empty(workspace_size(shape, dtype), dtype=torch.uint8,
+                       device=device or torch.device("cuda"))
+
+
+def compress(field: torch.Tensor, eb: float, mode: str = "rel", out: torch.Tensor | None = None,
+             workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """stz_compress: returns the container as a uint8 view of `out`."""
+    if not field.is_cuda or not field.is_contiguous():
+        raise ValueError("field must be a contiguous CUDA tensor")
+    shape = tuple(field.shape)
+    dt = _dt(field.dtype)
+    if out is None:
+        out = torch.empty(compress_bound(shape, field.dtype), dtype=torch.uint8, device=field.device)
+    if workspace is None:
+        workspace = alloc_workspace(shape, field.dtype, field.device)
+    nbytes = ctypes.c_size_t(0)
+    rc = lib().stz_compress(ctypes.c_void_p(field.data_ptr()), _i64(shape), len(shape), dt,
+                            EB_REL if mode == "rel" else EB_ABS, float(eb),
+                            ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(nbytes),
+                            ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                            _stream(stream))
+    _check(rc, "stz_compress")
+    return out[: nbytes.value]
+
+
+def info(comp: torch.Tensor) -> dict:
+    inf = _Info()
+    on_dev = 1 if comp.is_cuda else 0
+    rc = lib().stz_info(ctypes.c_void_p(comp.data_ptr()), comp.numel(), on_dev, ctypes.byref(inf))
+    if rc not in (OK, ERR_ARG):
+        _check(rc, "stz_info")
+    shape = tuple(inf.dims[:3]) if inf.ndim == 3 else tuple(inf.dims[:2])
+    return {
+        "dtype": torch.float32 if inf.dtype == F32 else torch.float64,
+        "ndim": inf.ndim,
+        "shape": shape,
+        "levels": inf.levels,
+        "eb": inf.eb,
+        "eb_mode": "rel" if inf.eb_mode == EB_REL else "abs",
+        "eb_abs": inf.eb_abs,
+        "total_bytes": int(inf.total_bytes),
+        "supported": rc == OK,
+    }
+
+
+def _shape_out(od, ndim):
+    return (int(od[0]), int(od[1]), int(od[2])) if ndim == 3 else (int(od[0]), int(od[1]))
+
+
+def decompress_full(comp: torch.Tensor, out: torch.Tensor | None = None,
+                    workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    inf = info(comp)
+    if out is None:
+        out = torch.empty(inf["shape"], dtype=inf["dtype"], device=comp.device)
+    if workspace is None:
+        workspace = alloc_workspace(inf["shape"], inf["dtype"], comp.device)
+    rc = lib().stz_decompress_full(ctypes.c_void_p(comp.data_ptr()), comp.numel(),
+                                   ctypes.c_void_p(out.data_ptr()),
+                                   out.numel() * out.element_size(),
+                                   ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                   _stream(stream))
+    _check(rc, "stz_decompress_full")
+    return out.view(inf["shape"])
+
+
+def decompress_progressive(comp: torch.Tensor, level: int, out: torch.Tensor | None = None,
+                           workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    inf = info(comp)
+    s = 1 << (inf["levels"] - level) if 1 <= level <= inf["levels"] else 1
+    shape = tuple(-(-d // s) for d in inf["shape"])
+    if out is None:
+        out = torch.empty(shape, dtype=inf["dtype"], device=comp.device)
+    if workspace is None:
+        workspace = alloc_workspace(inf["shape"], inf["dtype"], comp.device)
+    od = (ctypes.c_int64 * 3)()
+    rc = lib().stz_decompress_progressive(ctypes.c_void_p(comp.data_ptr()), comp.numel(),
+                                          int(level), ctypes.c_void_p(out.data_ptr()),
+                                          out.numel() * out.element_size(), od,
+                                          ctypes.c_void_p(workspace.data_ptr()),
+                                          workspace.numel(), _stream(stream))
+    _check(rc, "stz_decompress_progressive")
+    oshape = _shape_out(od, inf["ndim"])
+    return out.reshape(-1)[: int(torch.tensor(oshape).prod())].view(oshape)
+
+
+def decompress_region(comp: torch.Tensor, lo, hi, level: int | None = None,
+                      out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    inf = info(comp)
+    if level is None:
+        level = inf["levels"]
+    if out is None:
+        n = 1
+        for a, b in zip(lo, hi):
+            n *= max(1, b - a)
+        out = torch.empty(n, dtype=inf["dtype"], device=comp.device)
+    if workspace is None:
+        workspace = alloc_workspace(inf["shape"], inf["dtype"], comp.device)
+    od = (ctypes.c_int64 * 3)()
+    rc = lib().stz_decompress_region(ctypes.c_void_p(comp.data_ptr()), comp.numel(), _i64(lo),
+                                     _i64(hi), int(level), ctypes.c_void_p(out.data_ptr()),
+                                     out.numel() * out.element_size(), od,
+                                     ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                     _stream(stream))
+    _check(rc, "stz_decompress_region")
+    oshape = _shape_out(od, inf["ndim"])
+    n = 1
+    for v in oshape:
+        n *= v
+    return out.reshape(-1)[:n].view(oshape)

@@ -1,0 +1,103 @@
+"""The C-ABI library builds, loads and exports every function include/stz.h
+declares; its host-side argument checks and header parser work without a
+GPU (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="module")
+def stzmod():
+    from paper_2509_01626_gb300 import build, stz
+
+    build.build()
+    stz.lib()
+    return stz
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "stz.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(stz_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(stzmod):
+    names = declared_functions()
+    assert len(names) >= 9
+    L = stzmod.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    out = os.popen(f"nm -D --defined-only {stzmod.LIB_PATH}").read()
+    exported = set(re.findall(r" T (stz_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_version_and_errors(stzmod):
+    assert "sm_103a" in stzmod.version()
+    for c in (0, -1, -2, -3, -4, -5, -6):
+        assert stzmod.strerror(c) != "unknown error"
+
+
+def test_sizes(stzmod):
+    assert stzmod.compress_bound((512, 512, 512), "float32") > 512 ** 3 * 4
+    assert stzmod.workspace_size((512, 512, 512), "float32") > 512 ** 3 // 8 * 4
+    assert stzmod.compress_bound((1800, 3600), "float32") > 0
+    L = stzmod.lib()
+    bad = (ctypes.c_int64 * 3)(0, 5, 5)
+    assert L.stz_compress_bound(bad, 3, 0) == 0
+    assert L.stz_workspace_size((ctypes.c_int64 * 3)(5, 5, 5), 4, 0) == 0
+
+
+def test_argument_errors_need_no_gpu(stzmod):
+    L = stzmod.lib()
+    dims = (ctypes.c_int64 * 3)(8, 8, 8)
+    nb = ctypes.c_size_t(0)
+    vp = ctypes.c_void_p
+    # bad ndim, bad eb, null pointers: rejected before any CUDA call
+    assert L.stz_compress(vp(256), dims, 4, 0, 1, 1e-3, vp(256), 1 << 20, ctypes.byref(nb),
+                          vp(256), 1 << 20, None) == stzmod.ERR_ARG
+    assert L.stz_compress(vp(256), dims, 3, 0, 1, -1.0, vp(256), 1 << 20, ctypes.byref(nb),
+                          vp(256), 1 << 20, None) == stzmod.ERR_ARG
+    assert L.stz_compress(vp(256), dims, 3, 0, 1, float("nan"), vp(256), 1 << 20,
+                          ctypes.byref(nb), vp(256), 1 << 20, None) == stzmod.ERR_ARG
+    assert L.stz_compress(None, dims, 3, 0, 1, 1e-3, vp(256), 1 << 20, ctypes.byref(nb),
+                          vp(256), 1 << 20, None) == stzmod.ERR_ARG
+    assert L.stz_decompress_full(None, 100, vp(256), 100, vp(256), 100, None) == stzmod.ERR_ARG
+
+
+@pytest.mark.parametrize("name", ["sin3d_f32_22x19x27", "sin3d_f64_9x14x10", "sin2d_f32_37x50"])
+def test_host_header_parser_reads_oracle_containers(stzmod, ora, name):
+    comp = np.fromfile(os.path.join(GOLDEN, name + ".stz"), dtype=np.uint8)
+    ref = ora.info(comp)
+    inf = stzmod._Info()
+    rc = stzmod.lib().stz_info(comp.ctypes.data, comp.size, 0, ctypes.byref(inf))
+    assert rc == 0
+    dims = tuple(ref["dims"]) if ref["ndim"] == 3 else (ref["dims"][1], ref["dims"][2], 1)
+    assert tuple(inf.dims) == dims
+    assert inf.levels == ref["levels"] and inf.ndim == ref["ndim"]
+    assert inf.eb_abs == ref["eb_abs"] and inf.total_bytes == comp.size
+
+
+def test_host_header_parser_rejects_corruption(stzmod):
+    comp = np.fromfile(os.path.join(GOLDEN, "sin3d_f32_22x19x27.stz"), dtype=np.uint8)
+    inf = stzmod._Info()
+    L = stzmod.lib()
+    for cut in (0, 100, 255, 300):
+        b = comp[:cut].copy() if cut else np.zeros(1, np.uint8)
+        assert L.stz_info(b.ctypes.data, cut, 0, ctypes.byref(inf)) == stzmod.ERR_CORRUPT
+    rng = np.random.default_rng(0)
+    hits = 0
+    for _ in range(400):
+        b = comp.copy()
+        i = int(rng.integers(0, 256 + 15 * 48))
+        b[i] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        rc = L.stz_info(b.ctypes.data, b.size, 0, ctypes.byref(inf))
+        assert rc in (0, stzmod.ERR_CORRUPT, stzmod.ERR_ARG)
+        hits += rc != 0
+    assert hits > 100

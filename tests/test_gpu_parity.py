@@ -1,0 +1,203 @@
+"""GPU parity: the CUDA path reproduces the CPU oracle bit for bit.
+
+Compression must give the identical container (codes, outliers, codebooks,
+payload, header); every decode (full, progressive to each level, random
+boxes) must give bitwise the oracle's values.  Inputs are the seeded
+synthetic workloads (paper_2509_01626_gb300.synth) at sizes the oracle
+finishes in seconds, ragged shapes that leave partial bricks, 2D and f64
+fields, degenerate fields (constant, tiny, non-finite values), and the full
+512^3 workload.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2509_01626_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="module")
+def stzg():
+    from paper_2509_01626_gb300 import build, stz
+
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    stz.lib()
+    return stz
+
+
+def _nonfinite():
+    x = synth.sinusoids((23, 31, 17), 8)
+    x[1, 2, 3] = np.nan
+    x[0, 0, 0] = np.inf
+    x[22, 30, 16] = -np.inf
+    x[10, 10, 10] = np.float32(3e38)
+    return x
+
+
+CASES = {
+    "sin128_rel1e-3": (lambda: synth.sinusoids((128, 128, 128), synth.seed_for(1)), 1e-3, "rel"),
+    "grf128_rel1e-2": (lambda: synth.grf((128, 128, 128), synth.seed_for(2)), 1e-2, "rel"),
+    "grf128_rel1e-3": (lambda: synth.grf((128, 128, 128), synth.seed_for(2)), 1e-3, "rel"),
+    "grf128_rel1e-4": (lambda: synth.grf((128, 128, 128), synth.seed_for(2)), 1e-4, "rel"),
+    "grf128_rel1e-5": (lambda: synth.grf((128, 128, 128), synth.seed_for(2)), 1e-5, "rel"),
+    "ragged_37x29x41": (lambda: synth.sinusoids((37, 29, 41), 3), 1e-3, "rel"),
+    "ragged_5x3x200": (lambda: synth.sinusoids((5, 3, 200), 4), 1e-4, "rel"),
+    "tiny_1x1x1": (lambda: np.array([[[1.5]]], dtype=np.float32), 1e-3, "rel"),
+    "tiny_2x3x1": (lambda: synth.sinusoids((2, 3, 1), 5), 1e-3, "abs"),
+    "ones_axis_1x40x1": (lambda: synth.sinusoids((1, 40, 1), 6), 1e-3, "rel"),
+    "2d_180x360": (lambda: synth.banded2d((180, 360), 7), 1e-3, "rel"),
+    "2d_97x33": (lambda: synth.banded2d((97, 33), 8), 1e-2, "abs"),
+    "f64_40x33x27": (lambda: synth.sinusoids((40, 33, 27), 9, dtype=np.float64), 1e-5, "rel"),
+    "f64_2d_70x90": (lambda: synth.banded2d((70, 90), 10, dtype=np.float64), 1e-6, "rel"),
+    "abs_64": (lambda: synth.sinusoids((64, 64, 64), 11), 5e-3, "abs"),
+    "const_20": (lambda: np.full((20, 20, 20), 3.25, dtype=np.float32), 1e-3, "rel"),
+    "nonfinite": (_nonfinite, 1e-3, "rel"),
+}
+
+_cache = {}
+
+
+def case(name, ora):
+    if name not in _cache:
+        gen, eb, mode = CASES[name]
+        x = np.ascontiguousarray(gen())
+        _cache[name] = (x, eb, mode, ora.compress(x, eb, mode))
+    return _cache[name]
+
+
+def describe_mismatch(ora, got, ref):
+    """Which stream differs (decode both with the oracle)."""
+    msg = [f"sizes gpu={got.size} oracle={ref.size}"]
+    n = min(got.size, ref.size)
+    d = np.nonzero(got[:n] != ref[:n])[0]
+    if d.size:
+        msg.append(f"first differing byte {int(d[0])}")
+    try:
+        cg, sg = ora.decode_streams(got)
+        cr, sr = ora.decode_streams(ref)
+        for s in range(len(sr) - 1):
+            a, b = cg[sg[s]:sg[s + 1]], cr[sr[s]:sr[s + 1]]
+            if not np.array_equal(a, b):
+                k = int(np.nonzero(a != b)[0][0])
+                msg.append(f"stream {s} first code mismatch at {k}: gpu {a[k]} oracle {b[k]}")
+                break
+    except Exception as e:  # noqa: BLE001
+        msg.append(f"gpu container not decodable by the oracle: {e}")
+    return "; ".join(msg)
+
+
+def gpu_compress(stzg, x, eb, mode):
+    comp = stzg.compress(torch.from_numpy(x).cuda(), eb, mode)
+    return comp
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_compress_matches_oracle(stzg, ora, name):
+    x, eb, mode, ref = case(name, ora)
+    got = gpu_compress(stzg, x, eb, mode).cpu().numpy()
+    assert got.size == ref.size and np.array_equal(got, ref), describe_mismatch(ora, got, ref)
+
+
+def _bits(a):
+    return a.view(np.uint32 if a.dtype == np.float32 else np.uint64)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_decode_matches_oracle(stzg, ora, name):
+    x, eb, mode, ref = case(name, ora)
+    comp = torch.from_numpy(ref).cuda()
+    full = stzg.decompress_full(comp).cpu().numpy()
+    want = ora.decompress(ref)
+    assert full.shape == want.shape
+    assert np.array_equal(_bits(full), _bits(want))
+    fin = np.isfinite(x)
+    eb_abs = ora.info(ref)["eb_abs"]
+    assert (np.abs(full[fin].astype(np.float64) - x[fin]) <= eb_abs).all()
+    L = ora.info(ref)["levels"]
+    for k in range(1, L + 1):
+        p = stzg.decompress_progressive(comp, k).cpu().numpy()
+        assert np.array_equal(_bits(p), _bits(ora.decompress(ref, k))), k
+
+
+@pytest.mark.parametrize("name", ["sin128_rel1e-3", "ragged_37x29x41", "2d_180x360",
+                                  "f64_40x33x27", "nonfinite", "ones_axis_1x40x1"])
+def test_regions_match_oracle(stzg, ora, name):
+    x, eb, mode, ref = case(name, ora)
+    comp = torch.from_numpy(ref).cuda()
+    emax = min(64, max(x.shape))
+    boxes = synth.random_boxes(x.shape, 20, 1234, min(8, emax), emax)
+    full = ora.decompress(ref)
+    for i, (lo, hi) in enumerate(boxes):
+        level = 1 + i % 3
+        r = stzg.decompress_region(comp, lo, hi, level).cpu().numpy()
+        s = 1 << (3 - level)
+        sl = tuple(slice(-(-a // s) * s, b, s) for a, b in zip(lo, hi))
+        assert np.array_equal(_bits(r), _bits(np.ascontiguousarray(full[sl]))), (lo, hi, level)
+
+
+@pytest.mark.parametrize("name", ["sin3d_f32_22x19x27", "sin3d_f64_9x14x10", "sin2d_f32_37x50"])
+def test_golden_containers_decode(stzg, ora, name):
+    ref = np.fromfile(os.path.join(GOLDEN, name + ".stz"), dtype=np.uint8)
+    got = stzg.decompress_full(torch.from_numpy(ref).cuda()).cpu().numpy()
+    assert np.array_equal(_bits(got), _bits(ora.decompress(ref)))
+
+
+def test_capacity_error_reports_size(stzg, ora):
+    x = synth.sinusoids((32, 32, 32), 3)
+    xt = torch.from_numpy(x).cuda()
+    ref = ora.compress(x, 1e-3)
+    small = torch.empty(1000, dtype=torch.uint8, device="cuda")
+    with pytest.raises(stzg.StzError) as e:
+        stzg.compress(xt, 1e-3, out=small)
+    assert e.value.code == stzg.ERR_CAPACITY
+    ok = stzg.compress(xt, 1e-3).cpu().numpy()
+    assert np.array_equal(ok, ref)
+
+
+def test_corrupt_payload_is_harmless(stzg, ora):
+    """Bit flips after the directory never fault the device: each decode
+    returns ok or STZ_ERR_CORRUPT, and the context stays usable."""
+    x = synth.sinusoids((48, 40, 36), 12)
+    ref = ora.compress(x, 1e-3)
+    rng = np.random.default_rng(3)
+    start = 256 + 15 * 48
+    for _ in range(40):
+        b = ref.copy()
+        for _ in range(4):
+            i = int(rng.integers(start, b.size))
+            b[i] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        try:
+            stzg.decompress_full(torch.from_numpy(b).cuda())
+        except stzg.StzError as e:
+            assert e.code in (stzg.ERR_CORRUPT, stzg.ERR_ARG)
+    torch.cuda.synchronize()
+    got = stzg.decompress_full(torch.from_numpy(ref).cuda()).cpu().numpy()
+    assert np.array_equal(got, ora.decompress(ref))
+
+
+def test_full_size_512_grf(stzg, ora):
+    """The 512^3 workload: the GPU container equals the oracle's, and the GPU
+    decode equals the oracle's reconstruction, in full."""
+    x = synth.grf((512, 512, 512), synth.seed_for(2), device="cuda")
+    xt = torch.from_numpy(x).cuda()
+    got = stzg.compress(xt, 1e-3, "rel").cpu().numpy()
+    ref = ora.compress(x, 1e-3, "rel")
+    assert got.size == ref.size and np.array_equal(got, ref), describe_mismatch(ora, got, ref)
+    comp = torch.from_numpy(ref).cuda()
+    full = stzg.decompress_full(comp).cpu().numpy()
+    codes, soff, recon, ebs = ora.quantize(x, 1e-3, "rel")
+    assert np.array_equal(_bits(full), _bits(recon))
+    p2 = stzg.decompress_progressive(comp, 2).cpu().numpy()
+    assert np.array_equal(_bits(p2), _bits(recon[::2, ::2, ::2]))
+    for lo, hi in synth.random_boxes(x.shape, 5, 77, 16, 256):
+        r = stzg.decompress_region(comp, lo, hi, 3).cpu().numpy()
+        sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+        assert np.array_equal(_bits(r), _bits(np.ascontiguousarray(recon[sl])))
