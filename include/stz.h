@@ -138,6 +138,23 @@ int stz_decompress_region(const void* comp_dev, size_t comp_bytes, const int64_t
                           const int64_t* hi, int level, void* out_dev, size_t out_cap,
                           int64_t* out_dims, void* ws_dev, size_t ws_bytes, void* stream);
 
+/* ---- tracing (no counterpart in the paper, which reports wall times only) ----
+ * Every kernel launch of the library is counted.  With profiling enabled an
+ * event pair is recorded around each launch on its stream; stz_profile_read
+ * waits for those events and returns, per kernel name, the number of timed
+ * launches and their summed device time.  Off by default. */
+typedef struct {
+  char name[48];
+  unsigned long long launches;
+  double total_ms;
+} stz_kernel_time;
+
+unsigned long long stz_launch_count(void);
+void stz_profile_enable(int on);
+void stz_profile_reset(void);
+/* Fills up to max_entries entries; returns the number of kernel names seen. */
+int stz_profile_read(stz_kernel_time* out, int max_entries);
+
 #ifdef __cplusplus
 }
 #endif

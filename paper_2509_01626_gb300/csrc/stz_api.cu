@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include "stz_kernels.cuh"
+#include "stz_prof.cuh"
 
 namespace stz {
 
@@ -635,6 +636,7 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
     int64_t m1[3];
     grid_extent(g.n, g.L, 1, m1);
     const int blocks = (int)imin(cdiv(npts, 256), 4096);
+    ProfScope ps_("k_copy_box", st);
     if (ps == 4)
       k_copy_box<float><<<blocks, 256, 0, st>>>((const float*)g1buf, (float*)out_dev, P.OA[0],
                                                 P.OA[1], P.OA[2], od[0], od[1], od[2], m1[1],

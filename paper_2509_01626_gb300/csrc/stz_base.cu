@@ -8,6 +8,7 @@
 // itself, so each is one launch with a thread per point; the level-1 grid
 // (8 MiB for a 512^3 field) stays resident in L2 across passes.
 #include "stz_kernels.cuh"
+#include "stz_prof.cuh"
 #include "stz_predict.cuh"
 
 namespace stz {
@@ -84,7 +85,11 @@ static int run_passes(const BaseArgs& a, cudaStream_t s) {
   p.axis = 0;
   p.t = 1;
   p.origin = 1;
-  k_base_pass<T, DEC><<<1, 32, 0, s>>>(a, p);
+  const char* nm = DEC ? "k_base_pass_dec" : "k_base_pass_enc";
+  {
+    ProfScope ps_(nm, s);
+    k_base_pass<T, DEC><<<1, 32, 0, s>>>(a, p);
+  }
   p.origin = 0;
   for (int64_t t = T_ >> 1; t >= 1; t >>= 1) {
     for (int ax = 0; ax < 3; ax++) {
@@ -109,6 +114,7 @@ static int run_passes(const BaseArgs& a, cudaStream_t s) {
       }
       if (p.total == 0) continue;
       int64_t blocks = cdiv(p.total, 256);
+      ProfScope ps_(nm, s);
       k_base_pass<T, DEC><<<(unsigned)blocks, 256, 0, s>>>(a, p);
     }
   }

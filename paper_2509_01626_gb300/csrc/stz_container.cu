@@ -7,6 +7,7 @@
 // words, u32 outlier positions (ascending stream positions) and the raw
 // outlier values in the field's type.
 #include "stz_kernels.cuh"
+#include "stz_prof.cuh"
 
 namespace stz {
 
@@ -100,6 +101,7 @@ int launch_layout(const Geo& g, const DevParams* dp, int eb_mode,
                   const unsigned long long* word_off, const unsigned long long* out_off,
                   const BookDev* books, LayoutDev* lay, uint8_t* out, size_t cap,
                   cudaStream_t s) {
+  ProfScope ps_("k_layout", s);
   k_layout<<<1, 1, 0, s>>>(g, dp, eb_mode, word_off, out_off, books, lay, out,
                            (unsigned long long)cap);
   return cuda_ok(cudaGetLastError());
@@ -144,6 +146,7 @@ int launch_sections(const Geo& g, const LayoutDev* lay, const BookDev* books,
                     const unsigned long long* word_off, const DevParams* dp, uint8_t* out,
                     cudaStream_t s) {
   int64_t blocks = imax(g.nstreams, imin(cdiv(g.total_chunks, 256), 1024));
+  ProfScope ps_("k_sections", s);
   k_sections<<<(unsigned)blocks, 256, 0, s>>>(g, lay, books, word_off, dp, out);
   return cuda_ok(cudaGetLastError());
 }
@@ -194,6 +197,7 @@ int launch_outliers(const Geo& g, const uint16_t* codes, const void* field,
                     const uint32_t* chunk_outliers, const unsigned long long* out_off,
                     const LayoutDev* lay, const DevParams* dp, uint8_t* out, cudaStream_t s) {
   int64_t blocks = imax(1, imin(cdiv(g.total_chunks, 256), 1024));
+  ProfScope ps_("k_outliers", s);
   if (g.dtype == STZ_F32)
     k_outliers<float><<<(unsigned)blocks, 256, 0, s>>>(g, codes, (const float*)field,
                                                        chunk_outliers, out_off, lay, dp, out);

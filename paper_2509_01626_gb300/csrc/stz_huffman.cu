@@ -11,6 +11,7 @@
 // Decoding: 4096-entry table indexed by the next 12 bits, one thread per
 // chunk.
 #include "stz_kernels.cuh"
+#include "stz_prof.cuh"
 
 namespace stz {
 
@@ -38,6 +39,7 @@ int launch_stream_hist(const Geo& g, int sid, const uint16_t* codes, uint32_t* h
                        cudaStream_t s) {
   if (g.s[sid].nchunks == 0) return STZ_OK;
   int blocks = (int)imin(g.s[sid].nchunks, 304);
+  ProfScope ps_("k_stream_hist", s);
   k_stream_hist<<<blocks, 256, 0, s>>>(g, sid, codes, hist);
   return cuda_ok(cudaGetLastError());
 }
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
 
 int launch_codebook(const Geo& g, const uint32_t* hist, uint16_t* enc, BookDev* books,
                     cudaStream_t s) {
+  ProfScope ps_("k_codebook", s);
   k_codebook<<<g.nstreams, kBookThreads, 0, s>>>(hist, enc, books);
   return cuda_ok(cudaGetLastError());
 }
@@ -235,6 +238,7 @@ int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc,
                        cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
   int64_t blocks = cdiv(g.total_chunks * 32, 256);
+  ProfScope ps_("k_chunk_words", s);
   k_chunk_words<<<(unsigned)blocks, 256, 0, s>>>(g, codes, enc, words);
   return cuda_ok(cudaGetLastError());
 }
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ in,
 }
 
 int launch_scan(const uint32_t* in, unsigned long long* out, int64_t n, cudaStream_t s) {
+  ProfScope ps_("k_scan", s);
   k_scan<<<1, 1024, 0, s>>>(in, out, n);
   return cuda_ok(cudaGetLastError());
 }
@@ -332,6 +337,7 @@ int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
       cudaSuccess)
     return STZ_ERR_CUDA;
   int64_t blocks = cdiv(g.total_chunks, kPackWarps);
+  ProfScope ps_("k_pack", s);
   k_pack<<<(unsigned)blocks, kPackWarps * 32, smem, s>>>(g, codes, enc, word_off, sect, out, dp);
   return cuda_ok(cudaGetLastError());
 }
@@ -396,6 +402,7 @@ __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables t
 
 int launch_lut(const DecTables& tb, uint32_t* lut, uint32_t* status, cudaStream_t s) {
   if (tb.nlut == 0) return STZ_OK;
+  ProfScope ps_("k_lut", s);
   k_lut<<<tb.nlut, 256, 0, s>>>(tb, lut, status);
   return cuda_ok(cudaGetLastError());
 }
@@ -466,6 +473,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_chunks(
 int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,
                          uint16_t* codes, uint32_t* status, cudaStream_t s) {
   if (tb.nblocks == 0) return STZ_OK;
+  ProfScope ps_("k_decode_chunks", s);
   k_decode_chunks<<<(unsigned)tb.nblocks, kDecThreads, 0, s>>>(g, tb, lut, codes, status);
   return cuda_ok(cudaGetLastError());
 }

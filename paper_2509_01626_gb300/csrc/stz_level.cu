@@ -13,7 +13,10 @@
 // over tiles; compress accumulates per-stream histograms in shared memory
 // (16-bit counters packed in pairs, flushed before they can overflow).
 #include "stz_kernels.cuh"
+#include "stz_prof.cuh"
 #include "stz_predict.cuh"
+
+#include <stdio.h>
 
 namespace stz {
 
@@ -230,6 +233,10 @@ static int run_level(const LevelArgs& a, cudaStream_t s) {
   int64_t ntiles = a.tcnt[0] * a.tcnt[1] * a.tcnt[2];
   if (ntiles == 0) return STZ_OK;
   int64_t grid = imin(ntiles, (int64_t)sms * per_sm);
+  char nm[48];
+  snprintf(nm, sizeof(nm), "k_level%d_%s_%s", a.level, DEC ? "dec" : "enc",
+           sizeof(T) == 4 ? "f32" : "f64");
+  ProfScope ps_(nm, s);
   kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(a);
   return cuda_ok(cudaGetLastError());
 }

@@ -3,6 +3,7 @@
 // eb_l = eb_{l+1} / 2.5, Sec. 3.1 opt. 5, applied level by level as in the
 // three-level scheme of Sec. 3.2).
 #include "stz_kernels.cuh"
+#include "stz_prof.cuh"
 
 namespace stz {
 
@@ -143,6 +144,7 @@ __global__ void k_params(DevParams* dp, int dtype, int eb_mode, double eb, int L
 }
 
 int launch_params_init(DevParams* dp, cudaStream_t s) {
+  ProfScope ps_("k_params_init", s);
   k_params_init<<<1, 1, 0, s>>>(dp);
   return cuda_ok(cudaGetLastError());
 }
@@ -154,12 +156,14 @@ int launch_range(const void* field, int dtype, int64_t n, DevParams* dp, cudaStr
   int64_t per = dtype == STZ_F32 ? 4 : 2;
   int64_t want = cdiv(cdiv(n, per), 256);
   int blocks = (int)imin(imax(want, 1), (int64_t)sms * 8);
+  ProfScope ps_("k_range", s);
   if (dtype == STZ_F32) k_range<STZ_F32><<<blocks, 256, 0, s>>>(field, n, dp);
   else k_range<STZ_F64><<<blocks, 256, 0, s>>>(field, n, dp);
   return cuda_ok(cudaGetLastError());
 }
 
 int launch_params(DevParams* dp, int dtype, int eb_mode, double eb, int L, int R, cudaStream_t s) {
+  ProfScope ps_("k_params", s);
   k_params<<<1, 1, 0, s>>>(dp, dtype, eb_mode, eb, L, R);
   return cuda_ok(cudaGetLastError());
 }

@@ -42,6 +42,11 @@ class _Info(ctypes.Structure):
     ]
 
 
+class _KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_ulonglong),
+                ("total_ms", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -68,6 +73,9 @@ def lib() -> ctypes.CDLL:
         L.stz_decompress_progressive.argtypes = [vp, sz, ctypes.c_int, vp, sz, i64p, vp, sz, vp]
         L.stz_decompress_region.argtypes = [vp, sz, i64p, i64p, ctypes.c_int, vp, sz, i64p, vp,
                                             sz, vp]
+        L.stz_launch_count.restype = ctypes.c_ulonglong
+        L.stz_profile_enable.argtypes = [ctypes.c_int]
+        L.stz_profile_read.argtypes = [ctypes.POINTER(_KernelTime), ctypes.c_int]
         _lib = L
     return _lib
 
@@ -166,8 +174,10 @@ def _shape_out(od, ndim):
 
 
 def decompress_full(comp: torch.Tensor, out: torch.Tensor | None = None,
-                    workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    inf = info(comp)
+                    workspace: torch.Tensor | None = None, stream=None,
+                    meta: dict | None = None) -> torch.Tensor:
+    """stz_decompress_full; `meta` (from info()) skips reading the header here."""
+    inf = meta or info(comp)
     if out is None:
         out = torch.empty(inf["shape"], dtype=inf["dtype"], device=comp.device)
     if workspace is None:
@@ -182,8 +192,9 @@ def decompress_full(comp: torch.Tensor, out: torch.Tensor | None = None,
 
 
 def decompress_progressive(comp: torch.Tensor, level: int, out: torch.Tensor | None = None,
-                           workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    inf = info(comp)
+                           workspace: torch.Tensor | None = None, stream=None,
+                           meta: dict | None = None) -> torch.Tensor:
+    inf = meta or info(comp)
     s = 1 << (inf["levels"] - level) if 1 <= level <= inf["levels"] else 1
     shape = tuple(-(-d // s) for d in inf["shape"])
     if out is None:
@@ -203,8 +214,8 @@ def decompress_progressive(comp: torch.Tensor, level: int, out: torch.Tensor | N
 
 def decompress_region(comp: torch.Tensor, lo, hi, level: int | None = None,
                       out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
-                      stream=None) -> torch.Tensor:
-    inf = info(comp)
+                      stream=None, meta: dict | None = None) -> torch.Tensor:
+    inf = meta or info(comp)
     if level is None:
         level = inf["levels"]
     if out is None:
@@ -226,3 +237,24 @@ def decompress_region(comp: torch.Tensor, lo, hi, level: int | None = None,
     for v in oshape:
         n *= v
     return out.reshape(-1)[:n].view(oshape)
+
+
+def launch_count() -> int:
+    """Kernel launches made by the library so far (all streams)."""
+    return int(lib().stz_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    lib().stz_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    lib().stz_profile_reset()
+
+
+def profile_read() -> dict:
+    """{kernel name: (timed launches, total device ms)} since the last reset."""
+    buf = (_KernelTime * 64)()
+    n = lib().stz_profile_read(buf, 64)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+            for i in range(min(n, 64))}
