@@ -59,6 +59,7 @@ class _Params(ctypes.Structure):
         ("radius", ctypes.c_int),
         ("max_code_len", ctypes.c_int),
         ("brick", ctypes.c_int * 3),
+        ("nsub", ctypes.c_int),
     ]
 
 
@@ -119,7 +120,7 @@ def _dims3(shape):
 
 
 def make_params(shape, dtype, eb, mode="rel", levels=3, radius=1024, max_code_len=12,
-                brick=None) -> _Params:
+                brick=None, nsub=4) -> _Params:
     ndim, d3 = _dims3(shape)
     if brick is None:
         brick = BRICK_3D if ndim == 3 else BRICK_2D
@@ -134,6 +135,7 @@ def make_params(shape, dtype, eb, mode="rel", levels=3, radius=1024, max_code_le
     p.levels = int(levels)
     p.radius = int(radius)
     p.max_code_len = int(max_code_len)
+    p.nsub = int(nsub)
     return p
 
 
@@ -194,6 +196,7 @@ def info(comp: np.ndarray) -> dict:
         "radius": p.radius,
         "max_code_len": p.max_code_len,
         "brick": tuple(p.brick),
+        "nsub": p.nsub,
         "eb_mode": "rel" if p.eb_mode == 1 else "abs",
         "eb": p.eb,
         "eb_abs": inf.eb_abs,

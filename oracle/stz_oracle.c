@@ -25,7 +25,7 @@
  * Byte format (little-endian; the paper fixes none of it):
  *   header, 256 bytes:
  *     0 "STZ1" | 4 u16 version=1 | 6 u8 dtype | 7 u8 ndim | 8 u8 levels |
- *     9 u8 eb_mode | 10 u8 max_code_len | 11 u8 0 | 12 u32 radius |
+ *     9 u8 eb_mode | 10 u8 max_code_len | 11 u8 nsub | 12 u32 radius |
  *     16 u32 brick z,y,x | 28 u32 nstreams | 32 i64 nz,ny,nx | 56 f64 eb |
  *     64 f64 eb_abs | 72 f64 min | 80 f64 max | 88 u64 total_bytes |
  *     96 f64 eb_level[6] | 144 f64 two_eb[6] | 192 f64 ratio | rest 0
@@ -34,7 +34,8 @@
  *     u64 payload_words | u64 noutliers | u64 0
  *   stream section (8-byte aligned):
  *     u16 sym[nlive], u8 len[nlive]  (canonical order: length, then symbol)
- *     pad to 4 | u32 chunk_word_offset[nchunks] | u32 payload[payload_words]
+ *     pad to 4 | u32 chunk_word_offset[nchunks] |
+ *     u16 sub_offset[nchunks][nsub-1] | pad to 4 | u32 payload[payload_words]
  *     | u32 outlier_pos[noutliers] | pad to 8 | P outlier_val[noutliers] |
  *     pad to 8
  *   Streams: 0 = level 1; 1 + 7(l-2) + (k-1) = level l, sub-block k, where
@@ -42,7 +43,11 @@
  *   order: bricks of (bz, by, bx) cells in raster order, cells of a brick in
  *   raster order over the brick clipped to the sub-block.  Each brick is one
  *   chunk: its codes are written MSB-first into 32-bit words starting at its
- *   word offset, padded with zero bits to a whole word.
+ *   word offset, padded with zero bits to a whole word.  A chunk of n symbols
+ *   is cut into nsub sub-chunks of q = ceil(n / nsub) symbols (the last ones
+ *   shorter or empty) whose codes follow each other without padding;
+ *   sub_offset[k-1] is the bit position, relative to the chunk's first bit,
+ *   where sub-chunk k starts, so each sub-chunk decodes on its own.
  */
 #include "stz_oracle.h"
 
@@ -370,15 +375,16 @@ static size_t al4(size_t v) { return (v + 3) & ~(size_t)3; }
 static size_t al8(size_t v) { return (v + 7) & ~(size_t)7; }
 
 typedef struct {
-  size_t off_syms, off_lens, off_chunks, off_payload, off_opos, off_oval, size;
+  size_t off_syms, off_lens, off_chunks, off_subs, off_payload, off_opos, off_oval, size;
 } sect_layout;
 
 static void sect_of(uint64_t nlive, uint64_t nchunks, uint64_t pw, uint64_t no,
-                    size_t ps, sect_layout* s) {
+                    size_t ps, int nsub, sect_layout* s) {
   s->off_syms = 0;
   s->off_lens = 2 * nlive;
   s->off_chunks = al4(3 * nlive);
-  s->off_payload = s->off_chunks + 4 * nchunks;
+  s->off_subs = s->off_chunks + 4 * nchunks;
+  s->off_payload = al4(s->off_subs + 2 * nchunks * (uint64_t)(nsub - 1));
   s->off_opos = s->off_payload + 4 * pw;
   s->off_oval = al8(s->off_opos + 4 * no);
   s->size = al8(s->off_oval + ps * no);
@@ -428,7 +434,8 @@ static int check_params(const ora_params* p) {
   if ((int64_t)2 * p->radius > ((int64_t)1 << p->max_code_len)) return ORA_ERR_ARG;
   for (int a = 0; a < 3; a++)
     if (p->brick[a] < 1 || p->brick[a] > 4096) return ORA_ERR_ARG;
-  if ((int64_t)p->brick[0] * p->brick[1] * p->brick[2] > 65536) return ORA_ERR_ARG;
+  if ((int64_t)p->brick[0] * p->brick[1] * p->brick[2] * p->max_code_len > 65535) return ORA_ERR_ARG;
+  if (p->nsub != 1 && p->nsub != 2 && p->nsub != 4 && p->nsub != 8) return ORA_ERR_ARG;
   return ORA_OK;
 }
 
@@ -456,7 +463,7 @@ size_t ora_compress_bound(const ora_params* p) {
     uint64_t nlive = nsym < (uint64_t)(2 * p->radius) ? nsym : (uint64_t)(2 * p->radius);
     uint64_t pw = (nsym * (uint64_t)p->max_code_len + 31) / 32 + nch;
     sect_layout sl;
-    sect_of(nlive, nch, pw, nsym, ps, &sl);
+    sect_of(nlive, nch, pw, nsym, ps, p->nsub, &sl);
     total += sl.size;
   }
   return total;
@@ -611,7 +618,7 @@ int ora_compress(const void* field, const ora_params* p, uint8_t* out, size_t ca
     }
     pw[s] = words;
     sect_layout sl;
-    sect_of(nlive[s], nch[s], pw[s], nout[s], ps, &sl);
+    sect_of(nlive[s], nch[s], pw[s], nout[s], ps, p->nsub, &sl);
     sect_off[s] = total;
     total += sl.size;
   }
@@ -630,6 +637,7 @@ int ora_compress(const void* field, const ora_params* p, uint8_t* out, size_t ca
   out[8] = (uint8_t)g.L;
   out[9] = (uint8_t)p->eb_mode;
   out[10] = (uint8_t)p->max_code_len;
+  out[11] = (uint8_t)p->nsub;
   put32(out + 12, (uint32_t)p->radius);
   for (int a = 0; a < 3; a++) put32(out + 16 + 4 * a, (uint32_t)g.b[a]);
   put32(out + 28, (uint32_t)ns);
@@ -664,7 +672,7 @@ int ora_compress(const void* field, const ora_params* p, uint8_t* out, size_t ca
     ora_huffman_lengths(hist, nsym_alpha, p->max_code_len, lens);
     canonical(lens, nsym_alpha, cb);
     sect_layout sl;
-    sect_of(nlive[s], nch[s], pw[s], nout[s], ps, &sl);
+    sect_of(nlive[s], nch[s], pw[s], nout[s], ps, p->nsub, &sl);
     uint8_t* sec = out + sect_off[s];
     for (int k = 0; k < cb->nlive; k++) {
       put16(sec + sl.off_syms + 2 * (size_t)k, cb->sym[k]);
@@ -678,8 +686,16 @@ int ora_compress(const void* field, const ora_params* p, uint8_t* out, size_t ca
       put32(sec + sl.off_chunks + 4 * (size_t)j, (uint32_t)wpos);
       uint64_t acc = 0;
       int nacc = 0;
-      for (int64_t k = 0; k < count; k++) {
+      const int64_t q = (count + p->nsub - 1) / p->nsub;
+      uint64_t cbits = 0;
+      for (int64_t k = 0; k <= count; k++) {
+        /* sub-chunk boundaries: bit position of symbol k*q (or of the end) */
+        for (int u = 1; u < p->nsub; u++)
+          if ((u * q < count ? u * q : count) == k)
+            put16(sec + sl.off_subs + 2 * ((size_t)j * (p->nsub - 1) + (u - 1)), (uint16_t)cbits);
+        if (k == count) break;
         int sym = codes[soff[s] + start + k];
+        cbits += cb->len_of[sym];
         acc = (acc << cb->len_of[sym]) | cb->code_of[sym];
         nacc += cb->len_of[sym];
         while (nacc >= 32) {
@@ -739,6 +755,7 @@ static int parse(const uint8_t* c, size_t nbytes, parsed* P) {
   p->levels = c[8];
   p->eb_mode = c[9];
   p->max_code_len = c[10];
+  p->nsub = c[11];
   p->radius = (int)get32(c + 12);
   for (int a = 0; a < 3; a++) p->brick[a] = (int)get32(c + 16 + 4 * a);
   P->info.nstreams = (int)get32(c + 28);
@@ -777,7 +794,7 @@ static int parse(const uint8_t* c, size_t nbytes, parsed* P) {
     if (P->nout[s] > P->nsym[s]) return ORA_ERR_CORRUPT;
     if (P->pw[s] > P->nsym[s] * 24 + P->nch[s]) return ORA_ERR_CORRUPT;
     if (P->sect_off[s] % 8 != 0 || P->sect_off[s] > total) return ORA_ERR_CORRUPT;
-    sect_of(P->nlive[s], P->nch[s], P->pw[s], P->nout[s], P->ps, &P->sl[s]);
+    sect_of(P->nlive[s], P->nch[s], P->pw[s], P->nout[s], P->ps, p->nsub, &P->sl[s]);
     if (P->sl[s].size > total - P->sect_off[s]) return ORA_ERR_CORRUPT;
   }
   return ORA_OK;
@@ -835,7 +852,14 @@ static int decode_stream(const uint8_t* c, const parsed* P, int s, uint16_t* dst
                                              : P->pw[s];
     if (w0 > w1 || w1 > P->pw[s]) return ORA_ERR_CORRUPT;
     uint64_t bit = 0, nbits = (w1 - w0) * 32;
-    for (int64_t k = 0; k < count; k++) {
+    const int nsub = P->info.p.nsub;
+    const int64_t q = (count + nsub - 1) / nsub;
+    for (int64_t k = 0; k <= count; k++) {
+      for (int u = 1; u < nsub; u++)
+        if ((u * q < count ? u * q : count) == k &&
+            get16(sec + sl->off_subs + 2 * ((size_t)j * (nsub - 1) + (u - 1))) != bit)
+          return ORA_ERR_CORRUPT;
+      if (k == count) break;
       uint32_t code = 0;
       int l = 0, found = 0;
       while (!found) {

@@ -77,6 +77,7 @@ typedef struct {
   int radius;         /* quantization radius R, 2..32768 */
   int max_code_len;   /* Huffman length limit, 1..24 */
   int brick[3];       /* chunk brick (bz, by, bx) in sub-block cells */
+  int nsub;           /* sub-chunks per chunk: 1, 2, 4 or 8 */
 } ora_params;
 
 /* Upper bound on the container size for the given parameters. */

@@ -52,7 +52,7 @@ static int64_t vol(const int64_t e[3]) { return e[0] * e[1] * e[2]; }
 // Workspace plan; offsets in bytes from the workspace base.
 struct WsPlan {
   size_t dp, grid[kMaxLevels + 1], codes, hist, chunk_out, chunk_words, word_off, out_off, enc,
-      books, lay, lut, total;
+      books, lay, lut, scan_sums, total;
 };
 
 static WsPlan plan_compress(const Geo& g) {
@@ -88,6 +88,8 @@ static WsPlan plan_compress(const Geo& g) {
   o += al256(sizeof(LayoutDev));
   w.lut = o;
   o += al256(4 * (size_t)g.nstreams * kLutSize);
+  w.scan_sums = o;
+  o += al256(16 * (size_t)(cdiv(g.total_chunks, 4096) + 1));
   w.total = o;
   return w;
 }
@@ -119,7 +121,8 @@ static size_t bound_of(const Geo& g) {
     size_t nsym = (size_t)sg.nsym, nch = (size_t)sg.nchunks;
     size_t nlive = nsym < (size_t)kAlphabet ? nsym : (size_t)kAlphabet;
     size_t pw = (nsym * kMaxCodeLen + 31) / 32 + nch;
-    size_t sect = ((3 * nlive + 3) & ~(size_t)3) + 4 * nch + 4 * pw + 4 * nsym;
+    size_t sect = ((((3 * nlive + 3) & ~(size_t)3) + 4 * nch + 2 * nch * (kNSub - 1) + 3) &
+                   ~(size_t)3) + 4 * pw + 4 * nsym;
     sect = ((sect + 7) & ~(size_t)7) + ps * nsym;
     total += (sect + 7) & ~(size_t)7;
   }
@@ -128,7 +131,7 @@ static size_t bound_of(const Geo& g) {
 
 // ------------------------------------------------------------ header parsing
 struct Hdr {
-  int dtype, ndim, L, eb_mode, maxlen, R, ns;
+  int dtype, ndim, L, eb_mode, maxlen, R, ns, nsub;
   int b[3];
   int64_t n[3];
   double eb, eb_abs, two_eb[kMaxLevels + 1];
@@ -151,14 +154,16 @@ static double rdf64(const uint8_t* p) {
 }
 
 struct SectHost {
-  uint64_t off_syms, off_lens, off_chunks, off_payload, off_opos, off_oval, size;
+  uint64_t off_syms, off_lens, off_chunks, off_subs, off_payload, off_opos, off_oval, size;
 };
-static SectHost sect_host(uint64_t nlive, uint64_t nch, uint64_t pw, uint64_t nout, uint64_t ps) {
+static SectHost sect_host(uint64_t nlive, uint64_t nch, uint64_t pw, uint64_t nout, uint64_t ps,
+                          int nsub) {
   SectHost s;
   s.off_syms = 0;
   s.off_lens = 2 * nlive;
   s.off_chunks = (3 * nlive + 3) & ~3ull;
-  s.off_payload = s.off_chunks + 4 * nch;
+  s.off_subs = s.off_chunks + 4 * nch;
+  s.off_payload = (s.off_subs + 2 * nch * (uint64_t)(nsub - 1) + 3) & ~3ull;
   s.off_opos = s.off_payload + 4 * pw;
   s.off_oval = (s.off_opos + 4 * nout + 7) & ~7ull;
   s.size = (s.off_oval + ps * nout + 7) & ~7ull;
@@ -178,6 +183,7 @@ static int parse_hdr(const uint8_t* h, size_t avail, size_t comp_bytes, Hdr* H) 
   H->L = h[8];
   H->eb_mode = h[9];
   H->maxlen = h[10];
+  H->nsub = h[11];
   H->R = (int)rd32(h + 12);
   for (int a = 0; a < 3; a++) H->b[a] = (int)rd32(h + 16 + 4 * a);
   H->ns = (int)rd32(h + 28);
@@ -196,7 +202,8 @@ static int parse_hdr(const uint8_t* h, size_t avail, size_t comp_bytes, Hdr* H) 
     if (H->b[a] < 1 || H->b[a] > 4096) return STZ_ERR_CORRUPT;
     if (H->n[a] < 1 || H->n[a] > ((int64_t)1 << 31)) return STZ_ERR_CORRUPT;
   }
-  if ((int64_t)H->b[0] * H->b[1] * H->b[2] > 65536) return STZ_ERR_CORRUPT;
+  if ((int64_t)H->b[0] * H->b[1] * H->b[2] * H->maxlen > 65535) return STZ_ERR_CORRUPT;
+  if (H->nsub != 1 && H->nsub != 2 && H->nsub != 4 && H->nsub != 8) return STZ_ERR_CORRUPT;
   if (H->n[0] * H->n[1] > ((int64_t)1 << 40) / H->n[2]) return STZ_ERR_CORRUPT;
   if (H->ndim == 2 && H->n[0] != 1) return STZ_ERR_CORRUPT;
   if (H->ns != 1 + 7 * (H->L - 1)) return STZ_ERR_CORRUPT;
@@ -220,7 +227,7 @@ static int parse_hdr(const uint8_t* h, size_t avail, size_t comp_bytes, Hdr* H) 
     if (e.nlive > (uint64_t)2 * H->R || (e.nsym > 0 && e.nlive == 0)) return STZ_ERR_CORRUPT;
     if (e.nout > e.nsym || e.pw > e.nsym * 24 + e.nch) return STZ_ERR_CORRUPT;
     if (e.sect_off % 8 || e.sect_off < dir_end || e.sect_off > H->total) return STZ_ERR_CORRUPT;
-    SectHost sh = sect_host(e.nlive, e.nch, e.pw, e.nout, ps);
+    SectHost sh = sect_host(e.nlive, e.nch, e.pw, e.nout, ps, H->nsub);
     if (sh.size > H->total - e.sect_off) return STZ_ERR_CORRUPT;
   }
   if (H->R != kRadius || H->maxlen > kMaxCodeLen) return STZ_ERR_ARG;
@@ -476,8 +483,8 @@ int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype
   }
   STZ_TRY(launch_codebook(g, hist, enc, books, st));
   STZ_TRY(launch_chunk_words(g, codes, enc, chunk_words, st));
-  STZ_TRY(launch_scan(chunk_words, word_off, g.total_chunks, st));
-  STZ_TRY(launch_scan(chunk_out, out_off, g.total_chunks, st));
+  STZ_TRY(launch_scan2(chunk_words, chunk_out, g.total_chunks,
+                       (unsigned long long*)(ws + w.scan_sums), word_off, out_off, st));
   STZ_TRY(launch_layout(g, dp, eb_mode, word_off, out_off, books, lay, out, out_cap, st));
   STZ_TRY(launch_sections(g, lay, books, word_off, dp, out, st));
   STZ_TRY(launch_pack(g, codes, enc, word_off, lay->s, out, dp, st));
@@ -576,7 +583,7 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
   memset(&tb, 0, sizeof(tb));
   for (int s = 0; s < H.ns; s++) {
     DecStream& d = tb.ds[s];
-    SectHost sh = sect_host(H.d[s].nlive, H.d[s].nch, H.d[s].pw, H.d[s].nout, ps);
+    SectHost sh = sect_host(H.d[s].nlive, H.d[s].nch, H.d[s].pw, H.d[s].nout, ps, H.nsub);
     d.sect = comp + H.d[s].sect_off;
     d.nlive = H.d[s].nlive;
     d.nchunks = H.d[s].nch;
@@ -584,7 +591,9 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
     d.off_syms = sh.off_syms;
     d.off_lens = sh.off_lens;
     d.off_chunks = sh.off_chunks;
+    d.off_subs = sh.off_subs;
     d.off_payload = sh.off_payload;
+    d.nsub = H.nsub;
   }
   const int ns_needed = 1 + 7 * (level - 1);
   int64_t nblocks = 0;
@@ -603,7 +612,7 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
     jb.slot_base = sm.base;
     jb.nchunks_job = c;
     jb.block0 = nblocks;
-    nblocks += cdiv(c, 128);
+    nblocks += cdiv(c * H.nsub, kDecThreads);
   }
   tb.nblocks = nblocks;
 #define STZ_TRY(x)               \
@@ -615,7 +624,7 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
   STZ_TRY(launch_lut(tb, lut, status, st));
   STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, st));
   const uint8_t* sec0 = comp + H.d[0].sect_off;
-  SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps);
+  SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps, H.nsub);
   uint8_t* g1buf = ws + P.grid[1];
   {
     BaseArgs a;
@@ -668,7 +677,8 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
       const int sid = 1 + 7 * (j - 2) + K - 1;
       a.sm[K] = P.sm[sid];
       const uint8_t* sec = comp + H.d[sid].sect_off;
-      SectHost sh = sect_host(H.d[sid].nlive, H.d[sid].nch, H.d[sid].pw, H.d[sid].nout, ps);
+      SectHost sh = sect_host(H.d[sid].nlive, H.d[sid].nch, H.d[sid].pw, H.d[sid].nout, ps,
+                              H.nsub);
       a.opos[K] = (const uint32_t*)(sec + sh.off_opos);
       a.oval[K] = sec + sh.off_oval;
       a.nout[K] = (int64_t)H.d[sid].nout;

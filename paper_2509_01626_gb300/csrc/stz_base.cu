@@ -7,11 +7,16 @@
 // 2t, from already reconstructed points.  A pass has no dependency inside
 // itself, so each is one launch with a thread per point; the level-1 grid
 // (8 MiB for a 512^3 field) stays resident in L2 across passes.
+#include <cooperative_groups.h>
+#include <string.h>
+
 #include "stz_kernels.cuh"
 #include "stz_prof.cuh"
 #include "stz_predict.cuh"
 
 namespace stz {
+
+namespace cg = cooperative_groups;
 
 struct PassGeo {
   int64_t start[3], step[3], cnt[3];
@@ -68,6 +73,174 @@ __global__ void __launch_bounds__(256) k_base_pass(BaseArgs a, PassGeo p) {
   }
 }
 
+// All passes in one cooperative launch.  The first `nsmall` passes (the coarse
+// strides, a few thousand points) run in block 0 alone with block barriers;
+// the rest are spread over the grid with a grid-wide barrier between passes.
+// Level-1 values written by other blocks are read with L2-only loads (__ldcg),
+// never through a possibly stale L1 line.
+constexpr int kMaxPasses = 64;
+struct PassList {
+  PassGeo p[kMaxPasses];
+  int npass, nsmall;
+};
+
+template <typename T>
+__device__ __forceinline__ T base_predict_cg(const T* g1, int64_t idx, int64_t st, int64_t c,
+                                             int64_t t, int64_t m) {
+  const int64_t d = t * st;
+  T vm1 = __ldcg(g1 + idx - d);
+  bool p1 = c + t < m, m3 = c - 3 * t >= 0, p3 = c + 3 * t < m;
+  if (m3 && p3)
+    return cubic_1d(__ldcg(g1 + idx - 3 * d), vm1, __ldcg(g1 + idx + d), __ldcg(g1 + idx + 3 * d));
+  if (p1) return op_mul(op_add(vm1, __ldcg(g1 + idx + d)), T(0.5));
+  if (m3) return op_add(vm1, op_mul(op_sub(vm1, __ldcg(g1 + idx - 3 * d)), T(0.5)));
+  return vm1;
+}
+
+template <typename T, bool DEC>
+__device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p, int64_t i,
+                                           const int64_t m[3], int64_t s1, const QConst<T>& q) {
+  const Geo& geo = a.geo;
+  int64_t i2 = i % p.cnt[2], r = i / p.cnt[2];
+  int64_t i1 = r % p.cnt[1], i0 = r / p.cnt[1];
+  int64_t g0 = p.start[0] + i0 * p.step[0];
+  int64_t g1 = p.start[1] + i1 * p.step[1];
+  int64_t g2 = p.start[2] + i2 * p.step[2];
+  int64_t idx = (g0 * m[1] + g1) * m[2] + g2;
+  T* grid = (T*)a.g1;
+  T pred = T(0);
+  if (!p.origin) {
+    const int64_t st = p.axis == 0 ? m[1] * m[2] : (p.axis == 1 ? m[2] : 1);
+    const int64_t c = p.axis == 0 ? g0 : (p.axis == 1 ? g1 : g2);
+    pred = base_predict_cg(grid, idx, st, c, p.t, m[p.axis]);
+  }
+  CellAddr ad = cell_addr(geo.s[0], geo.b, geo.bvol, a.sm, g0, g1, g2);
+  if (!DEC) {
+    const T* f = (const T*)a.field;
+    T x = f[((g0 * s1) * geo.n[1] + g1 * s1) * geo.n[2] + g2 * s1];
+    T xr;
+    int sym = quantize(x, pred, q, kRadius, xr);
+    __stcg(grid + idx, xr);
+    a.codes[ad.slot] = (uint16_t)sym;
+    if (sym == 0) atomicAdd(&a.chunk_outliers[geo.s[0].chunk0 + ad.chunk], 1u);
+  } else {
+    int sym = a.codes[ad.slot];
+    T v;
+    if (sym == 0) {
+      if (!find_outlier(a.opos, (const T*)a.oval, a.nout, ad.pos, v)) {
+        v = T(0);
+        atomicOr(a.status, kStatCorrupt);
+      }
+    } else {
+      v = dequantize(sym, pred, (T)a.two_eb, kRadius);
+    }
+    __stcg(grid + idx, v);
+  }
+}
+
+template <typename T, bool DEC>
+__global__ void __launch_bounds__(256) k_base_coop(const __grid_constant__ BaseArgs a,
+                                                   const __grid_constant__ PassList pl) {
+  cg::grid_group grid = cg::this_grid();
+  int64_t m[3];
+  grid_extent(a.geo.n, a.geo.L, 1, m);
+  const int64_t s1 = level_stride(a.geo.L, 1);
+  QConst<T> q;
+  if (!DEC) q.load(a.dp, 1, kRadius);
+  if (blockIdx.x == 0) {
+    for (int k = 0; k < pl.nsmall; k++) {
+      const PassGeo& p = pl.p[k];
+      for (int64_t i = threadIdx.x; i < p.total; i += blockDim.x) base_point<T, DEC>(a, p, i, m, s1, q);
+      __syncthreads();
+    }
+  }
+  for (int k = pl.nsmall; k < pl.npass; k++) {
+    grid.sync();
+    const PassGeo& p = pl.p[k];
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.total; i += nth)
+      base_point<T, DEC>(a, p, i, m, s1, q);
+  }
+}
+
+template <typename T, bool DEC>
+static int run_passes(const BaseArgs& a, cudaStream_t s);
+
+template <typename T, bool DEC>
+static int run_coop(const BaseArgs& a, cudaStream_t s) {
+  int64_t m[3];
+  grid_extent(a.geo.n, a.geo.L, 1, m);
+  int64_t mx = imax(m[0], imax(m[1], m[2]));
+  int64_t T_ = 1;
+  while (T_ < mx) T_ <<= 1;
+  PassList pl;
+  memset(&pl, 0, sizeof(pl));
+  {
+    PassGeo& p = pl.p[pl.npass++];
+    for (int b = 0; b < 3; b++) {
+      p.start[b] = 0;
+      p.step[b] = 1;
+      p.cnt[b] = 1;
+    }
+    p.total = 1;
+    p.origin = 1;
+    p.t = 1;
+  }
+  int64_t biggest = 1;
+  for (int64_t t = T_ >> 1; t >= 1; t >>= 1) {
+    for (int ax = 0; ax < 3; ax++) {
+      PassGeo p;
+      memset(&p, 0, sizeof(p));
+      p.axis = ax;
+      p.t = t;
+      p.total = 1;
+      for (int b = 0; b < 3; b++) {
+        if (b == ax) {
+          p.start[b] = t;
+          p.step[b] = 2 * t;
+          p.cnt[b] = m[b] > t ? (m[b] - t - 1) / (2 * t) + 1 : 0;
+        } else if (b < ax) {
+          p.start[b] = 0;
+          p.step[b] = t;
+          p.cnt[b] = cdiv(m[b], t);
+        } else {
+          p.start[b] = 0;
+          p.step[b] = 2 * t;
+          p.cnt[b] = cdiv(m[b], 2 * t);
+        }
+        p.total *= p.cnt[b];
+      }
+      if (p.total == 0) continue;
+      if (pl.npass >= kMaxPasses) return STZ_ERR_ARG;
+      pl.p[pl.npass++] = p;
+      biggest = imax(biggest, p.total);
+    }
+  }
+  // leading passes small enough for one block
+  pl.nsmall = 0;
+  while (pl.nsmall < pl.npass && pl.p[pl.nsmall].total <= 4096) pl.nsmall++;
+  auto kern = k_base_coop<T, DEC>;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+  if (per_sm < 1) return STZ_ERR_CUDA;
+  int64_t blocks = imin((int64_t)sms * imin(per_sm, 4), imax(1, cdiv(biggest, 256)));
+  if (pl.nsmall == pl.npass) blocks = 1;
+  void* args[] = {(void*)&a, (void*)&pl};
+  cudaError_t e;
+  {
+    ProfScope ps_(DEC ? "k_base_coop_dec" : "k_base_coop_enc", s);
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)blocks), dim3(256), args, 0,
+                                    s);
+  }
+  if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+    cudaGetLastError();  // clear, then one launch per pass
+    return run_passes<T, DEC>(a, s);
+  }
+  return cuda_ok(e);
+}
+
 template <typename T, bool DEC>
 static int run_passes(const BaseArgs& a, cudaStream_t s) {
   int64_t m[3];
@@ -122,6 +295,14 @@ static int run_passes(const BaseArgs& a, cudaStream_t s) {
 }
 
 int launch_base(const BaseArgs& a, bool decode, cudaStream_t s) {
+  if (a.geo.dtype == STZ_F32)
+    return decode ? run_coop<float, true>(a, s) : run_coop<float, false>(a, s);
+  return decode ? run_coop<double, true>(a, s) : run_coop<double, false>(a, s);
+}
+
+// One launch per pass (kept for comparison and for devices without
+// cooperative launch).
+int launch_base_passes(const BaseArgs& a, bool decode, cudaStream_t s) {
   if (a.geo.dtype == STZ_F32)
     return decode ? run_passes<float, true>(a, s) : run_passes<float, false>(a, s);
   return decode ? run_passes<double, true>(a, s) : run_passes<double, false>(a, s);

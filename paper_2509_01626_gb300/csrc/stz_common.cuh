@@ -27,6 +27,8 @@ constexpr int kLevels = 3;              // L used by stz_compress
 constexpr int kRadius = 1024;           // quantization radius R
 constexpr int kAlphabet = 2 * kRadius;  // symbols 0 (outlier) .. 2R-1
 constexpr int kMaxCodeLen = 12;         // Huffman length limit = decode table index bits
+constexpr int kNSub = 4;                // sub-chunks per chunk (independent decode chains)
+constexpr int kDecThreads = 256;        // threads per block of the chunk decoder
 constexpr int kLutSize = 1 << kMaxCodeLen;
 constexpr int kHeaderBytes = 256;
 constexpr int kDirEntryBytes = 48;
@@ -181,6 +183,20 @@ __device__ __forceinline__ int quantize(T x, T pred, const QConst<T>& q, int R, 
   }
   xr = rec;
   return qi + R;
+}
+
+// The same quantizer without branches (identical results): both tests are
+// evaluated and the outcome selected at the end.
+template <typename T>
+__device__ __forceinline__ int quantize_sel(T x, T pred, const QConst<T>& q, int R, T& xr) {
+  const T d = op_sub(x, pred);
+  const T qf = op_mul(d, q.inv2eb);
+  const bool in_range = op_abs(qf) < q.rlim;
+  const int qi = in_range ? to_int_rn(qf) : 0;
+  const T rec = op_add(pred, op_mul(from_int(qi, T()), q.two_eb));
+  const bool ok = in_range && (op_abs(op_sub(rec, x)) <= q.ebc);
+  xr = ok ? rec : x;
+  return ok ? qi + R : 0;
 }
 
 template <typename T>

@@ -47,7 +47,8 @@ __global__ void k_layout(const __grid_constant__ Geo g, const DevParams* __restr
     d.off_syms = 0;
     d.off_lens = 2 * d.nlive;
     d.off_chunks = al4(3 * d.nlive);
-    d.off_payload = d.off_chunks + 4 * nch;
+    d.off_subs = d.off_chunks + 4 * nch;
+    d.off_payload = al4(d.off_subs + 2 * nch * (kNSub - 1));
     d.off_opos = d.off_payload + 4 * d.pw;
     d.off_oval = al8(d.off_opos + 4 * d.nout);
     d.size = al8(d.off_oval + ps * d.nout);
@@ -70,6 +71,7 @@ __global__ void k_layout(const __grid_constant__ Geo g, const DevParams* __restr
   out[8] = (uint8_t)g.L;
   out[9] = (uint8_t)eb_mode;
   out[10] = (uint8_t)kMaxCodeLen;
+  out[11] = (uint8_t)kNSub;
   put_u32(out + 12, kRadius);
   for (int a = 0; a < 3; a++) put_u32(out + 16 + 4 * a, (uint32_t)g.b[a]);
   put_u32(out + 28, (uint32_t)g.nstreams);
@@ -127,6 +129,9 @@ __global__ void __launch_bounds__(256) k_sections(const __grid_constant__ Geo g,
     }
     if (threadIdx.x == 0) {
       for (unsigned long long p = d.off_lens + d.nlive; p < d.off_chunks; p++) sec[p] = 0;
+      const unsigned long long sub_end =
+          d.off_subs + 2ull * (unsigned long long)g.s[s].nchunks * (kNSub - 1);
+      for (unsigned long long p = sub_end; p < d.off_payload; p++) sec[p] = 0;
       for (unsigned long long p = d.off_opos + 4 * d.nout; p < d.off_oval; p++) sec[p] = 0;
       for (unsigned long long p = d.off_oval + ps * d.nout; p < d.size; p++) sec[p] = 0;
     }
@@ -151,8 +156,8 @@ int launch_sections(const Geo& g, const LayoutDev* lay, const BookDev* books,
   return cuda_ok(cudaGetLastError());
 }
 
-// Outlier lists: chunks holding outliers (symbol 0) list them in stream order
-// with the raw value of the field at that point.
+// Outlier lists: one warp per chunk holding outliers (symbol 0) lists them in
+// stream order (ballot compaction) with the raw value of the field there.
 template <typename T>
 __global__ void __launch_bounds__(256) k_outliers(const __grid_constant__ Geo g,
                                                   const uint16_t* __restrict__ codes,
@@ -163,8 +168,10 @@ __global__ void __launch_bounds__(256) k_outliers(const __grid_constant__ Geo g,
                                                   const DevParams* __restrict__ dp,
                                                   uint8_t* __restrict__ out) {
   if (dp->status & kStatCapacity) return;
-  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.total_chunks; j += nth) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < g.total_chunks;
+       j += nw) {
     if (chunk_outliers[j] == 0) continue;
     int sid = 0;
     for (int s = 1; s < g.nstreams; s++)
@@ -179,16 +186,21 @@ __global__ void __launch_bounds__(256) k_outliers(const __grid_constant__ Geo g,
     const int64_t s = level_stride(g.L, sg.level);
     unsigned long long k = out_off[j] - d.out0;
     const uint16_t* c = codes + j * g.bvol;
-    for (int64_t i = 0; i < cnt; i++) {
-      if (c[i] != 0) continue;
-      const int64_t lz = i / (l[1] * l[2]), ly = (i / l[2]) % l[1], lx = i % l[2];
-      int64_t p[3] = {B[0] * g.b[0] + lz, B[1] * g.b[1] + ly, B[2] * g.b[2] + lx};
-      if (sg.level > 1)
-        for (int a = 0; a < 3; a++) p[a] = 2 * p[a] + sg.o[a];
-      const int64_t f = ((p[0] * s) * g.n[1] + p[1] * s) * g.n[2] + p[2] * s;
-      opos[k] = (uint32_t)(start + i);
-      oval[k] = field[f];
-      k++;
+    for (int64_t i0 = 0; i0 < cnt; i0 += 32) {
+      const int64_t i = i0 + lane;
+      const bool hit = i < cnt && c[i] == 0;
+      const unsigned bm = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const int64_t lz = i / (l[1] * l[2]), ly = (i / l[2]) % l[1], lx = i % l[2];
+        int64_t p[3] = {B[0] * g.b[0] + lz, B[1] * g.b[1] + ly, B[2] * g.b[2] + lx};
+        if (sg.level > 1)
+          for (int a = 0; a < 3; a++) p[a] = 2 * p[a] + sg.o[a];
+        const int64_t f = ((p[0] * s) * g.n[1] + p[1] * s) * g.n[2] + p[2] * s;
+        const unsigned long long kk = k + __popc(bm & ((1u << lane) - 1u));
+        opos[kk] = (uint32_t)(start + i);
+        oval[kk] = field[f];
+      }
+      k += __popc(bm);
     }
   }
 }
@@ -196,7 +208,7 @@ __global__ void __launch_bounds__(256) k_outliers(const __grid_constant__ Geo g,
 int launch_outliers(const Geo& g, const uint16_t* codes, const void* field,
                     const uint32_t* chunk_outliers, const unsigned long long* out_off,
                     const LayoutDev* lay, const DevParams* dp, uint8_t* out, cudaStream_t s) {
-  int64_t blocks = imax(1, imin(cdiv(g.total_chunks, 256), 1024));
+  int64_t blocks = imax(1, imin(cdiv(g.total_chunks * 32, 256), 2048));
   ProfScope ps_("k_outliers", s);
   if (g.dtype == STZ_F32)
     k_outliers<float><<<(unsigned)blocks, 256, 0, s>>>(g, codes, (const float*)field,

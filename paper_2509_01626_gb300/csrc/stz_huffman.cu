@@ -244,33 +244,131 @@ int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc,
 }
 
 // ---------------------------------------------------------------- scan
-__global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ in,
-                                               unsigned long long* __restrict__ out, int64_t n) {
-  __shared__ unsigned long long part[1024];
-  const int tid = threadIdx.x;
-  const int64_t per = (n + blockDim.x - 1) / blockDim.x;
-  const int64_t lo = imin(n, tid * per), hi = imin(n, lo + per);
-  unsigned long long sum = 0;
-  for (int64_t i = lo; i < hi; i++) sum += in[i];
-  part[tid] = sum;
+// Exclusive prefix sums of two u32 arrays (chunk payload words, chunk outlier
+// counts) into u64 offsets, in two launches over tiles of 4096: per-tile sums,
+// then per-tile scans offset by the sum of the earlier tiles.
+constexpr int kScanThreads = 1024, kScanTile = 4096;
+
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v,
+                                                              unsigned long long* wsum,
+                                                              unsigned long long* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
   __syncthreads();
-  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-    unsigned long long v = tid >= off ? part[tid - off] : 0ull;
-    __syncthreads();
-    part[tid] += v;
-    __syncthreads();
+  if (w == 0) {
+    unsigned long long t = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    wsum[lane] = t;
   }
-  unsigned long long run = part[tid] - sum;
-  for (int64_t i = lo; i < hi; i++) {
-    out[i] = run;
-    run += in[i];
-  }
-  if (tid == (int)blockDim.x - 1) out[n] = part[tid];
+  __syncthreads();
+  *total = wsum[31];
+  return x - v + (w > 0 ? wsum[w - 1] : 0ull);
 }
 
-int launch_scan(const uint32_t* in, unsigned long long* out, int64_t n, cudaStream_t s) {
-  ProfScope ps_("k_scan", s);
-  k_scan<<<1, 1024, 0, s>>>(in, out, n);
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t* __restrict__ a,
+                                                             const uint32_t* __restrict__ b,
+                                                             int64_t n,
+                                                             unsigned long long* __restrict__ sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  unsigned long long sa = 0, sb = 0;
+  for (int k = 0; k < kScanTile / kScanThreads; k++) {
+    const int64_t i = base + k * kScanThreads + threadIdx.x;
+    if (i < n) {
+      sa += a[i];
+      sb += b[i];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  __shared__ unsigned long long ra[32], rb[32];
+  if ((threadIdx.x & 31) == 0) {
+    ra[threadIdx.x >> 5] = sa;
+    rb[threadIdx.x >> 5] = sb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long ta = 0, tb = 0;
+    for (int w = 0; w < kScanThreads / 32; w++) {
+      ta += ra[w];
+      tb += rb[w];
+    }
+    sums[2 * blockIdx.x] = ta;
+    sums[2 * blockIdx.x + 1] = tb;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(
+    const uint32_t* __restrict__ a, const uint32_t* __restrict__ b, int64_t n,
+    const unsigned long long* __restrict__ sums, unsigned long long* __restrict__ oa,
+    unsigned long long* __restrict__ ob) {
+  __shared__ uint32_t ta[kScanTile], tbuf[kScanTile];
+  __shared__ unsigned long long wsum[32];
+  __shared__ unsigned long long pre[2];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  if (threadIdx.x < 32) {
+    unsigned long long pa = 0, pb = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += 32) {
+      pa += sums[2 * t];
+      pb += sums[2 * t + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      pa += __shfl_xor_sync(0xffffffffu, pa, o);
+      pb += __shfl_xor_sync(0xffffffffu, pb, o);
+    }
+    if (threadIdx.x == 0) {
+      pre[0] = pa;
+      pre[1] = pb;
+    }
+  }
+  for (int k = 0; k < kScanTile / kScanThreads; k++) {
+    const int j = k * kScanThreads + threadIdx.x;
+    const int64_t i = base + j;
+    ta[j] = i < n ? a[i] : 0u;
+    tbuf[j] = i < n ? b[i] : 0u;
+  }
+  __syncthreads();
+  constexpr int per = kScanTile / kScanThreads;
+  for (int arr = 0; arr < 2; arr++) {
+    const uint32_t* t = arr == 0 ? ta : tbuf;
+    unsigned long long* o = arr == 0 ? oa : ob;
+    unsigned long long loc[per];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int k = 0; k < per; k++) {
+      loc[k] = sum;
+      sum += t[threadIdx.x * per + k];
+    }
+    unsigned long long total;
+    const unsigned long long off = block_excl_scan(sum, wsum, &total) + pre[arr];
+#pragma unroll
+    for (int k = 0; k < per; k++) {
+      const int64_t i = base + threadIdx.x * per + k;
+      if (i < n) o[i] = off + loc[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) o[n] = pre[arr] + total;
+    __syncthreads();
+  }
+}
+
+int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* sums,
+                 unsigned long long* oa, unsigned long long* ob, cudaStream_t s) {
+  const int64_t nb = imax(1, cdiv(n, kScanTile));
+  {
+    ProfScope ps_("k_scan_tiles", s);
+    k_scan_tiles<<<(unsigned)nb, kScanThreads, 0, s>>>(a, b, n, sums);
+  }
+  ProfScope ps_("k_scan_apply", s);
+  k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(a, b, n, sums, oa, ob);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -295,6 +393,9 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(
   __syncwarp();
   const uint16_t* c = codes + j * g.bvol;
   const uint16_t* e = enc + (int64_t)sid * kAlphabet;
+  const SectDev& sd = sect[sid];
+  const int64_t q = (cnt + kNSub - 1) / kNSub;
+  uint16_t* so = (uint16_t*)(out + sd.sect_off + sd.off_subs) + (j - g.s[sid].chunk0) * (kNSub - 1);
   uint32_t base = 0;
   for (int64_t i0 = 0; i0 < cnt; i0 += 32) {
     const int64_t i = i0 + lane;
@@ -310,6 +411,9 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(
       if (lane >= off) incl += t;
     }
     const uint32_t p = base + incl - len;
+#pragma unroll
+    for (int u = 1; u < kNSub; u++)
+      if (i == u * q && i < cnt) so[u - 1] = (uint16_t)p;
     if (len) {
       const uint32_t wi = p >> 5, r = p & 31u;
       if (r + len <= 32u) {
@@ -321,8 +425,10 @@ __global__ void __launch_bounds__(kPackWarps * 32) k_pack(
     }
     base += __shfl_sync(0xffffffffu, incl, 31);
   }
+  if (lane == 0)
+    for (int u = 1; u < kNSub; u++)
+      if (u * q >= cnt) so[u - 1] = (uint16_t)base;
   __syncwarp();
-  const SectDev& sd = sect[sid];
   uint32_t* dst = (uint32_t*)(out + sd.sect_off + sd.off_payload) + (word_off[j] - sd.word0);
   for (int64_t i = lane; i < nw; i += 32) dst[i] = buf[i];
 }
@@ -408,8 +514,10 @@ int launch_lut(const DecTables& tb, uint32_t* lut, uint32_t* status, cudaStream_
 }
 
 // ---------------------------------------------------------------- chunk decode
-constexpr int kDecThreads = 128;
-
+// One thread per sub-chunk: a chunk of n symbols is cut into nsub runs of
+// q = ceil(n / nsub) symbols whose start bits are stored, so every run decodes
+// independently.  A run that does not end exactly where the next one starts,
+// reads past its chunk, or meets an invalid code marks the container corrupt.
 __global__ void __launch_bounds__(kDecThreads) k_decode_chunks(
     const __grid_constant__ Geo g, const __grid_constant__ DecTables tb,
     const uint32_t* __restrict__ lut, uint16_t* __restrict__ codes,
@@ -423,7 +531,11 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_chunks(
   const uint32_t* src = lut + (int64_t)sid * kLutSize;
   for (int i = threadIdx.x; i < kLutSize; i += blockDim.x) t[i] = src[i];
   __syncthreads();
-  const int64_t q = ((int64_t)blockIdx.x - job.block0) * kDecThreads + threadIdx.x;
+  const DecStream& d = tb.ds[sid];
+  const int nsub = d.nsub;
+  const int64_t qq = ((int64_t)blockIdx.x - job.block0) * kDecThreads + threadIdx.x;
+  const int64_t q = qq / nsub;
+  const int u = (int)(qq - q * nsub);
   if (q >= job.nchunks_job) return;
   const StreamGeo& sg = g.s[sid];
   const int64_t B0 = job.lo[0] + q / (job.cnt[1] * job.cnt[2]);
@@ -432,28 +544,40 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_chunks(
   const int64_t jl = (B0 * sg.nb[1] + B1) * sg.nb[2] + B2;
   const int64_t cnt = imin(g.b[0], sg.e[0] - B0 * g.b[0]) * imin(g.b[1], sg.e[1] - B1 * g.b[1]) *
                       imin(g.b[2], sg.e[2] - B2 * g.b[2]);
-  const DecStream& d = tb.ds[sid];
+  const int64_t per = (cnt + nsub - 1) / nsub;
+  const int64_t i0 = imin(cnt, (int64_t)u * per), i1 = imin(cnt, (int64_t)(u + 1) * per);
   const uint32_t* coff = (const uint32_t*)(d.sect + d.off_chunks);
+  const uint16_t* soff = (const uint16_t*)(d.sect + d.off_subs) + jl * (nsub - 1);
   const uint32_t* pay = (const uint32_t*)(d.sect + d.off_payload);
-  uint64_t w0 = coff[jl];
-  uint64_t w1 = jl + 1 < (int64_t)d.nchunks ? coff[jl + 1] : d.pw;
+  const uint64_t w0 = coff[jl];
+  const uint64_t w1 = jl + 1 < (int64_t)d.nchunks ? coff[jl + 1] : d.pw;
   uint16_t* out = codes + (job.slot_base + q) * g.bvol;
-  if (w0 > w1 || w1 > d.pw) {
+  const uint64_t cbits = w1 >= w0 ? (w1 - w0) * 32 : 0;
+  const uint64_t b0 = u == 0 ? 0 : soff[u - 1];
+  const uint64_t b1 = u + 1 < nsub ? soff[u] : cbits;
+  if (w0 > w1 || w1 > d.pw || b0 > b1 || b1 > cbits) {
     atomicOr(status, kStatCorrupt);
-    for (int64_t i = 0; i < cnt; i++) out[i] = 0;
+    for (int64_t i = i0; i < i1; i++) out[i] = 0;
     return;
   }
-  const uint32_t* wp = pay + w0;
+  const uint32_t* wp = pay + w0 + (b0 >> 5);
   const uint32_t* we = pay + w1;
   unsigned long long buf = 0;
   int nb = 0;
-  int64_t loaded = 0;
+  uint64_t consumed = 0;
+  {
+    const int sh = (int)(b0 & 31);
+    uint32_t word = wp < we ? *wp : 0u;
+    wp++;
+    buf = (unsigned long long)word << (32 + sh);
+    nb = 32 - sh;
+  }
   bool badcode = false;
-  for (int64_t i = 0; i < cnt; i++) {
+  // decode one symbol: refill below 32 buffered bits, look up the next 12
+  auto next = [&]() -> uint32_t {
     if (nb < 32) {
       uint32_t word = wp < we ? *wp : 0u;
       wp++;
-      loaded++;
       buf |= (unsigned long long)word << (32 - nb);
       nb += 32;
     }
@@ -463,11 +587,28 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_chunks(
       badcode = true;
       L = 1;
     }
-    out[i] = (uint16_t)(ent >> 8);
     buf <<= L;
     nb -= L;
+    consumed += (uint64_t)L;
+    return ent >> 8;
+  };
+  int64_t i = i0;
+  // 8 symbols per 16-byte store where the run start is 16-byte aligned
+  if ((((uintptr_t)(out + i)) & 15) == 0) {
+    for (; i + 8 <= i1; i += 8) {
+      uint32_t v[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const uint32_t lo = next();
+        const uint32_t hi = next();
+        v[k] = lo | (hi << 16);
+      }
+      *(uint4*)(out + i) = make_uint4(v[0], v[1], v[2], v[3]);
+    }
   }
-  if (badcode || (uint64_t)(loaded * 32 - nb) > (w1 - w0) * 32) atomicOr(status, kStatCorrupt);
+  for (; i < i1; i++) out[i] = (uint16_t)next();
+  const bool exact = u + 1 < nsub ? (b0 + consumed == b1) : (b0 + consumed <= b1);
+  if (badcode || !exact) atomicOr(status, kStatCorrupt);
 }
 
 int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,

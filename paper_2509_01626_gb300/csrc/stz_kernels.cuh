@@ -28,6 +28,7 @@ struct BaseArgs {
   uint32_t* status;           // decode: corrupt flag
 };
 int launch_base(const BaseArgs& a, bool decode, cudaStream_t s);
+int launch_base_passes(const BaseArgs& a, bool decode, cudaStream_t s);
 
 // ---- stz_level.cu: levels 2..L (multi-dimensional cubic prediction) ----
 struct LevelArgs {
@@ -67,8 +68,10 @@ int launch_codebook(const Geo& g, const uint32_t* hist, uint16_t* enc, BookDev* 
 // bits per chunk -> words per chunk
 int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc,
                        uint32_t* chunk_words, cudaStream_t s);
-// exclusive scan of n u32 into n+1 u64 (single block)
-int launch_scan(const uint32_t* in, unsigned long long* out, int64_t n, cudaStream_t s);
+// exclusive scans of two n-entry u32 arrays into (n+1)-entry u64 arrays;
+// sums: 2 * ceil(n / 4096) scratch entries
+int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* sums,
+                 unsigned long long* oa, unsigned long long* ob, cudaStream_t s);
 // pack every chunk's codes into the container payload
 struct SectDev;  // stz_container.cu
 int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
@@ -79,7 +82,8 @@ int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
 struct DecStream {
   const uint8_t* sect;        // section start in the container
   uint64_t nlive, nchunks, pw;
-  uint64_t off_syms, off_lens, off_chunks, off_payload;
+  uint64_t off_syms, off_lens, off_chunks, off_subs, off_payload;
+  int nsub;
 };
 // entropy-decode the chunks of bricks [lo, lo+cnt) of each stream into slots
 struct DecChunkJob {
@@ -103,8 +107,8 @@ int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,
 
 // ---- stz_container.cu: layout, header, sections, outliers ----
 struct SectDev {
-  unsigned long long sect_off, off_syms, off_lens, off_chunks, off_payload, off_opos, off_oval,
-      size;
+  unsigned long long sect_off, off_syms, off_lens, off_chunks, off_subs, off_payload, off_opos,
+      off_oval, size;
   unsigned long long pw, nout, nlive, word0, out0;
 };
 struct LayoutDev {

@@ -17,6 +17,7 @@
 #include "stz_predict.cuh"
 
 #include <stdio.h>
+#include <string.h>
 
 namespace stz {
 
@@ -213,8 +214,467 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const __grid_constant__
   }
 }
 
+// ---------------------------------------------------------------- fast path
+// Interior cells of 3D fields with the 8 x 16 x 16 brick.  Thread (ly, lx)
+// walks the 8 cells of its column along z and keeps the coarse values it
+// needs in a register window of 4 planes (dz = -1, 0, 1, 2) x 12 points,
+// loading one new plane of 12 values per cell.  Pattern of (dy, dx) offsets:
+//   0 (0,-1)  1 (0,0)  2 (0,1)  3 (0,2)  4 (-1,0)  5 (1,0)  6 (2,0)  7 (1,1)
+//   8 (-1,-1) 9 (-1,2) 10 (2,-1) 11 (2,2)
+// which covers every tap of Eqs. 6-8 for the 7 sub-blocks of a cell.  Only
+// cells with 1 <= c <= M-3 on every axis are handled here (all stencils cubic,
+// all points present); the others belong to the shell kernel below.
+constexpr int kFBZ = 8, kFBY = 16, kFBX = 16;
+constexpr int kFEY = kFBY + 3, kFEX = kFBX + 3, kFEZY = kFEY * kFEX;
+
+template <typename T>
+__device__ __forceinline__ void load_plane(T (&w)[12], const T* __restrict__ t, int b) {
+  w[0] = t[b - 1];
+  w[1] = t[b];
+  w[2] = t[b + 1];
+  w[3] = t[b + 2];
+  w[4] = t[b - kFEX];
+  w[5] = t[b + kFEX];
+  w[6] = t[b + 2 * kFEX];
+  w[7] = t[b + kFEX + 1];
+  w[8] = t[b - kFEX - 1];
+  w[9] = t[b - kFEX + 2];
+  w[10] = t[b + 2 * kFEX - 1];
+  w[11] = t[b + 2 * kFEX + 2];
+}
+
+// the 7 interior predictions of a cell (index K-1), with the operand order of
+// level_predict's cubic branch
+template <typename T>
+__device__ __forceinline__ void cell_predict(const T (&w0)[12], const T (&w1)[12],
+                                             const T (&w2)[12], const T (&w3)[12], T (&p)[7]) {
+  p[0] = cubic_1d(w1[0], w1[1], w1[2], w1[3]);  // K=1 (x)
+  p[1] = cubic_1d(w1[4], w1[1], w1[5], w1[6]);  // K=2 (y)
+  {                                             // K=3 (y, x)
+    T si = op_add(op_add(w1[1], w1[2]), op_add(w1[5], w1[7]));
+    T so = op_add(op_add(w1[8], w1[9]), op_add(w1[10], w1[11]));
+    p[2] = op_add(op_mul(si, T(0.25)), op_mul(op_sub(si, so), T(0.03125)));
+  }
+  p[3] = cubic_1d(w0[1], w1[1], w2[1], w3[1]);  // K=4 (z)
+  {                                             // K=5 (z, x)
+    T si = op_add(op_add(w1[1], w1[2]), op_add(w2[1], w2[2]));
+    T so = op_add(op_add(w0[0], w0[3]), op_add(w3[0], w3[3]));
+    p[4] = op_add(op_mul(si, T(0.25)), op_mul(op_sub(si, so), T(0.03125)));
+  }
+  {                                             // K=6 (z, y)
+    T si = op_add(op_add(w1[1], w1[5]), op_add(w2[1], w2[5]));
+    T so = op_add(op_add(w0[4], w0[6]), op_add(w3[4], w3[6]));
+    p[5] = op_add(op_mul(si, T(0.25)), op_mul(op_sub(si, so), T(0.03125)));
+  }
+  {                                             // K=7 (z, y, x)
+    T si = op_add(op_add(op_add(w1[1], w1[2]), op_add(w1[5], w1[7])),
+                  op_add(op_add(w2[1], w2[2]), op_add(w2[5], w2[7])));
+    T so = op_add(op_add(op_add(w0[8], w0[9]), op_add(w0[10], w0[11])),
+                  op_add(op_add(w3[8], w3[9]), op_add(w3[10], w3[11])));
+    p[6] = op_add(op_mul(si, T(0.125)), op_mul(op_sub(si, so), T(0.015625)));
+  }
+}
+
+// ---- asynchronous copies into shared memory (cp.async, zero fill) ----
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? BYTES : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES),
+               "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Per-tile stream information, computed by threads 0..6 (one per sub-block).
+struct TileInfo {
+  int64_t slot[8], pos[8], chunk[8];
+  int l[8][3];
+  int c0[3];
+  int full;
+};
+
+__device__ __forceinline__ void tile_info(const LevelArgs& a, int64_t tt, TileInfo& ti) {
+  const Geo& geo = a.geo;
+  const int l = a.level;
+  const int64_t Tb[3] = {a.tlo[0] + tt / (a.tcnt[1] * a.tcnt[2]),
+                         a.tlo[1] + (tt / a.tcnt[2]) % a.tcnt[1], a.tlo[2] + tt % a.tcnt[2]};
+  const int c0[3] = {(int)Tb[0] * kFBZ, (int)Tb[1] * kFBY, (int)Tb[2] * kFBX};
+  const int tid = threadIdx.x;
+  if (tid < 3) ti.c0[tid] = c0[tid];
+  if (tid < 7) {
+    const int K = tid + 1;
+    const StreamGeo& sg = geo.s[1 + 7 * (l - 2) + (K - 1)];
+    const SlotMap& sm = a.sm[K];
+    if (Tb[0] < sg.nb[0] && Tb[1] < sg.nb[1] && Tb[2] < sg.nb[2]) {
+      const int64_t l0 = imin(kFBZ, sg.e[0] - c0[0]), l1 = imin(kFBY, sg.e[1] - c0[1]),
+                    l2 = imin(kFBX, sg.e[2] - c0[2]);
+      ti.l[K][0] = (int)l0;
+      ti.l[K][1] = (int)l1;
+      ti.l[K][2] = (int)l2;
+      ti.chunk[K] = sg.chunk0 + (Tb[0] * sg.nb[1] + Tb[1]) * sg.nb[2] + Tb[2];
+      ti.pos[K] = (int64_t)c0[0] * sg.e[1] * sg.e[2] + c0[1] * l0 * sg.e[2] + c0[2] * l0 * l1;
+      const int64_t ord =
+          ((Tb[0] - sm.lo[0]) * sm.cnt[1] + (Tb[1] - sm.lo[1])) * sm.cnt[2] + (Tb[2] - sm.lo[2]);
+      ti.slot[K] = (sm.base + ord) * geo.bvol;
+    } else {
+      ti.l[K][0] = ti.l[K][1] = ti.l[K][2] = 0;
+      ti.chunk[K] = ti.pos[K] = ti.slot[K] = 0;
+    }
+  }
+}
+
+// Issue the copies of tile tt's coarse grid (with halo) into `tile`.
+template <typename T>
+__device__ __forceinline__ void tile_prefetch(const LevelArgs& a, int64_t tt, T* tile) {
+  const int64_t Tb[3] = {a.tlo[0] + tt / (a.tcnt[1] * a.tcnt[2]),
+                         a.tlo[1] + (tt / a.tcnt[2]) % a.tcnt[1], a.tlo[2] + tt % a.tcnt[2]};
+  const int c0[3] = {(int)Tb[0] * kFBZ - 1, (int)Tb[1] * kFBY - 1, (int)Tb[2] * kFBX - 1};
+  const T* coarse = (const T*)a.coarse;
+  const int clo0 = (int)a.clo[0], clo1 = (int)a.clo[1], clo2 = (int)a.clo[2];
+  const int chi0 = (int)a.chi[0], chi1 = (int)a.chi[1], chi2 = (int)a.chi[2];
+  const int64_t ce1 = a.chi[1] - a.clo[1], ce2 = a.chi[2] - a.clo[2];
+  constexpr int tvol = (kFBZ + 3) * kFEZY;
+  for (int i = threadIdx.x; i < tvol; i += blockDim.x) {
+    const int iz = i / kFEZY, iy = (i / kFEX) % kFEY, ix = i % kFEX;
+    const int cz = c0[0] + iz, cy = c0[1] + iy, cx = c0[2] + ix;
+    const bool in = cz >= clo0 && cz < chi0 && cy >= clo1 && cy < chi1 && cx >= clo2 && cx < chi2;
+    const T* src = in ? coarse + ((int64_t)(cz - clo0) * ce1 + (cy - clo1)) * ce2 + (cx - clo2)
+                      : coarse;
+    cp_async<sizeof(T)>(tile + i, src, in);
+  }
+  cp_async_commit();
+}
+
+// One tile of the fast path.  FULL: all 7 sub-block bricks of the tile are
+// whole, so a cell has the same local code index lz*256 + tid in every stream.
+// The 7 global loads of a cell (x when compressing, codes when decoding) are
+// issued one cell ahead of their use.
+template <typename T, bool DEC, bool FULL>
+__device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restrict__ tile,
+                                          const TileInfo& ti, const int M[3], const QConst<T>& q,
+                                          T two_eb, uint32_t* hist, int xdz, int xdy, int xdx,
+                                          int fe2, int fdz) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ly = tid >> 4, lx = tid & 15;
+  const int c0z = ti.c0[0], cy = ti.c0[1] + ly, cx = ti.c0[2] + lx;
+  const bool in_yx = (unsigned)(cy - 1) <= (unsigned)(M[1] - 4) &&
+                     (unsigned)(cx - 1) <= (unsigned)(M[2] - 4);
+  const int flo0 = (int)a.flo[0], flo1 = (int)a.flo[1], flo2 = (int)a.flo[2];
+  const int fhi0 = (int)a.fhi[0], fhi1 = (int)a.fhi[1], fhi2 = (int)a.fhi[2];
+  const bool fy0 = 2 * cy >= flo1 && 2 * cy < fhi1, fy1 = 2 * cy + 1 >= flo1 && 2 * cy + 1 < fhi1;
+  const bool fx0 = 2 * cx >= flo2 && 2 * cx < fhi2, fx1 = 2 * cx + 1 >= flo2 && 2 * cx + 1 < fhi2;
+  const int tb = (kFEY + ly + 1) * kFEX + (lx + 1);
+  uint16_t* cp[7];
+  int cstep[7];
+#pragma unroll
+  for (int K = 1; K <= 7; K++) {
+    const int l1 = FULL ? kFBY : ti.l[K][1], l2 = FULL ? kFBX : ti.l[K][2];
+    cp[K - 1] = a.codes + ti.slot[K] + (FULL ? tid : ly * l2 + lx);
+    cstep[K - 1] = l1 * l2;
+  }
+  const T* xp = DEC ? nullptr
+                    : (const T*)a.field + (int64_t)(2 * c0z) * xdz + (int64_t)(2 * cy) * xdy +
+                          (int64_t)(2 * cx) * xdx;
+  T* fp = a.fine ? (T*)a.fine + ((int64_t)(2 * c0z - flo0) * (fhi1 - flo1) + (2 * cy - flo1)) *
+                                    (int64_t)fe2 +
+                       (2 * cx - flo2)
+                 : nullptr;
+  // cell lz is "on" for sub-block K if interior (and its point inside the box)
+  auto cell_on = [&](int lz, int K) -> bool {
+    const int cz = c0z + lz;
+    const bool interior = in_yx && (unsigned)(cz - 1) <= (unsigned)(M[0] - 4);
+    if (!DEC) return interior;
+    const int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
+    const int gz = 2 * cz + oz;
+    return interior && gz >= flo0 && gz < fhi0 && (oy ? fy1 : fy0) && (ox ? fx1 : fx0);
+  };
+  // loads of cell 0
+  T xv[7];
+  int cv[7];
+#pragma unroll
+  for (int K = 1; K <= 7; K++) {
+    const int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
+    const bool on = cell_on(0, K);
+    if (!DEC) xv[K - 1] = on ? xp[oz * xdz + oy * xdy + ox * xdx] : T(0);
+    else cv[K - 1] = on ? (int)*cp[K - 1] : 1;
+  }
+  T w0[12], w1[12], w2[12], w3[12];
+  load_plane(w0, tile, tb - kFEZY);
+  load_plane(w1, tile, tb);
+  load_plane(w2, tile, tb + kFEZY);
+#pragma unroll 1
+  for (int lz = 0; lz < kFBZ; lz++) {
+    load_plane(w3, tile, tb + (lz + 2) * kFEZY);
+    const int cz = c0z + lz;
+    const bool interior = in_yx && (unsigned)(cz - 1) <= (unsigned)(M[0] - 4);
+    const bool fz0 = 2 * cz >= flo0 && 2 * cz < fhi0;
+    // issue the next cell's loads before this cell's arithmetic
+    T xn[7];
+    int cn[7];
+    const bool more = lz + 1 < kFBZ;
+#pragma unroll
+    for (int K = 1; K <= 7; K++) {
+      const int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
+      const bool on = more && cell_on(lz + 1, K);
+      if (!DEC) xn[K - 1] = on ? xp[2 * xdz + oz * xdz + oy * xdy + ox * xdx] : T(0);
+      else cn[K - 1] = on ? (int)*(cp[K - 1] + cstep[K - 1]) : 1;
+    }
+    T p[7];
+    cell_predict(w0, w1, w2, w3, p);
+    if (interior && fp && fz0 && fy0 && fx0) fp[0] = w1[1];  // the coarse point itself
+#pragma unroll
+    for (int K = 1; K <= 7; K++) {
+      const int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
+      const bool on = cell_on(lz, K);
+      const int fo = oz * fdz + oy * fe2 + ox;
+      if (!DEC) {
+        int sym = -1;
+        if (on) {
+          T xq;
+          sym = quantize_sel(xv[K - 1], p[K - 1], q, kRadius, xq);
+          *cp[K - 1] = (uint16_t)sym;
+          if (fp) fp[fo] = xq;
+          if (sym == 0) atomicAdd(&a.chunk_outliers[ti.chunk[K]], 1u);
+        }
+        const unsigned bm = __ballot_sync(0xffffffffu, sym == kRadius);
+        uint32_t* h = hist + (K - 1) * kHistWords;
+        if (lane == 0 && bm) atomicAdd(&h[kRadius >> 1], (uint32_t)__popc(bm));
+        if (sym >= 0 && sym != kRadius) atomicAdd(&h[sym >> 1], 1u << ((sym & 1) * 16));
+      } else if (on) {
+        const int sym = cv[K - 1];
+        T val;
+        if (sym != 0) {
+          val = dequantize(sym, p[K - 1], two_eb, kRadius);
+        } else {
+          const int64_t local = cp[K - 1] - (a.codes + ti.slot[K]);
+          if (!find_outlier(a.opos[K], (const T*)a.oval[K], a.nout[K], ti.pos[K] + local, val)) {
+            val = T(0);
+            atomicOr(a.status, kStatCorrupt);
+          }
+        }
+        fp[fo] = val;
+      }
+    }
+    if (!DEC) xp += 2 * xdz;
+    if (fp) fp += 2 * fdz;
+#pragma unroll
+    for (int K = 0; K < 7; K++) {
+      cp[K] += cstep[K];
+      if (!DEC) xv[K] = xn[K];
+      else cv[K] = cn[K];
+    }
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+      w0[j] = w1[j];
+      w1[j] = w2[j];
+      w2[j] = w3[j];
+    }
+  }
+}
+
 template <typename T, bool DEC>
-static int run_level(const LevelArgs& a, cudaStream_t s) {
+__global__ void __launch_bounds__(kLevelThreads, 2) k_level_fast(const __grid_constant__ LevelArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileInfo s_ti[2];
+  const Geo& geo = a.geo;
+  const int l = a.level;
+  int64_t M64[3];
+  grid_extent(geo.n, geo.L, l - 1, M64);
+  const int M[3] = {(int)M64[0], (int)M64[1], (int)M64[2]};
+  constexpr int tvol = (kFBZ + 3) * kFEZY;
+  constexpr size_t tbytes = ((size_t)tvol * sizeof(T) + 15) & ~(size_t)15;
+  T* tiles[2] = {(T*)smem, (T*)(smem + tbytes)};
+  uint32_t* hist = (uint32_t*)(smem + 2 * tbytes);
+  const int tid = threadIdx.x;
+  QConst<T> q;
+  if (!DEC) {
+    q.load(a.dp, l, kRadius);
+    for (int w = tid; w < 7 * kHistWords; w += blockDim.x) hist[w] = 0;
+  }
+  const T two_eb = (T)a.two_eb;
+  const int64_t ntiles = a.tcnt[0] * a.tcnt[1] * a.tcnt[2];
+  const int64_t s = level_stride(geo.L, l);
+  const int xdz = (int)(s * geo.n[1] * geo.n[2]), xdy = (int)(s * geo.n[2]), xdx = (int)s;
+  const int fe2 = (int)(a.fhi[2] - a.flo[2]);
+  const int fdz = (int)((a.fhi[1] - a.flo[1]) * fe2);
+  int since_flush = 0;
+  int64_t tt = blockIdx.x;
+  int b = 0;
+  if (tt < ntiles) {
+    tile_info(a, tt, s_ti[0]);
+    tile_prefetch(a, tt, tiles[0]);
+  }
+  for (; tt < ntiles; tt += gridDim.x, b ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t nt = tt + gridDim.x;
+    if (nt < ntiles) {
+      tile_info(a, nt, s_ti[b ^ 1]);
+      tile_prefetch(a, nt, tiles[b ^ 1]);
+    }
+    const TileInfo& ti = s_ti[b];
+    bool full = true;
+#pragma unroll
+    for (int K = 1; K <= 7; K++)
+      full = full && ti.l[K][0] == kFBZ && ti.l[K][1] == kFBY && ti.l[K][2] == kFBX;
+    if (full)
+      fast_tile<T, DEC, true>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2, fdz);
+    else
+      fast_tile<T, DEC, false>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2, fdz);
+    if (!DEC && ++since_flush == kFlushTiles) {
+      __syncthreads();
+      flush_hist<T>(hist, a.hist, l);
+      since_flush = 0;
+    }
+  }
+  cp_async_wait_all();
+  if (!DEC) {
+    __syncthreads();
+    flush_hist<T>(hist, a.hist, l);
+  }
+}
+
+// ---------------------------------------------------------------- shell
+// Cells on the field boundary (c = 0 or c >= M-2 on some axis) of the needed
+// cell range, one thread per cell, generic per-point rules read straight from
+// the coarse grid.  Enumerated as three disjoint slabs: boundary z; interior z
+// with boundary y; interior z and y with boundary x.
+struct ShellGeo {
+  int64_t lo[3], hi[3];  // needed cell range
+  int64_t bv[3][3];      // boundary values per axis
+  int nb[3];
+  int64_t ilo[3], ihi[3];  // interior range per axis (may be empty)
+  int64_t nA, nB, nC;
+};
+
+template <typename T, bool DEC>
+__global__ void __launch_bounds__(256) k_level_shell(const __grid_constant__ LevelArgs a,
+                                                     const __grid_constant__ ShellGeo sh) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* hist = (uint32_t*)smem;
+  const Geo& geo = a.geo;
+  const int l = a.level;
+  const int lane = threadIdx.x & 31;
+  QConst<T> q;
+  if (!DEC) {
+    q.load(a.dp, l, kRadius);
+    for (int w = threadIdx.x; w < 7 * kHistWords; w += blockDim.x) hist[w] = 0;
+    __syncthreads();
+  }
+  int64_t m[3];
+  grid_extent(geo.n, geo.L, l, m);
+  const T two_eb = (T)a.two_eb;
+  const T* coarse = (const T*)a.coarse;
+  const int64_t ce1 = a.chi[1] - a.clo[1], ce2 = a.chi[2] - a.clo[2];
+  const int64_t st[3] = {ce1 * ce2, ce2, 1};
+  const int64_t fe1 = a.fhi[1] - a.flo[1], fe2 = a.fhi[2] - a.flo[2];
+  const int64_t s = level_stride(geo.L, l);
+  const int64_t total = sh.nA + sh.nB + sh.nC;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = cdiv(total, nth);
+  for (int64_t it = 0; it < iters; it++) {
+    const int64_t i = it * nth + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool cv = i < total;
+    int64_t c[3] = {0, 0, 0};
+    if (cv) {
+      const int64_t nx = sh.hi[2] - sh.lo[2], ny = sh.hi[1] - sh.lo[1];
+      if (i < sh.nA) {
+        const int64_t r = i / (ny * nx);
+        c[0] = sh.bv[0][r];
+        c[1] = sh.lo[1] + (i / nx) % ny;
+        c[2] = sh.lo[2] + i % nx;
+      } else if (i < sh.nA + sh.nB) {
+        const int64_t k = i - sh.nA, nbyx = sh.nb[1] * nx;
+        c[0] = sh.ilo[0] + k / nbyx;
+        c[1] = sh.bv[1][(k / nx) % sh.nb[1]];
+        c[2] = sh.lo[2] + k % nx;
+      } else {
+        const int64_t k = i - sh.nA - sh.nB, iyn = sh.ihi[1] - sh.ilo[1];
+        c[0] = sh.ilo[0] + k / (iyn * sh.nb[2]);
+        c[1] = sh.ilo[1] + (k / sh.nb[2]) % iyn;
+        c[2] = sh.bv[2][k % sh.nb[2]];
+      }
+    }
+    const int64_t base = ((c[0] - a.clo[0]) * ce1 + (c[1] - a.clo[1])) * ce2 + (c[2] - a.clo[2]);
+    if (cv && a.fine) {
+      const int64_t g0 = 2 * c[0], g1 = 2 * c[1], g2 = 2 * c[2];
+      if (g0 >= a.flo[0] && g0 < a.fhi[0] && g1 >= a.flo[1] && g1 < a.fhi[1] && g2 >= a.flo[2] &&
+          g2 < a.fhi[2])
+        ((T*)a.fine)[((g0 - a.flo[0]) * fe1 + (g1 - a.flo[1])) * fe2 + (g2 - a.flo[2])] =
+            coarse[base];
+    }
+#pragma unroll
+    for (int K = 1; K <= 7; K++) {
+      const int o[3] = {(K >> 2) & 1, (K >> 1) & 1, K & 1};
+      const int64_t g[3] = {2 * c[0] + o[0], 2 * c[1] + o[1], 2 * c[2] + o[2]};
+      bool v = cv && g[0] < m[0] && g[1] < m[1] && g[2] < m[2];
+      const bool inbox = g[0] >= a.flo[0] && g[0] < a.fhi[0] && g[1] >= a.flo[1] &&
+                         g[1] < a.fhi[1] && g[2] >= a.flo[2] && g[2] < a.fhi[2];
+      if (DEC) v = v && inbox;
+      const int sid = 1 + 7 * (l - 2) + (K - 1);
+      int sym = -1;
+      if (v) {
+        const CellAddr ad = cell_addr(geo.s[sid], geo.b, geo.bvol, a.sm[K], c[0], c[1], c[2]);
+        const int64_t fidx = ((g[0] - a.flo[0]) * fe1 + (g[1] - a.flo[1])) * fe2 + (g[2] - a.flo[2]);
+        T pred;
+        switch (K) {
+          case 1: pred = level_predict<1>(coarse, base, st, g, m); break;
+          case 2: pred = level_predict<2>(coarse, base, st, g, m); break;
+          case 3: pred = level_predict<3>(coarse, base, st, g, m); break;
+          case 4: pred = level_predict<4>(coarse, base, st, g, m); break;
+          case 5: pred = level_predict<5>(coarse, base, st, g, m); break;
+          case 6: pred = level_predict<6>(coarse, base, st, g, m); break;
+          default: pred = level_predict<7>(coarse, base, st, g, m); break;
+        }
+        if (!DEC) {
+          const T x = ((const T*)a.field)[((g[0] * s) * geo.n[1] + g[1] * s) * geo.n[2] + g[2] * s];
+          T xq;
+          sym = quantize(x, pred, q, kRadius, xq);
+          a.codes[ad.slot] = (uint16_t)sym;
+          if (a.fine) ((T*)a.fine)[fidx] = xq;
+          if (sym == 0) atomicAdd(&a.chunk_outliers[geo.s[sid].chunk0 + ad.chunk], 1u);
+        } else {
+          const int sy = a.codes[ad.slot];
+          T val;
+          if (sy != 0) {
+            val = dequantize(sy, pred, two_eb, kRadius);
+          } else if (!find_outlier(a.opos[K], (const T*)a.oval[K], a.nout[K], ad.pos, val)) {
+            val = T(0);
+            atomicOr(a.status, kStatCorrupt);
+          }
+          ((T*)a.fine)[fidx] = val;
+        }
+      }
+      if (!DEC) {
+        const unsigned bm = __ballot_sync(0xffffffffu, sym == kRadius);
+        uint32_t* h = hist + (K - 1) * kHistWords;
+        if (lane == 0 && bm) atomicAdd(&h[kRadius >> 1], (uint32_t)__popc(bm));
+        if (sym >= 0 && sym != kRadius) atomicAdd(&h[sym >> 1], 1u << ((sym & 1) * 16));
+      }
+    }
+  }
+  if (!DEC) {
+    __syncthreads();
+    flush_hist<T>(hist, a.hist, l);
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+static int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+template <typename T, bool DEC>
+static int run_level_generic(const LevelArgs& a, cudaStream_t s) {
   int64_t M[3];
   grid_extent(a.geo.n, a.geo.L, a.level - 1, M);
   int tvol = 1;
@@ -225,20 +685,102 @@ static int run_level(const LevelArgs& a, cudaStream_t s) {
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return STZ_ERR_CUDA;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLevelThreads, smem);
   if (per_sm < 1) per_sm = 1;
   int64_t ntiles = a.tcnt[0] * a.tcnt[1] * a.tcnt[2];
   if (ntiles == 0) return STZ_OK;
-  int64_t grid = imin(ntiles, (int64_t)sms * per_sm);
+  int64_t grid = imin(ntiles, (int64_t)sm_count() * per_sm);
   char nm[48];
   snprintf(nm, sizeof(nm), "k_level%d_%s_%s", a.level, DEC ? "dec" : "enc",
            sizeof(T) == 4 ? "f32" : "f64");
   ProfScope ps_(nm, s);
   kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(a);
   return cuda_ok(cudaGetLastError());
+}
+
+template <typename T, bool DEC>
+static int run_level_fast(const LevelArgs& a, const int64_t M[3], cudaStream_t s) {
+  // interior cells exist only with M >= 4 on every axis
+  if (M[0] < 4 || M[1] < 4 || M[2] < 4) return STZ_OK;
+  size_t smem = 2 * (((size_t)(kFBZ + 3) * kFEZY * sizeof(T) + 15) & ~(size_t)15);
+  if (!DEC) smem += sizeof(uint32_t) * 7 * kHistWords;
+  auto kern = k_level_fast<T, DEC>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return STZ_ERR_CUDA;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLevelThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t ntiles = a.tcnt[0] * a.tcnt[1] * a.tcnt[2];
+  if (ntiles == 0) return STZ_OK;
+  const int64_t grid = imin(ntiles, (int64_t)sm_count() * per_sm);
+  char nm[48];
+  snprintf(nm, sizeof(nm), "k_level%d_%s_%s", a.level, DEC ? "dec" : "enc",
+           sizeof(T) == 4 ? "f32" : "f64");
+  ProfScope ps_(nm, s);
+  kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(a);
+  return cuda_ok(cudaGetLastError());
+}
+
+template <typename T, bool DEC>
+static int run_level_shell(const LevelArgs& a, const int64_t M[3], cudaStream_t s) {
+  ShellGeo sh;
+  memset(&sh, 0, sizeof(sh));
+  for (int d = 0; d < 3; d++) {
+    // needed cells: those whose points can fall in the fine box
+    sh.lo[d] = imax(0, a.flo[d] / 2);
+    sh.hi[d] = imin(M[d], cdiv(a.fhi[d], 2));
+    if (sh.hi[d] <= sh.lo[d]) return STZ_OK;
+    const int64_t cand[3] = {0, M[d] - 2, M[d] - 1};
+    sh.nb[d] = 0;
+    for (int k = 0; k < 3; k++) {
+      const int64_t v = cand[k];
+      bool dup = false;
+      for (int j = 0; j < sh.nb[d]; j++) dup = dup || sh.bv[d][j] == v;
+      const bool boundary = !(v >= 1 && v <= M[d] - 3);
+      if (!dup && boundary && v >= sh.lo[d] && v < sh.hi[d]) sh.bv[d][sh.nb[d]++] = v;
+    }
+    sh.ilo[d] = imax(1, sh.lo[d]);
+    sh.ihi[d] = imax(sh.ilo[d], imin(M[d] - 2, sh.hi[d]));
+  }
+  const int64_t nz = sh.hi[0] - sh.lo[0], ny = sh.hi[1] - sh.lo[1], nx = sh.hi[2] - sh.lo[2];
+  (void)nz;
+  const int64_t iz = sh.ihi[0] - sh.ilo[0], iy = sh.ihi[1] - sh.ilo[1];
+  sh.nA = sh.nb[0] * ny * nx;
+  sh.nB = iz * sh.nb[1] * nx;
+  sh.nC = iz * iy * sh.nb[2];
+  const int64_t total = sh.nA + sh.nB + sh.nC;
+  if (total == 0) return STZ_OK;
+  const size_t smem = DEC ? 0 : sizeof(uint32_t) * 7 * kHistWords;
+  auto kern = k_level_shell<T, DEC>;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+    return STZ_ERR_CUDA;
+  // at most 65535 cells per block keeps the 16-bit histogram counters exact
+  int64_t grid = imax(cdiv(total, 65535), imin(cdiv(total, 256), (int64_t)sm_count() * 4));
+  char nm[48];
+  snprintf(nm, sizeof(nm), "k_level%d_shell_%s_%s", a.level, DEC ? "dec" : "enc",
+           sizeof(T) == 4 ? "f32" : "f64");
+  ProfScope ps_(nm, s);
+  kern<<<(unsigned)grid, 256, smem, s>>>(a, sh);
+  return cuda_ok(cudaGetLastError());
+}
+
+template <typename T, bool DEC>
+static int run_level(const LevelArgs& a, cudaStream_t s) {
+  int64_t M[3];
+  grid_extent(a.geo.n, a.geo.L, a.level - 1, M);
+  const int64_t sl = level_stride(a.geo.L, a.level);
+  const int64_t fe = (a.fhi[1] - a.flo[1]) * (a.fhi[2] - a.flo[2]);
+  const bool fast = a.geo.b[0] == kFBZ && a.geo.b[1] == kFBY && a.geo.b[2] == kFBX &&
+                    2 * kFBZ * sl * a.geo.n[1] * a.geo.n[2] < ((int64_t)1 << 31) &&
+                    2 * kFBZ * fe < ((int64_t)1 << 31);
+  if (!fast) return run_level_generic<T, DEC>(a, s);
+  int rc = run_level_fast<T, DEC>(a, M, s);
+  if (rc != STZ_OK) return rc;
+  return run_level_shell<T, DEC>(a, M, s);
 }
 
 int launch_level(const LevelArgs& a, bool decode, cudaStream_t s) {

@@ -44,15 +44,15 @@ __device__ __forceinline__ int slot_coarse(int slot) { return slot == 0 ? 0 : (s
 // extent.  Interior: Eq. 6 / Eq. 7 / Eq. 8 by number of odd axes; otherwise
 // the separable product of the one-axis rules along the odd axes in the
 // order z, y, x (multi-linear Eqs. 3-5 where every rule is the midpoint).
-template <int K, typename T>
-__device__ __forceinline__ T level_predict(const T* __restrict__ t, int base, const int st[3],
+template <int K, typename T, typename I>
+__device__ __forceinline__ T level_predict(const T* __restrict__ t, I base, const I st[3],
                                            const int64_t g[3], const int64_t m[3]) {
   constexpr int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
   constexpr int nodd = oz + oy + ox;
   constexpr int a0 = oz ? 0 : (oy ? 1 : 2);
   constexpr int a1 = nodd >= 2 ? (oz ? (oy ? 1 : 2) : 2) : 2;
   constexpr int a2 = 2;
-  const int s0 = st[a0], s1 = st[a1], s2 = st[a2];
+  const I s0 = st[a0], s1 = st[a1], s2 = st[a2];
   bool cub = g[a0] >= 3 && g[a0] + 3 < m[a0];
   if (nodd >= 2) cub = cub && g[a1] >= 3 && g[a1] + 3 < m[a1];
   if (nodd == 3) cub = cub && g[a2] >= 3 && g[a2] + 3 < m[a2];
@@ -65,11 +65,11 @@ __device__ __forceinline__ T level_predict(const T* __restrict__ t, int base, co
                     op_add(t[base + 2 * s0 - s1], t[base + 2 * s0 + 2 * s1]));
       return op_add(op_mul(si, T(0.25)), op_mul(op_sub(si, so), T(0.03125)));
     } else {
-      const int z = s0, y = s1, x = s2;
+      const I z = s0, y = s1, x = s2;
       T si = op_add(op_add(op_add(t[base], t[base + x]), op_add(t[base + y], t[base + y + x])),
                     op_add(op_add(t[base + z], t[base + z + x]),
                            op_add(t[base + z + y], t[base + z + y + x])));
-      const int zm = -z, zp = 2 * z, ym = -y, yp = 2 * y, xm = -x, xp = 2 * x;
+      const I zm = -z, zp = 2 * z, ym = -y, yp = 2 * y, xm = -x, xp = 2 * x;
       T so = op_add(op_add(op_add(t[base + zm + ym + xm], t[base + zm + ym + xp]),
                            op_add(t[base + zm + yp + xm], t[base + zm + yp + xp])),
                     op_add(op_add(t[base + zp + ym + xm], t[base + zp + ym + xp]),

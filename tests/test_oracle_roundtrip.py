@@ -89,14 +89,14 @@ def test_header_layout(ora):
     b = c.tobytes()
     assert b[:4] == b"STZ1"
     (version,) = struct.unpack_from("<H", b, 4)
-    dtype, ndim, levels, mode, maxlen = b[6], b[7], b[8], b[9], b[10]
+    dtype, ndim, levels, mode, maxlen, nsub = b[6], b[7], b[8], b[9], b[10], b[11]
     (radius,) = struct.unpack_from("<I", b, 12)
     bricks = struct.unpack_from("<3I", b, 16)
     (ns,) = struct.unpack_from("<I", b, 28)
     dims = struct.unpack_from("<3q", b, 32)
     eb, eb_abs, vmin, vmax = struct.unpack_from("<4d", b, 56)
     (total,) = struct.unpack_from("<Q", b, 88)
-    assert (version, dtype, ndim, levels, mode, maxlen) == (1, 0, 3, 3, 1, 12)
+    assert (version, dtype, ndim, levels, mode, maxlen, nsub) == (1, 0, 3, 3, 1, 12, 4)
     assert radius == 1024 and bricks == (8, 16, 16) and ns == 15 and dims == (9, 10, 11)
     assert total == len(b)
     assert vmin == float(x.min()) and vmax == float(x.max())
@@ -135,3 +135,27 @@ def test_corruption_is_detected_or_harmless(ora):
             assert e.code in (ora.ERR_CORRUPT, ora.ERR_ARG)
             outcomes["corrupt"] += 1
     assert outcomes["corrupt"] > 0
+
+
+@pytest.mark.parametrize("nsub", [1, 2, 4, 8])
+def test_sub_chunk_counts(ora, nsub):
+    """Any sub-chunk count round-trips; the stored sub-chunk offsets are
+    checked against the decode (a shifted offset is rejected)."""
+    x = synth.sinusoids((30, 26, 33), 21)
+    c = ora.compress(x, 1e-3, nsub=nsub, brick=(4, 4, 8))
+    assert ora.info(c)["nsub"] == nsub
+    y = ora.decompress(c)
+    codes, soff, recon, ebs = ora.quantize(x, 1e-3)
+    assert np.array_equal(y.view(np.uint32), recon.view(np.uint32))
+    if nsub > 1:
+        # first sub-chunk offset of the level-3 x-odd stream (index 8)
+        sect = int(struct.unpack_from("<Q", c.tobytes(), 256 + 48 * 8)[0])
+        nlive = int(struct.unpack_from("<I", c.tobytes(), 256 + 48 * 8 + 20)[0])
+        nch = int(struct.unpack_from("<I", c.tobytes(), 256 + 48 * 8 + 16)[0])
+        off_subs = ((3 * nlive + 3) & ~3) + 4 * nch
+        b = c.copy()
+        v = struct.unpack_from("<H", b.tobytes(), sect + off_subs)[0]
+        struct.pack_into("<H", b, sect + off_subs, v + 1)
+        with pytest.raises(ora.OracleError) as e:
+            ora.decompress(b)
+        assert e.value.code == ora.ERR_CORRUPT
