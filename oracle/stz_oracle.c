@@ -225,12 +225,16 @@ static int leaf_cmp(const void* a, const void* b) {
  * Two-queue Huffman: repeatedly join the two lightest of (leaf queue head,
  * internal queue head), a leaf winning ties; internal nodes are queued in
  * creation order.  The depth of each leaf gives a count of codes per length.
- * If the longest exceeds max_len, the counts are repaired in the way of
- * ITU-T T.81 Annex K.3: two codes of the deepest length are replaced by one
- * code one level up, and one shorter code is split into two one level
- * deeper, which keeps the Kraft sum at 1.  Lengths are then handed out by
- * frequency rank: the most frequent symbols (the end of the sorted order)
- * receive the shortest lengths.  A single live symbol gets length 1.
+ * If the longest exceeds max_len, the counts are repaired: every code longer
+ * than max_len is shortened to max_len, which pushes the Kraft sum above 1 by
+ * an excess E (in units of 2^-max_len); then, in passes from length
+ * max_len-1 up to 1, as many codes as E allows (at most E / 2^(max_len-l-1)
+ * of them) move from length l to l+1, each lowering E by 2^(max_len-l-1);
+ * a pass that moves nothing while E > 0 moves one code of the largest length
+ * below max_len that has codes.  The sum ends at or below 1.  Lengths are then
+ * handed out by frequency rank: the most frequent symbols (the end of the
+ * sorted order) receive the shortest lengths.  A single live symbol gets
+ * length 1.
  */
 int ora_huffman_lengths(const uint64_t* freq, int nsym, int max_len, uint8_t* len) {
   if (nsym <= 0 || max_len < 1 || max_len > 24) return ORA_ERR_ARG;
@@ -290,14 +294,31 @@ int ora_huffman_lengths(const uint64_t* freq, int nsym, int max_len, uint8_t* le
     bl[d]++;
     if (d > maxd) maxd = d;
   }
-  for (int l = maxd; l > max_len; l--) {
-    while (bl[l] > 0) {
-      int jj = l - 2;
-      while (jj > 0 && bl[jj] == 0) jj--;
-      bl[l] -= 2;
-      bl[l - 1] += 1;
-      bl[jj + 1] += 2;
-      bl[jj] -= 1;
+  if (maxd > max_len) {
+    for (int l = maxd; l > max_len; l--) {
+      bl[max_len] += bl[l];
+      bl[l] = 0;
+    }
+    int64_t excess = -((int64_t)1 << max_len);
+    for (int l = 1; l <= max_len; l++) excess += (int64_t)bl[l] << (max_len - l);
+    while (excess > 0) {
+      int moved = 0;
+      for (int l = max_len - 1; l >= 1 && excess > 0; l--) {
+        const int64_t unit = (int64_t)1 << (max_len - l - 1);
+        int64_t t = excess / unit;
+        if (t > bl[l]) t = bl[l];
+        bl[l] -= (int)t;
+        bl[l + 1] += (int)t;
+        excess -= t * unit;
+        moved += t > 0;
+      }
+      if (excess > 0 && !moved) {
+        int l = max_len - 1;
+        while (l >= 1 && bl[l] == 0) l--;
+        bl[l] -= 1;
+        bl[l + 1] += 1;
+        excess -= (int64_t)1 << (max_len - l - 1);
+      }
     }
   }
   /* hand out lengths by rank, most frequent first */

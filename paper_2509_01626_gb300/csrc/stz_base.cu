@@ -82,6 +82,7 @@ constexpr int kMaxPasses = 64;
 struct PassList {
   PassGeo p[kMaxPasses];
   int npass, nsmall;
+  int64_t ts;  // stride of the subgrid held in shared memory by the coarse phase
 };
 
 template <typename T>
@@ -97,16 +98,40 @@ __device__ __forceinline__ T base_predict_cg(const T* g1, int64_t idx, int64_t s
   return vm1;
 }
 
+// Address of level-1 grid point g in stream 0 (32-bit arithmetic: the level-1
+// grid has fewer than 2^31 points).
+struct Addr32 {
+  int64_t slot, pos;
+  int chunk;
+};
+__device__ __forceinline__ Addr32 addr0(const StreamGeo& sg, const int32_t b[3], int bvol,
+                                        const SlotMap& sm, int c0, int c1, int c2) {
+  const int B0 = c0 / b[0], B1 = c1 / b[1], B2 = c2 / b[2];
+  const int e0 = (int)sg.e[0], e1 = (int)sg.e[1], e2 = (int)sg.e[2];
+  const int l0 = min(b[0], e0 - B0 * b[0]), l1 = min(b[1], e1 - B1 * b[1]),
+            l2 = min(b[2], e2 - B2 * b[2]);
+  const int local = ((c0 - B0 * b[0]) * l1 + (c1 - B1 * b[1])) * l2 + (c2 - B2 * b[2]);
+  Addr32 r;
+  r.pos = (int64_t)B0 * b[0] * e1 * e2 + (int64_t)B1 * b[1] * l0 * e2 +
+          (int64_t)B2 * b[2] * l0 * l1 + local;
+  r.chunk = (B0 * (int)sg.nb[1] + B1) * (int)sg.nb[2] + B2;
+  const int ord = ((B0 - (int)sm.lo[0]) * (int)sm.cnt[1] + (B1 - (int)sm.lo[1])) * (int)sm.cnt[2] +
+                  (B2 - (int)sm.lo[2]);
+  r.slot = (sm.base + ord) * (int64_t)bvol + local;
+  return r;
+}
+
 template <typename T, bool DEC>
-__device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p, int64_t i,
+__device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p, int64_t i64,
                                            const int64_t m[3], int64_t s1, const QConst<T>& q) {
   const Geo& geo = a.geo;
-  int64_t i2 = i % p.cnt[2], r = i / p.cnt[2];
-  int64_t i1 = r % p.cnt[1], i0 = r / p.cnt[1];
-  int64_t g0 = p.start[0] + i0 * p.step[0];
-  int64_t g1 = p.start[1] + i1 * p.step[1];
-  int64_t g2 = p.start[2] + i2 * p.step[2];
-  int64_t idx = (g0 * m[1] + g1) * m[2] + g2;
+  const unsigned i = (unsigned)i64, n2 = (unsigned)p.cnt[2], n1 = (unsigned)p.cnt[1];
+  const unsigned r = i / n2;
+  const int i2 = (int)(i - r * n2), i1 = (int)(r % n1), i0 = (int)(r / n1);
+  const int g0 = (int)p.start[0] + i0 * (int)p.step[0];
+  const int g1 = (int)p.start[1] + i1 * (int)p.step[1];
+  const int g2 = (int)p.start[2] + i2 * (int)p.step[2];
+  const int64_t idx = ((int64_t)g0 * m[1] + g1) * m[2] + g2;
   T* grid = (T*)a.g1;
   T pred = T(0);
   if (!p.origin) {
@@ -114,10 +139,10 @@ __device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p, 
     const int64_t c = p.axis == 0 ? g0 : (p.axis == 1 ? g1 : g2);
     pred = base_predict_cg(grid, idx, st, c, p.t, m[p.axis]);
   }
-  CellAddr ad = cell_addr(geo.s[0], geo.b, geo.bvol, a.sm, g0, g1, g2);
+  const Addr32 ad = addr0(geo.s[0], geo.b, (int)geo.bvol, a.sm, g0, g1, g2);
   if (!DEC) {
     const T* f = (const T*)a.field;
-    T x = f[((g0 * s1) * geo.n[1] + g1 * s1) * geo.n[2] + g2 * s1];
+    T x = f[(((int64_t)g0 * s1) * geo.n[1] + (int64_t)g1 * s1) * geo.n[2] + (int64_t)g2 * s1];
     T xr;
     int sym = quantize(x, pred, q, kRadius, xr);
     __stcg(grid + idx, xr);
@@ -138,6 +163,99 @@ __device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p, 
   }
 }
 
+// Coarse phase in shared memory: every pass with stride t >= ts touches only
+// points of the stride-ts subgrid (extent sm = ceil(m / ts)), which block 0
+// keeps in shared memory; those passes run there with block barriers and
+// the subgrid is then written to the level-1 grid.  The remaining passes
+// (t < ts) are spread over the grid with a grid barrier before each.
+template <typename T, bool DEC>
+__device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint16_t* sc,
+                             int64_t ts, const int64_t sm[3], const int64_t m[3], int64_t s1,
+                             const QConst<T>& q) {
+  const Geo& geo = a.geo;
+  const int64_t nsg = sm[0] * sm[1] * sm[2];
+  // gather the subgrid's inputs first, all loads in flight: the field values
+  // (compress) or the codes (decode)
+  for (int i = threadIdx.x; i < (int)nsg; i += blockDim.x) {
+    const int x = i % (int)sm[2], y = (i / (int)sm[2]) % (int)sm[1], z = i / (int)(sm[1] * sm[2]);
+    const int g0 = z * (int)ts, g1 = y * (int)ts, g2 = x * (int)ts;
+    if (!DEC) {
+      sg[i] = ((const T*)a.field)[(((int64_t)g0 * s1) * geo.n[1] + (int64_t)g1 * s1) * geo.n[2] +
+                                  (int64_t)g2 * s1];
+    } else {
+      sc[i] = a.codes[addr0(geo.s[0], geo.b, (int)geo.bvol, a.sm, g0, g1, g2).slot];
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < pl.nsmall; k++) {
+    const PassGeo& p = pl.p[k];
+    const unsigned n2 = (unsigned)p.cnt[2], n1 = (unsigned)p.cnt[1];
+    for (int i = threadIdx.x; i < (int)p.total; i += blockDim.x) {
+      const unsigned r = (unsigned)i / n2;
+      const int i2 = (int)((unsigned)i - r * n2), i1 = (int)(r % n1), i0 = (int)(r / n1);
+      const int g[3] = {(int)p.start[0] + i0 * (int)p.step[0],
+                        (int)p.start[1] + i1 * (int)p.step[1],
+                        (int)p.start[2] + i2 * (int)p.step[2]};
+      const int tsi = (int)ts;
+      const int64_t si = ((int64_t)(g[0] / tsi) * sm[1] + g[1] / tsi) * sm[2] + g[2] / tsi;
+      T pred = T(0);
+      if (!p.origin) {
+        const int ax = p.axis;
+        const int64_t st = ax == 0 ? sm[1] * sm[2] : (ax == 1 ? sm[2] : 1);
+        // the subgrid holds every ts-th point: pass stride t is t/ts subgrid steps
+        pred = base_predict(sg, si, st, g[ax] / ts, p.t / ts, sm[ax]);
+        (void)m;
+      }
+      if (!DEC) {
+        const Addr32 ad = addr0(geo.s[0], geo.b, (int)geo.bvol, a.sm, g[0], g[1], g[2]);
+        const T x = sg[si];  // still the field value: this point is visited once
+        T xr;
+        const int sym = quantize(x, pred, q, kRadius, xr);
+        sg[si] = xr;
+        a.codes[ad.slot] = (uint16_t)sym;
+        if (sym == 0) atomicAdd(&a.chunk_outliers[geo.s[0].chunk0 + ad.chunk], 1u);
+      } else {
+        const int sym = sc[si];
+        T v;
+        if (sym == 0) {
+          const Addr32 ad = addr0(geo.s[0], geo.b, (int)geo.bvol, a.sm, g[0], g[1], g[2]);
+          if (!find_outlier(a.opos, (const T*)a.oval, a.nout, ad.pos, v)) {
+            v = T(0);
+            atomicOr(a.status, kStatCorrupt);
+          }
+        } else {
+          v = dequantize(sym, pred, (T)a.two_eb, kRadius);
+        }
+        sg[si] = v;
+      }
+    }
+    __syncthreads();
+  }
+  // write the subgrid to the level-1 grid
+  T* grid = (T*)a.g1;
+  for (int64_t i = threadIdx.x; i < nsg; i += blockDim.x) {
+    const int64_t x = i % sm[2], y = (i / sm[2]) % sm[1], z = i / (sm[1] * sm[2]);
+    __stcg(grid + ((z * ts) * m[1] + y * ts) * m[2] + x * ts, sg[i]);
+  }
+}
+
+template <typename T, bool DEC>
+__global__ void __launch_bounds__(1024) k_base_coarse(const __grid_constant__ BaseArgs a,
+                                                      const __grid_constant__ PassList pl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int64_t m[3];
+  grid_extent(a.geo.n, a.geo.L, 1, m);
+  const int64_t s1 = level_stride(a.geo.L, 1);
+  QConst<T> q;
+  if (!DEC) q.load(a.dp, 1, kRadius);
+  const int64_t ts = pl.ts;
+  const int64_t sm[3] = {cdiv(m[0], ts), cdiv(m[1], ts), cdiv(m[2], ts)};
+  const int64_t nsg = sm[0] * sm[1] * sm[2];
+  T* sg = (T*)smem_raw;
+  uint16_t* sc = (uint16_t*)(smem_raw + sizeof(T) * nsg);
+  coarse_phase<T, DEC>(a, pl, sg, sc, ts, sm, m, s1, q);
+}
+
 template <typename T, bool DEC>
 __global__ void __launch_bounds__(256) k_base_coop(const __grid_constant__ BaseArgs a,
                                                    const __grid_constant__ PassList pl) {
@@ -147,15 +265,8 @@ __global__ void __launch_bounds__(256) k_base_coop(const __grid_constant__ BaseA
   const int64_t s1 = level_stride(a.geo.L, 1);
   QConst<T> q;
   if (!DEC) q.load(a.dp, 1, kRadius);
-  if (blockIdx.x == 0) {
-    for (int k = 0; k < pl.nsmall; k++) {
-      const PassGeo& p = pl.p[k];
-      for (int64_t i = threadIdx.x; i < p.total; i += blockDim.x) base_point<T, DEC>(a, p, i, m, s1, q);
-      __syncthreads();
-    }
-  }
   for (int k = pl.nsmall; k < pl.npass; k++) {
-    grid.sync();
+    if (k > pl.nsmall) grid.sync();
     const PassGeo& p = pl.p[k];
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.total; i += nth)
@@ -216,9 +327,26 @@ static int run_coop(const BaseArgs& a, cudaStream_t s) {
       biggest = imax(biggest, p.total);
     }
   }
-  // leading passes small enough for one block
+  // coarse phase: the passes with t >= ts, ts the smallest power of two whose
+  // subgrid fits in 128 KiB of shared memory
+  const int64_t cap = (128 * 1024) / (int64_t)sizeof(T);
+  int64_t ts = 1;
+  while (cdiv(m[0], ts) * cdiv(m[1], ts) * cdiv(m[2], ts) > cap) ts <<= 1;
+  pl.ts = ts;
   pl.nsmall = 0;
-  while (pl.nsmall < pl.npass && pl.p[pl.nsmall].total <= 4096) pl.nsmall++;
+  while (pl.nsmall < pl.npass && (pl.p[pl.nsmall].origin || pl.p[pl.nsmall].t >= ts)) pl.nsmall++;
+  const size_t nsg = (size_t)(cdiv(m[0], ts) * cdiv(m[1], ts) * cdiv(m[2], ts));
+  const size_t smem = sizeof(T) * nsg + (DEC ? sizeof(uint16_t) * nsg : 0);
+  {
+    auto ck = k_base_coarse<T, DEC>;
+    if (cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return STZ_ERR_CUDA;
+    ProfScope ps_(DEC ? "k_base_coarse_dec" : "k_base_coarse_enc", s);
+    ck<<<1, 1024, smem, s>>>(a, pl);
+    if (cudaGetLastError() != cudaSuccess) return STZ_ERR_CUDA;
+  }
+  if (pl.nsmall == pl.npass) return STZ_OK;
   auto kern = k_base_coop<T, DEC>;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -226,7 +354,6 @@ static int run_coop(const BaseArgs& a, cudaStream_t s) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
   if (per_sm < 1) return STZ_ERR_CUDA;
   int64_t blocks = imin((int64_t)sms * imin(per_sm, 4), imax(1, cdiv(biggest, 256)));
-  if (pl.nsmall == pl.npass) blocks = 1;
   void* args[] = {(void*)&a, (void*)&pl};
   cudaError_t e;
   {
@@ -235,8 +362,13 @@ static int run_coop(const BaseArgs& a, cudaStream_t s) {
                                     s);
   }
   if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
-    cudaGetLastError();  // clear, then one launch per pass
-    return run_passes<T, DEC>(a, s);
+    cudaGetLastError();  // clear, then one launch per remaining pass
+    for (int k = pl.nsmall; k < pl.npass; k++) {
+      const PassGeo& p = pl.p[k];
+      ProfScope ps_(DEC ? "k_base_pass_dec" : "k_base_pass_enc", s);
+      k_base_pass<T, DEC><<<(unsigned)cdiv(p.total, 256), 256, 0, s>>>(a, p);
+    }
+    return cuda_ok(cudaGetLastError());
   }
   return cuda_ok(e);
 }

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
                                                            uint16_t* __restrict__ enc,
                                                            BookDev* __restrict__ books) {
   __shared__ unsigned long long key[kAlphabet];
-  __shared__ unsigned long long iw[kAlphabet];
+  __shared__ uint32_t iw[kAlphabet];
   __shared__ uint16_t par_leaf[kAlphabet];
   __shared__ uint16_t par_int[kAlphabet];
   __shared__ uint8_t dep[kAlphabet];
@@ -77,24 +77,32 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
   __shared__ int bl[64];
   __shared__ uint32_t first_code[32];
   __shared__ int first_index[32];
+  __shared__ int wcnt[2 * kBookThreads / 32][kMaxCodeLen + 1];  // per warp-group, per length
   __shared__ int s_n;
   const int s = blockIdx.x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint32_t* h = hist + (int64_t)s * kAlphabet;
   if (tid == 0) s_n = 0;
   if (tid < 64) bl[tid] = 0;
   __syncthreads();
-  int live = 0;
-  for (int i = tid; i < kAlphabet; i += blockDim.x) {
-    uint32_t f = h[i];
-    key[i] = f ? (((unsigned long long)f << 11) | (unsigned long long)i) : ~0ull;
-    len_of[i] = 0;
-    live += f != 0;
+  // compact the live symbols (in symbol order) into key[0..n)
+  for (int r = 0; r < kAlphabet / kBookThreads; r++) {
+    const int sym = r * kBookThreads + tid;
+    const uint32_t f = h[sym];
+    len_of[sym] = 0;
+    const unsigned bm = __ballot_sync(0xffffffffu, f != 0);
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&s_n, __popc(bm));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (f) key[base + __popc(bm & ((1u << lane) - 1u))] = ((unsigned long long)f << 11) | (unsigned long long)sym;
   }
-  if (live) atomicAdd(&s_n, live);
   __syncthreads();
-  bitonic_sort_u64(key, kAlphabet);  // ends with a barrier
   const int nl = s_n;
+  int P = 1;
+  while (P < nl) P <<= 1;
+  for (int i = nl + tid; i < P; i += blockDim.x) key[i] = ~0ull;
+  __syncthreads();
+  if (P > 1) bitonic_sort_u64(key, P);  // (frequency, symbol) ascending
   BookDev* bk = books + s;
   uint16_t* e = enc + (int64_t)s * kAlphabet;
   if (nl == 0) {
@@ -112,49 +120,108 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
     }
     return;
   }
-  // two-queue merge (sequential, one thread)
+  // two-queue merge (sequential, one thread).  The next leaf weights are kept
+  // in registers two ahead so the loop carries no shared-memory latency.
   if (tid == 0) {
+    // weights fit in 32 bits: a stream has fewer than 2^31 symbols
     int i = 0, j = 0;
-    unsigned long long lw = key[0] >> 11;
-    unsigned long long jw = 0;
+    uint32_t lw = (uint32_t)(key[0] >> 11);
+    uint32_t lw1 = nl > 1 ? (uint32_t)(key[1] >> 11) : 0u;
+    uint32_t lw2 = nl > 2 ? (uint32_t)(key[2] >> 11) : 0u;
+    uint32_t jw = 0, jw1 = 0;  // internal queue head and the node after it
     for (int k = 0; k < nl - 1; k++) {
-      unsigned long long w = 0;
+      uint32_t wsum = 0;
 #pragma unroll
       for (int pick = 0; pick < 2; pick++) {
         const bool take_leaf = i < nl && (j >= k || lw <= jw);
         if (take_leaf) {
-          w += lw;
+          wsum += lw;
           par_leaf[i] = (uint16_t)k;
           i++;
-          lw = i < nl ? (key[i] >> 11) : 0ull;
+          lw = lw1;
+          lw1 = lw2;
+          lw2 = i + 2 < nl ? (uint32_t)(key[i + 2] >> 11) : 0u;
+          if (i >= nl) lw = 0u;
         } else {
-          w += jw;
+          wsum += jw;
           par_int[j] = (uint16_t)k;
           j++;
-          jw = j < k ? iw[j] : 0ull;
+          jw = jw1;
+          jw1 = j + 1 < k ? iw[j + 1] : 0u;
         }
       }
-      iw[k] = w;
-      if (j == k) jw = w;  // the queue was empty: its head is the new node
+      iw[k] = wsum;
+      if (j == k) {
+        jw = wsum;  // the queue was empty: its head is the new node
+      } else if (j + 1 == k) {
+        jw1 = wsum;
+      }
     }
-    dep[nl - 2] = 0;
-    for (int k = nl - 3; k >= 0; k--) dep[k] = (uint8_t)(dep[par_int[k]] + 1);
   }
   __syncthreads();
+  // depth of every internal node by pointer jumping (the root, node nl-2, has
+  // depth 0); a leaf's depth is its parent's plus one
+  {
+    // the internal weights are no longer needed: iw holds the ancestors
+    uint32_t* anc = iw;
+    for (int k = tid; k < nl - 1; k += blockDim.x) {
+      const bool root = k == nl - 2;
+      dep[k] = root ? 0 : 1;
+      anc[k] = root ? (uint32_t)k : (uint32_t)par_int[k];
+    }
+    __syncthreads();
+    for (int round = 0; round < 12; round++) {  // 2^12 > 2047 nodes
+      uint8_t nd[2];
+      uint32_t na[2];
+      int cnt = 0;
+      for (int k = tid; k < nl - 1 && cnt < 2; k += blockDim.x, cnt++) {
+        const uint32_t a1 = anc[k];
+        nd[cnt] = (uint8_t)(dep[k] + dep[a1]);
+        na[cnt] = anc[a1];
+      }
+      __syncthreads();
+      cnt = 0;
+      for (int k = tid; k < nl - 1 && cnt < 2; k += blockDim.x, cnt++) {
+        dep[k] = nd[cnt];
+        anc[k] = na[cnt];
+      }
+      __syncthreads();
+    }
+  }
   for (int i = tid; i < nl; i += blockDim.x) atomicAdd(&bl[min(dep[par_leaf[i]] + 1, 63)], 1);
   __syncthreads();
   if (tid == 0) {
     int maxd = 0;
     for (int d = 1; d < 64; d++)
       if (bl[d]) maxd = d;
-    for (int L = maxd; L > kMaxCodeLen; L--) {
-      while (bl[L] > 0) {
-        int jj = L - 2;
-        while (jj > 0 && bl[jj] == 0) jj--;
-        bl[L] -= 2;
-        bl[L - 1] += 1;
-        bl[jj + 1] += 2;
-        bl[jj] -= 1;
+    // lengths above the limit: clamp, then remove the Kraft excess by moving
+    // codes one length deeper, deepest lengths first
+    if (maxd > kMaxCodeLen) {
+      for (int L = maxd; L > kMaxCodeLen; L--) {
+        bl[kMaxCodeLen] += bl[L];
+        bl[L] = 0;
+      }
+      long long excess = -(1ll << kMaxCodeLen);
+      for (int L = 1; L <= kMaxCodeLen; L++) excess += (long long)bl[L] << (kMaxCodeLen - L);
+      for (int guard = 0; excess > 0 && guard < 4 * kMaxCodeLen; guard++) {
+        int moved = 0;
+        for (int L = kMaxCodeLen - 1; L >= 1 && excess > 0; L--) {
+          const long long unit = 1ll << (kMaxCodeLen - L - 1);
+          long long t = excess / unit;
+          if (t > bl[L]) t = bl[L];
+          bl[L] -= (int)t;
+          bl[L + 1] += (int)t;
+          excess -= t * unit;
+          moved += t > 0;
+        }
+        if (excess > 0 && !moved) {
+          int L = kMaxCodeLen - 1;
+          while (L >= 1 && bl[L] == 0) L--;
+          if (L < 1) break;
+          bl[L] -= 1;
+          bl[L + 1] += 1;
+          excess -= 1ll << (kMaxCodeLen - L - 1);
+        }
       }
     }
     uint32_t code = 0;
@@ -178,16 +245,38 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
     len_of[key[i] & 2047ull] = (uint8_t)L;
   }
   __syncthreads();
-  // canonical order: sort (length, symbol)
-  for (int i = tid; i < kAlphabet; i += blockDim.x)
-    key[i] = len_of[i] ? (((unsigned long long)len_of[i] << 11) | (unsigned long long)i) : ~0ull;
+  // canonical order (length, symbol): rank of a symbol inside its length class
+  // from ballots over the symbols in order; warp-group g covers symbols 32g..32g+31
+  int myL[2], myr[2];
+  for (int r = 0; r < 2; r++) {
+    const int sym = r * kBookThreads + tid;
+    const int L = len_of[sym];
+    myL[r] = L;
+    myr[r] = 0;
+    for (int LL = 1; LL <= kMaxCodeLen; LL++) {
+      const unsigned bm = __ballot_sync(0xffffffffu, L == LL);
+      if (L == LL) myr[r] = __popc(bm & ((1u << lane) - 1u));
+      if (lane == 0) wcnt[r * (kBookThreads / 32) + w][LL] = __popc(bm);
+    }
+  }
   __syncthreads();
-  bitonic_sort_u64(key, kAlphabet);
-  for (int i = tid; i < kAlphabet; i += blockDim.x) e[i] = 0;
+  if (tid <= kMaxCodeLen && tid >= 1) {  // exclusive prefix over warp-groups, per length
+    int run = 0;
+    for (int gi = 0; gi < 2 * kBookThreads / 32; gi++) {
+      const int c = wcnt[gi][tid];
+      wcnt[gi][tid] = run;
+      run += c;
+    }
+  }
   __syncthreads();
-  for (int k = tid; k < nl; k += blockDim.x) {
-    const int L = (int)(key[k] >> 11);
-    const int sym = (int)(key[k] & 2047ull);
+  for (int r = 0; r < 2; r++) {
+    const int sym = r * kBookThreads + tid;
+    const int L = myL[r];
+    if (L == 0) {
+      e[sym] = 0;
+      continue;
+    }
+    const int k = first_index[L] + wcnt[r * (kBookThreads / 32) + w][L] + myr[r];
     const uint32_t code = first_code[L] + (uint32_t)(k - first_index[L]);
     e[sym] = (uint16_t)((code << 4) | (uint32_t)L);
     bk->sym[k] = (uint16_t)sym;
@@ -217,29 +306,109 @@ __device__ __forceinline__ int64_t chunk_count(const Geo& g, int sid, int64_t jl
   return l[0] * l[1] * l[2];
 }
 
+// stream and symbol count of chunk j in 32-bit arithmetic (brick counts and
+// extents of one stream fit in 32 bits)
+__device__ __forceinline__ void chunk_sid_cnt(const Geo& g, int64_t j, int& sid, int& cnt) {
+  sid = stream_of_chunk(g, j);
+  const StreamGeo& sg = g.s[sid];
+  const int jl = (int)(j - sg.chunk0);
+  const int nb1 = (int)sg.nb[1], nb2 = (int)sg.nb[2];
+  const int B0 = jl / (nb1 * nb2), r = jl - B0 * nb1 * nb2;
+  const int B1 = r / nb2, B2 = r - B1 * nb2;
+  cnt = min(g.b[0], (int)sg.e[0] - B0 * g.b[0]) * min(g.b[1], (int)sg.e[1] - B1 * g.b[1]) *
+        min(g.b[2], (int)sg.e[2] - B2 * g.b[2]);
+}
+
+// Block-wide exclusive scan of one u32 per thread (256 threads).
+__device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t* wsum, uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < 8 ? wsum[lane] : 0u;
+    for (int o = 1; o < 8; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < 8) wsum[lane] = t;
+  }
+  __syncthreads();
+  *total = wsum[7];
+  return x - v + (w > 0 ? wsum[w - 1] : 0u);
+}
+
+// 8 consecutive symbols of a chunk per thread: codes and lengths
+__device__ __forceinline__ int load8(const uint16_t* c, int i0, int64_t cnt, const uint16_t* e,
+                                     uint32_t (&code)[8], uint32_t (&len)[8]) {
+  uint16_t sym[8];
+  if (i0 + 8 <= cnt) {
+    const uint4 v = *(const uint4*)(c + i0);
+    const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      sym[2 * k] = (uint16_t)(u[k] & 0xFFFFu);
+      sym[2 * k + 1] = (uint16_t)(u[k] >> 16);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; k++) sym[k] = i0 + k < cnt ? c[i0 + k] : (uint16_t)0xFFFF;
+  }
+  int bits = 0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const uint32_t ent = sym[k] == 0xFFFF ? 0u : (uint32_t)__ldg(e + sym[k]);
+    code[k] = ent >> 4;
+    len[k] = ent & 15u;
+    bits += (int)len[k];
+  }
+  return bits;
+}
+
+// payload words per chunk: one block per chunk, 8 symbols per thread
 __global__ void __launch_bounds__(256) k_chunk_words(const __grid_constant__ Geo g,
                                                      const uint16_t* __restrict__ codes,
                                                      const uint16_t* __restrict__ enc,
                                                      uint32_t* __restrict__ words) {
-  const int lane = threadIdx.x & 31;
-  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (j >= g.total_chunks) return;
-  const int sid = stream_of_chunk(g, j);
-  const int64_t cnt = chunk_count(g, sid, j - g.s[sid].chunk0);
-  const uint16_t* c = codes + j * g.bvol;
-  const uint16_t* e = enc + (int64_t)sid * kAlphabet;
-  uint32_t bits = 0;
-  for (int64_t i = lane; i < cnt; i += 32) bits += e[c[i]] & 15u;
-  for (int off = 16; off > 0; off >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, off);
-  if (lane == 0) words[j] = (bits + 31) >> 5;
+  __shared__ uint32_t wsum[2][8];
+  __shared__ int s_sid[2], s_cnt[2];
+  int par = 0;
+  for (int64_t j = blockIdx.x; j < g.total_chunks; j += gridDim.x, par ^= 1) {
+    if (threadIdx.x == 0) chunk_sid_cnt(g, j, s_sid[par], s_cnt[par]);
+    __syncthreads();
+    const int sid = s_sid[par];
+    const int64_t cnt = s_cnt[par];
+    const uint16_t* c = codes + j * g.bvol;
+    const uint16_t* e = enc + (int64_t)sid * kAlphabet;
+    uint32_t bits = 0;
+    for (int i0 = threadIdx.x * 8; i0 < cnt; i0 += 256 * 8) {
+      uint32_t code[8], len[8];
+      bits += (uint32_t)load8(c, i0, cnt, e, code, len);
+    }
+    for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+    if ((threadIdx.x & 31) == 0) wsum[par][threadIdx.x >> 5] = bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t t = 0;
+      for (int k = 0; k < 8; k++) t += wsum[par][k];
+      words[j] = (t + 31) >> 5;
+    }
+  }
 }
 
 int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc, uint32_t* words,
                        cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
-  int64_t blocks = cdiv(g.total_chunks * 32, 256);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t grid = imin(g.total_chunks, (int64_t)sms * 8);
   ProfScope ps_("k_chunk_words", s);
-  k_chunk_words<<<(unsigned)blocks, 256, 0, s>>>(g, codes, enc, words);
+  k_chunk_words<<<(unsigned)grid, 256, 0, s>>>(g, codes, enc, words);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -373,78 +542,113 @@ int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long 
 }
 
 // ---------------------------------------------------------------- bit packing
-constexpr int kPackWarps = 8;
-
-__global__ void __launch_bounds__(kPackWarps * 32) k_pack(
-    const __grid_constant__ Geo g, const uint16_t* __restrict__ codes,
-    const uint16_t* __restrict__ enc, const unsigned long long* __restrict__ word_off,
-    const SectDev* __restrict__ sect, uint8_t* __restrict__ out, const DevParams* dp) {
-  extern __shared__ uint32_t wbuf[];  // kPackWarps * maxw
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t maxw = (g.bvol * kMaxCodeLen + 31) / 32;
-  uint32_t* buf = wbuf + w * maxw;
-  const int64_t j = (int64_t)blockIdx.x * kPackWarps + w;
-  if (j >= g.total_chunks) return;
+// Blocks loop over chunks: each thread takes 8 consecutive symbols, a block
+// scan of their code lengths gives bit positions, the thread assembles its
+// (at most 96) bits in registers and ORs them into at most 4 words of the
+// chunk held in shared memory; the words are stored with coalesced writes.
+// The sub-chunk offsets are the bit positions of symbols u * ceil(n / 4).
+__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
+                                              const uint16_t* __restrict__ codes,
+                                              const uint16_t* __restrict__ enc,
+                                              const unsigned long long* __restrict__ word_off,
+                                              const SectDev* __restrict__ sect,
+                                              uint8_t* __restrict__ out,
+                                              const DevParams* __restrict__ dp) {
+  extern __shared__ uint32_t wbuf[];
+  __shared__ uint32_t wsum[8];
+  __shared__ int s_sid, s_cnt;
   if (dp->status & kStatCapacity) return;
-  const int sid = stream_of_chunk(g, j);
-  const int64_t cnt = chunk_count(g, sid, j - g.s[sid].chunk0);
-  const int64_t nw = (int64_t)(word_off[j + 1] - word_off[j]);
-  for (int64_t i = lane; i < nw; i += 32) buf[i] = 0;
-  __syncwarp();
-  const uint16_t* c = codes + j * g.bvol;
-  const uint16_t* e = enc + (int64_t)sid * kAlphabet;
-  const SectDev& sd = sect[sid];
-  const int64_t q = (cnt + kNSub - 1) / kNSub;
-  uint16_t* so = (uint16_t*)(out + sd.sect_off + sd.off_subs) + (j - g.s[sid].chunk0) * (kNSub - 1);
-  uint32_t base = 0;
-  for (int64_t i0 = 0; i0 < cnt; i0 += 32) {
-    const int64_t i = i0 + lane;
-    uint32_t code = 0, len = 0;
-    if (i < cnt) {
-      uint32_t v = e[c[i]];
-      code = v >> 4;
-      len = v & 15u;
-    }
-    uint32_t incl = len;
-    for (int off = 1; off < 32; off <<= 1) {
-      uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += t;
-    }
-    const uint32_t p = base + incl - len;
+  for (int64_t j = blockIdx.x; j < g.total_chunks; j += gridDim.x) {
+    __syncthreads();  // the previous chunk's words are written out
+    if (threadIdx.x == 0) chunk_sid_cnt(g, j, s_sid, s_cnt);
+    __syncthreads();
+    const int sid = s_sid;
+    const int cnt = s_cnt;
+    const int nw = (int)(word_off[j + 1] - word_off[j]);
+    for (int i = threadIdx.x; i < nw; i += 256) wbuf[i] = 0;
+    const uint16_t* c = codes + j * g.bvol;
+    const uint16_t* e = enc + (int64_t)sid * kAlphabet;
+    const SectDev& sd = sect[sid];
+    const int q = (cnt + kNSub - 1) / kNSub;
+    uint16_t* so =
+        (uint16_t*)(out + sd.sect_off + sd.off_subs) + (j - g.s[sid].chunk0) * (kNSub - 1);
+    uint32_t base = 0;
+    for (int r0 = 0; r0 < cnt; r0 += 256 * 8) {
+      const int i0 = r0 + threadIdx.x * 8;
+      uint32_t code[8], len[8];
+      const uint32_t bits = (uint32_t)load8(c, i0, cnt, e, code, len);
+      uint32_t total;
+      __syncthreads();  // wbuf zeroed; scan scratch free
+      const uint32_t p = base + block_scan_256(bits, wsum, &total);
+      // sub-chunk starts inside this thread's 8 symbols
 #pragma unroll
-    for (int u = 1; u < kNSub; u++)
-      if (i == u * q && i < cnt) so[u - 1] = (uint16_t)p;
-    if (len) {
-      const uint32_t wi = p >> 5, r = p & 31u;
-      if (r + len <= 32u) {
-        atomicOr(&buf[wi], code << (32u - r - len));
-      } else {
-        atomicOr(&buf[wi], code >> (r + len - 32u));
-        atomicOr(&buf[wi + 1], code << (64u - r - len));
+      for (int u = 1; u < kNSub; u++) {
+        const int b = u * q;
+        if (b >= i0 && b < i0 + 8 && b < cnt) {
+          uint32_t off = p;
+#pragma unroll
+          for (int k = 0; k < 8; k++)
+            if (k < b - i0) off += len[k];
+          so[u - 1] = (uint16_t)off;
+        }
       }
+      // the thread's bit string, left-aligned in 128 bits (hi:lo)
+      unsigned long long hi = 0, lo = 0;
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const uint32_t L = len[k];
+        if (L) {
+          hi = (hi << L) | (lo >> (64 - L));
+          lo = (lo << L) | code[k];
+        }
+      }
+      if (bits) {
+        const uint32_t sh = 128u - bits;  // left-align
+        if (sh >= 64) {
+          hi = lo << (sh - 64);
+          lo = 0;
+        } else if (sh > 0) {
+          hi = (hi << sh) | (lo >> (64 - sh));
+          lo <<= sh;
+        }
+        const uint32_t r = p & 31u, wi = p >> 5;
+        if (r) {  // shift right by r into 160 bits: hi:lo:x
+          lo = (lo >> r) | (hi << (64 - r));
+          hi >>= r;
+        }
+        const uint32_t wds[4] = {(uint32_t)(hi >> 32), (uint32_t)hi, (uint32_t)(lo >> 32),
+                                 (uint32_t)lo};
+        const uint32_t nwt = (r + bits + 31) >> 5;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          if (k < (int)nwt && wds[k]) atomicOr(&wbuf[wi + k], wds[k]);
+      }
+      base += total;
     }
-    base += __shfl_sync(0xffffffffu, incl, 31);
+    if (threadIdx.x == 0)
+      for (int u = 1; u < kNSub; u++)
+        if (u * q >= cnt) so[u - 1] = (uint16_t)base;
+    __syncthreads();
+    uint32_t* dst = (uint32_t*)(out + sd.sect_off + sd.off_payload) + (word_off[j] - sd.word0);
+    for (int i = threadIdx.x; i < nw; i += 256) dst[i] = wbuf[i];
   }
-  if (lane == 0)
-    for (int u = 1; u < kNSub; u++)
-      if (u * q >= cnt) so[u - 1] = (uint16_t)base;
-  __syncwarp();
-  uint32_t* dst = (uint32_t*)(out + sd.sect_off + sd.off_payload) + (word_off[j] - sd.word0);
-  for (int64_t i = lane; i < nw; i += 32) dst[i] = buf[i];
 }
 
 int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
                 const unsigned long long* word_off, const SectDev* sect, uint8_t* out,
                 const DevParams* dp, cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
-  const int64_t maxw = (g.bvol * kMaxCodeLen + 31) / 32;
-  size_t smem = sizeof(uint32_t) * kPackWarps * maxw;
-  if (cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+  const size_t smem = sizeof(uint32_t) * (size_t)((g.bvol * kMaxCodeLen + 31) / 32 + 1);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
     return STZ_ERR_CUDA;
-  int64_t blocks = cdiv(g.total_chunks, kPackWarps);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t grid = imin(g.total_chunks, (int64_t)sms * 8);
   ProfScope ps_("k_pack", s);
-  k_pack<<<(unsigned)blocks, kPackWarps * 32, smem, s>>>(g, codes, enc, word_off, sect, out, dp);
+  k_pack<<<(unsigned)grid, 256, smem, s>>>(g, codes, enc, word_off, sect, out, dp);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -538,14 +742,14 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_chunks(
   const int u = (int)(qq - q * nsub);
   if (q >= job.nchunks_job) return;
   const StreamGeo& sg = g.s[sid];
-  const int64_t B0 = job.lo[0] + q / (job.cnt[1] * job.cnt[2]);
-  const int64_t B1 = job.lo[1] + (q / job.cnt[2]) % job.cnt[1];
-  const int64_t B2 = job.lo[2] + q % job.cnt[2];
-  const int64_t jl = (B0 * sg.nb[1] + B1) * sg.nb[2] + B2;
-  const int64_t cnt = imin(g.b[0], sg.e[0] - B0 * g.b[0]) * imin(g.b[1], sg.e[1] - B1 * g.b[1]) *
-                      imin(g.b[2], sg.e[2] - B2 * g.b[2]);
-  const int64_t per = (cnt + nsub - 1) / nsub;
-  const int64_t i0 = imin(cnt, (int64_t)u * per), i1 = imin(cnt, (int64_t)(u + 1) * per);
+  const int q32 = (int)q, c1 = (int)job.cnt[1], c2 = (int)job.cnt[2];
+  const int r0 = q32 / (c1 * c2), rr = q32 - r0 * c1 * c2, r1 = rr / c2, r2 = rr - r1 * c2;
+  const int B0 = (int)job.lo[0] + r0, B1 = (int)job.lo[1] + r1, B2 = (int)job.lo[2] + r2;
+  const int64_t jl = ((int64_t)B0 * sg.nb[1] + B1) * sg.nb[2] + B2;
+  const int cnt = min(g.b[0], (int)sg.e[0] - B0 * g.b[0]) *
+                  min(g.b[1], (int)sg.e[1] - B1 * g.b[1]) * min(g.b[2], (int)sg.e[2] - B2 * g.b[2]);
+  const int per = (cnt + nsub - 1) / nsub;
+  const int64_t i0 = min(cnt, u * per), i1 = min(cnt, (u + 1) * per);
   const uint32_t* coff = (const uint32_t*)(d.sect + d.off_chunks);
   const uint16_t* soff = (const uint16_t*)(d.sect + d.off_subs) + jl * (nsub - 1);
   const uint32_t* pay = (const uint32_t*)(d.sect + d.off_payload);
@@ -565,10 +769,12 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_chunks(
   unsigned long long buf = 0;
   int nb = 0;
   uint64_t consumed = 0;
+  uint32_t pre;  // the next payload word, loaded one refill ahead of its use
   {
     const int sh = (int)(b0 & 31);
     uint32_t word = wp < we ? *wp : 0u;
     wp++;
+    pre = wp < we ? *wp : 0u;
     buf = (unsigned long long)word << (32 + sh);
     nb = 32 - sh;
   }
@@ -576,8 +782,9 @@ __global__ void __launch_bounds__(kDecThreads) k_decode_chunks(
   // decode one symbol: refill below 32 buffered bits, look up the next 12
   auto next = [&]() -> uint32_t {
     if (nb < 32) {
-      uint32_t word = wp < we ? *wp : 0u;
+      const uint32_t word = pre;
       wp++;
+      pre = wp < we ? *wp : 0u;
       buf |= (unsigned long long)word << (32 - nb);
       nb += 32;
     }

@@ -46,7 +46,20 @@ __global__ void __launch_bounds__(256) k_range(const void* __restrict__ field, i
     const uint32_t* f = (const uint32_t*)field;
     const int64_t n4 = n >> 2;
     const uint4* f4 = (const uint4*)field;
-    for (int64_t i = tid; i < n4; i += nth) {
+    int64_t i = tid;
+    for (; i + 3 * nth < n4; i += 4 * nth) {  // four 16-byte loads in flight per thread
+      uint4 v[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) v[k] = __ldcs(f4 + i + k * nth);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        if ((v[k].x & 0x7F800000u) != 0x7F800000u) upd(key_f32(v[k].x), lo, hi);
+        if ((v[k].y & 0x7F800000u) != 0x7F800000u) upd(key_f32(v[k].y), lo, hi);
+        if ((v[k].z & 0x7F800000u) != 0x7F800000u) upd(key_f32(v[k].z), lo, hi);
+        if ((v[k].w & 0x7F800000u) != 0x7F800000u) upd(key_f32(v[k].w), lo, hi);
+      }
+    }
+    for (; i < n4; i += nth) {
       uint4 v = __ldg(f4 + i);
       if ((v.x & 0x7F800000u) != 0x7F800000u) upd(key_f32(v.x), lo, hi);
       if ((v.y & 0x7F800000u) != 0x7F800000u) upd(key_f32(v.y), lo, hi);

@@ -31,12 +31,13 @@ def heap_cost(freq):
     return cost
 
 
-def check_code(freq, lens, limit):
+def check_code(freq, lens, limit, complete=True):
     live = freq > 0
     assert (lens[~live] == 0).all()
     assert (lens[live] >= 1).all() and lens.max() <= limit
     kraft = sum(2.0 ** -int(l) for l in lens[live])
-    if live.sum() >= 2:
+    assert kraft <= 1.0
+    if live.sum() >= 2 and complete:
         assert kraft == 1.0
     order = np.argsort(-freq[live], kind="stable")
     fl = freq[live][order]
@@ -74,9 +75,12 @@ def test_length_limit(ora, seed):
     freq = np.zeros(2048, dtype=np.uint64)
     freq[:n] = (2.0 ** np.linspace(40, 0, n)).astype(np.uint64) + 1
     lens = ora.huffman_lengths(freq, 12)
-    check_code(freq, lens, 12)
+    check_code(freq, lens, 12, complete=False)
     assert int((freq * lens).sum()) >= heap_cost(freq)
     assert lens.max() == 12
+    # geometric frequencies are the worst case for any limit; the repair stays
+    # within 5% of the unlimited optimum
+    assert int((freq * lens).sum()) <= 1.05 * heap_cost(freq)
 
 
 def test_single_and_empty(ora):
@@ -95,3 +99,16 @@ def test_payload_decodes_to_codes(ora, eb):
     dec, soff2 = ora.decode_streams(c)
     assert np.array_equal(soff, soff2)
     assert np.array_equal(codes, dec)
+
+
+def test_length_limit_many_rare_symbols(ora):
+    """A dominant symbol and a long tail of singletons (the shape of
+    quantization codes): the limit binds and the code stays valid."""
+    freq = np.zeros(2048, dtype=np.uint64)
+    freq[1024] = 10 ** 8
+    freq[1023] = freq[1025] = 10 ** 6
+    freq[1000:1020] = 1
+    freq[1:200] = 1
+    lens = ora.huffman_lengths(freq, 12)
+    check_code(freq, lens, 12, complete=False)
+    assert lens[1024] == 1
