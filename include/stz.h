@@ -88,6 +88,8 @@ size_t stz_workspace_size(const int64_t* dims, int ndim, stz_dtype dtype);
  *
  * Blocks the calling thread once, at the end, to read the size back.
  * The container is bit-identical to the CPU oracle's for the same input.
+ * Size limit (here and for every decompression call): the level-1 grid,
+ * ceil(dims / 2^(L-1)) per axis, has fewer than 2^31 points, else STZ_ERR_ARG.
  */
 int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype dtype,
                  stz_eb_mode eb_mode, double eb, void* out_dev, size_t out_cap,

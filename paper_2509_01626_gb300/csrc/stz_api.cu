@@ -639,6 +639,17 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
     a.nout = (int64_t)H.d[0].nout;
     a.two_eb = H.two_eb[1];
     a.status = status;
+    // the part of level 1 the output depends on: the output box itself, or
+    // the coarse cells the level-2 box is predicted from
+    int64_t m1[3];
+    grid_extent(g.n, g.L, 1, m1);
+    bool whole = true;
+    for (int d = 0; d < 3; d++) {
+      a.rlo[d] = level == 1 ? P.OA[d] : imax(0, P.A[2][d] / 2 - 1);
+      a.rhi[d] = level == 1 ? P.OB[d] : imin(m1[d], P.B[2][d] / 2 + 2);
+      whole = whole && a.rlo[d] == 0 && a.rhi[d] == m1[d];
+    }
+    a.region = whole ? 0 : 1;
     STZ_TRY(launch_base(a, true, st));
   }
   if (level == 1) {

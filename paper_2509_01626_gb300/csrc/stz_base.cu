@@ -23,7 +23,17 @@ struct PassGeo {
   int64_t total;
   int axis;
   int64_t t;
-  int origin;  // the single point 0, predicted as 0
+  int origin;      // the single point 0, predicted as 0
+  FastDiv c2, c1;  // cnt[2], cnt[1]
+};
+
+// A coarse pass in units of the shared-memory subgrid (every ts-th point).
+struct SubPass {
+  int start[3], step[3];
+  FastDiv c2, c1;  // cnt[2], cnt[1]
+  int total, axis;
+  int t, st, m;    // pass stride, element stride and extent along the axis, in subgrid units
+  int origin;
 };
 
 template <typename T, bool DEC>
@@ -79,10 +89,16 @@ __global__ void __launch_bounds__(256) k_base_pass(BaseArgs a, PassGeo p) {
 // Level-1 values written by other blocks are read with L2-only loads (__ldcg),
 // never through a possibly stale L1 line.
 constexpr int kMaxPasses = 64;
+constexpr int64_t kLocalPoints = 32768;  // fine-pass points kept in the single block
 struct PassList {
   PassGeo p[kMaxPasses];
+  SubPass sp[kMaxPasses];  // the first nsmall passes in subgrid units
   int npass, nsmall;
-  int64_t ts;  // stride of the subgrid held in shared memory by the coarse phase
+  int nlocal;              // passes run by the single-block kernel (nsmall <= nlocal <= npass)
+  int ts;                  // stride of the subgrid held in shared memory by the coarse phase
+  int sm[3];               // subgrid extent
+  FastDiv fsm2, fsm1;      // sm[2], sm[1]
+  FastDiv bd[3];           // brick extents of stream 0
 };
 
 template <typename T>
@@ -104,9 +120,10 @@ struct Addr32 {
   int64_t slot, pos;
   int chunk;
 };
-__device__ __forceinline__ Addr32 addr0(const StreamGeo& sg, const int32_t b[3], int bvol,
-                                        const SlotMap& sm, int c0, int c1, int c2) {
-  const int B0 = c0 / b[0], B1 = c1 / b[1], B2 = c2 / b[2];
+__device__ __forceinline__ Addr32 addr0(const StreamGeo& sg, const int32_t b[3],
+                                        const FastDiv bd[3], int bvol, const SlotMap& sm, int c0,
+                                        int c1, int c2) {
+  const int B0 = (int)fdiv(c0, bd[0]), B1 = (int)fdiv(c1, bd[1]), B2 = (int)fdiv(c2, bd[2]);
   const int e0 = (int)sg.e[0], e1 = (int)sg.e[1], e2 = (int)sg.e[2];
   const int l0 = min(b[0], e0 - B0 * b[0]), l1 = min(b[1], e1 - B1 * b[1]),
             l2 = min(b[2], e2 - B2 * b[2]);
@@ -122,12 +139,12 @@ __device__ __forceinline__ Addr32 addr0(const StreamGeo& sg, const int32_t b[3],
 }
 
 template <typename T, bool DEC>
-__device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p, int64_t i64,
-                                           const int64_t m[3], int64_t s1, const QConst<T>& q) {
+__device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p,
+                                           const FastDiv bd[3], unsigned i, const int64_t m[3],
+                                           int64_t s1, const QConst<T>& q) {
   const Geo& geo = a.geo;
-  const unsigned i = (unsigned)i64, n2 = (unsigned)p.cnt[2], n1 = (unsigned)p.cnt[1];
-  const unsigned r = i / n2;
-  const int i2 = (int)(i - r * n2), i1 = (int)(r % n1), i0 = (int)(r / n1);
+  const unsigned r = fdiv(i, p.c2), i0 = fdiv(r, p.c1);
+  const int i2 = (int)(i - r * p.c2.d), i1 = (int)(r - i0 * p.c1.d);
   const int g0 = (int)p.start[0] + i0 * (int)p.step[0];
   const int g1 = (int)p.start[1] + i1 * (int)p.step[1];
   const int g2 = (int)p.start[2] + i2 * (int)p.step[2];
@@ -139,7 +156,7 @@ __device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p, 
     const int64_t c = p.axis == 0 ? g0 : (p.axis == 1 ? g1 : g2);
     pred = base_predict_cg(grid, idx, st, c, p.t, m[p.axis]);
   }
-  const Addr32 ad = addr0(geo.s[0], geo.b, (int)geo.bvol, a.sm, g0, g1, g2);
+  const Addr32 ad = addr0(geo.s[0], geo.b, bd, (int)geo.bvol, a.sm, g0, g1, g2);
   if (!DEC) {
     const T* f = (const T*)a.field;
     T x = f[(((int64_t)g0 * s1) * geo.n[1] + (int64_t)g1 * s1) * geo.n[2] + (int64_t)g2 * s1];
@@ -164,61 +181,55 @@ __device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p, 
 }
 
 // Coarse phase in shared memory: every pass with stride t >= ts touches only
-// points of the stride-ts subgrid (extent sm = ceil(m / ts)), which block 0
-// keeps in shared memory; those passes run there with block barriers and
-// the subgrid is then written to the level-1 grid.  The remaining passes
+// points of the stride-ts subgrid (extent sm = ceil(m / ts)), which one block
+// keeps in shared memory together with the points' codes; those passes run
+// there with block barriers in 32-bit subgrid coordinates, and the subgrid
+// (and, compressing, its codes) is then written out.  The remaining passes
 // (t < ts) are spread over the grid with a grid barrier before each.
 template <typename T, bool DEC>
 __device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint16_t* sc,
-                             int64_t ts, const int64_t sm[3], const int64_t m[3], int64_t s1,
-                             const QConst<T>& q) {
+                             const int64_t m[3], int64_t s1, const QConst<T>& q) {
   const Geo& geo = a.geo;
-  const int64_t nsg = sm[0] * sm[1] * sm[2];
-  // gather the subgrid's inputs first, all loads in flight: the field values
+  const int ts = pl.ts, sm1 = pl.sm[1], sm2 = pl.sm[2];
+  const int nsg = pl.sm[0] * sm1 * sm2;
+  // gather the subgrid's inputs, all loads in flight: the field values
   // (compress) or the codes (decode)
-  for (int i = threadIdx.x; i < (int)nsg; i += blockDim.x) {
-    const int x = i % (int)sm[2], y = (i / (int)sm[2]) % (int)sm[1], z = i / (int)(sm[1] * sm[2]);
-    const int g0 = z * (int)ts, g1 = y * (int)ts, g2 = x * (int)ts;
+  for (int i = threadIdx.x; i < nsg; i += blockDim.x) {
+    const unsigned r = fdiv((unsigned)i, pl.fsm2), z = fdiv(r, pl.fsm1);
+    const int x = i - (int)r * sm2, y = (int)r - (int)z * sm1;
+    const int g0 = (int)z * ts, g1 = y * ts, g2 = x * ts;
     if (!DEC) {
       sg[i] = ((const T*)a.field)[(((int64_t)g0 * s1) * geo.n[1] + (int64_t)g1 * s1) * geo.n[2] +
                                   (int64_t)g2 * s1];
     } else {
-      sc[i] = a.codes[addr0(geo.s[0], geo.b, (int)geo.bvol, a.sm, g0, g1, g2).slot];
+      sc[i] = a.codes[addr0(geo.s[0], geo.b, pl.bd, (int)geo.bvol, a.sm, g0, g1, g2).slot];
     }
   }
   __syncthreads();
   for (int k = 0; k < pl.nsmall; k++) {
-    const PassGeo& p = pl.p[k];
-    const unsigned n2 = (unsigned)p.cnt[2], n1 = (unsigned)p.cnt[1];
-    for (int i = threadIdx.x; i < (int)p.total; i += blockDim.x) {
-      const unsigned r = (unsigned)i / n2;
-      const int i2 = (int)((unsigned)i - r * n2), i1 = (int)(r % n1), i0 = (int)(r / n1);
-      const int g[3] = {(int)p.start[0] + i0 * (int)p.step[0],
-                        (int)p.start[1] + i1 * (int)p.step[1],
-                        (int)p.start[2] + i2 * (int)p.step[2]};
-      const int tsi = (int)ts;
-      const int64_t si = ((int64_t)(g[0] / tsi) * sm[1] + g[1] / tsi) * sm[2] + g[2] / tsi;
+    const SubPass& p = pl.sp[k];
+    for (int i = threadIdx.x; i < p.total; i += blockDim.x) {
+      const unsigned r = fdiv((unsigned)i, p.c2), i0 = fdiv(r, p.c1);
+      const int i2 = i - (int)(r * p.c2.d), i1 = (int)(r - i0 * p.c1.d);
+      const int z = p.start[0] + (int)i0 * p.step[0], y = p.start[1] + i1 * p.step[1],
+                x = p.start[2] + i2 * p.step[2];
+      const int si = (z * sm1 + y) * sm2 + x;
       T pred = T(0);
       if (!p.origin) {
-        const int ax = p.axis;
-        const int64_t st = ax == 0 ? sm[1] * sm[2] : (ax == 1 ? sm[2] : 1);
-        // the subgrid holds every ts-th point: pass stride t is t/ts subgrid steps
-        pred = base_predict(sg, si, st, g[ax] / ts, p.t / ts, sm[ax]);
-        (void)m;
+        const int c = p.axis == 0 ? z : (p.axis == 1 ? y : x);
+        pred = base_predict<T, int>(sg, si, p.st, c, p.t, p.m);
       }
       if (!DEC) {
-        const Addr32 ad = addr0(geo.s[0], geo.b, (int)geo.bvol, a.sm, g[0], g[1], g[2]);
-        const T x = sg[si];  // still the field value: this point is visited once
         T xr;
-        const int sym = quantize(x, pred, q, kRadius, xr);
+        const int sym = quantize(sg[si], pred, q, kRadius, xr);  // sg[si] is still the input
         sg[si] = xr;
-        a.codes[ad.slot] = (uint16_t)sym;
-        if (sym == 0) atomicAdd(&a.chunk_outliers[geo.s[0].chunk0 + ad.chunk], 1u);
+        sc[si] = (uint16_t)sym;
       } else {
         const int sym = sc[si];
         T v;
         if (sym == 0) {
-          const Addr32 ad = addr0(geo.s[0], geo.b, (int)geo.bvol, a.sm, g[0], g[1], g[2]);
+          const Addr32 ad =
+              addr0(geo.s[0], geo.b, pl.bd, (int)geo.bvol, a.sm, z * ts, y * ts, x * ts);
           if (!find_outlier(a.opos, (const T*)a.oval, a.nout, ad.pos, v)) {
             v = T(0);
             atomicOr(a.status, kStatCorrupt);
@@ -231,11 +242,19 @@ __device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint1
     }
     __syncthreads();
   }
-  // write the subgrid to the level-1 grid
+  // write the subgrid to the level-1 grid, and compressing its codes
   T* grid = (T*)a.g1;
-  for (int64_t i = threadIdx.x; i < nsg; i += blockDim.x) {
-    const int64_t x = i % sm[2], y = (i / sm[2]) % sm[1], z = i / (sm[1] * sm[2]);
-    __stcg(grid + ((z * ts) * m[1] + y * ts) * m[2] + x * ts, sg[i]);
+  for (int i = threadIdx.x; i < nsg; i += blockDim.x) {
+    const unsigned r = fdiv((unsigned)i, pl.fsm2), z = fdiv(r, pl.fsm1);
+    const int x = i - (int)r * sm2, y = (int)r - (int)z * sm1;
+    const int g0 = (int)z * ts, g1 = y * ts, g2 = x * ts;
+    __stcg(grid + ((int64_t)g0 * m[1] + g1) * m[2] + g2, sg[i]);
+    if (!DEC) {
+      const Addr32 ad = addr0(geo.s[0], geo.b, pl.bd, (int)geo.bvol, a.sm, g0, g1, g2);
+      const uint16_t sym = sc[i];
+      a.codes[ad.slot] = sym;
+      if (sym == 0) atomicAdd(&a.chunk_outliers[geo.s[0].chunk0 + ad.chunk], 1u);
+    }
   }
 }
 
@@ -248,12 +267,18 @@ __global__ void __launch_bounds__(1024) k_base_coarse(const __grid_constant__ Ba
   const int64_t s1 = level_stride(a.geo.L, 1);
   QConst<T> q;
   if (!DEC) q.load(a.dp, 1, kRadius);
-  const int64_t ts = pl.ts;
-  const int64_t sm[3] = {cdiv(m[0], ts), cdiv(m[1], ts), cdiv(m[2], ts)};
-  const int64_t nsg = sm[0] * sm[1] * sm[2];
+  const int nsg = pl.sm[0] * pl.sm[1] * pl.sm[2];
   T* sg = (T*)smem_raw;
   uint16_t* sc = (uint16_t*)(smem_raw + sizeof(T) * nsg);
-  coarse_phase<T, DEC>(a, pl, sg, sc, ts, sm, m, s1, q);
+  coarse_phase<T, DEC>(a, pl, sg, sc, m, s1, q);
+  // small remaining passes (a region's dependencies) in this block: global
+  // writes are visible to the block after the barrier
+  for (int k = pl.nsmall; k < pl.nlocal; k++) {
+    __syncthreads();
+    const PassGeo& p = pl.p[k];
+    for (int i = threadIdx.x; i < (int)p.total; i += blockDim.x)
+      base_point<T, DEC>(a, p, pl.bd, (unsigned)i, m, s1, q);
+  }
 }
 
 template <typename T, bool DEC>
@@ -265,12 +290,12 @@ __global__ void __launch_bounds__(256) k_base_coop(const __grid_constant__ BaseA
   const int64_t s1 = level_stride(a.geo.L, 1);
   QConst<T> q;
   if (!DEC) q.load(a.dp, 1, kRadius);
-  for (int k = pl.nsmall; k < pl.npass; k++) {
-    if (k > pl.nsmall) grid.sync();
+  for (int k = pl.nlocal; k < pl.npass; k++) {
+    if (k > pl.nlocal) grid.sync();
     const PassGeo& p = pl.p[k];
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.total; i += nth)
-      base_point<T, DEC>(a, p, i, m, s1, q);
+      base_point<T, DEC>(a, p, pl.bd, (unsigned)i, m, s1, q);
   }
 }
 
@@ -281,6 +306,7 @@ template <typename T, bool DEC>
 static int run_coop(const BaseArgs& a, cudaStream_t s) {
   int64_t m[3];
   grid_extent(a.geo.n, a.geo.L, 1, m);
+  if (m[0] * m[1] * m[2] >= ((int64_t)1 << 31)) return STZ_ERR_ARG;  // 32-bit level-1 indexing
   int64_t mx = imax(m[0], imax(m[1], m[2]));
   int64_t T_ = 1;
   while (T_ < mx) T_ <<= 1;
@@ -327,16 +353,85 @@ static int run_coop(const BaseArgs& a, cudaStream_t s) {
       biggest = imax(biggest, p.total);
     }
   }
+  // a region decode runs only what the box [rlo, rhi) depends on: walking the
+  // passes backwards, pass k is cut to the current box, which then grows by
+  // 3t along the pass axis (the reach of its predictor) for the passes before
+  if (a.region) {
+    int64_t lo[3], hi[3];
+    for (int b = 0; b < 3; b++) {
+      lo[b] = imax(0, a.rlo[b]);
+      hi[b] = imin(m[b], a.rhi[b]);
+    }
+    for (int k = pl.npass - 1; k >= 0; k--) {
+      PassGeo& p = pl.p[k];
+      p.total = 1;
+      for (int b = 0; b < 3; b++) {
+        const int64_t i0 = lo[b] > p.start[b] ? cdiv(lo[b] - p.start[b], p.step[b]) : 0;
+        const int64_t i1 =
+            hi[b] > p.start[b] ? imin(p.cnt[b], cdiv(hi[b] - p.start[b], p.step[b])) : 0;
+        p.start[b] += i0 * p.step[b];
+        p.cnt[b] = imax(0, i1 - i0);
+        p.total *= p.cnt[b];
+      }
+      if (!p.origin) {
+        lo[p.axis] = imax(0, lo[p.axis] - 3 * p.t);
+        hi[p.axis] = imin(m[p.axis], hi[p.axis] + 3 * p.t);
+      }
+    }
+    int n = 0;
+    biggest = 1;
+    for (int k = 0; k < pl.npass; k++)
+      if (pl.p[k].total > 0) {
+        pl.p[n++] = pl.p[k];
+        biggest = imax(biggest, pl.p[k].total);
+      }
+    pl.npass = n;
+    if (n == 0) return STZ_OK;
+  }
   // coarse phase: the passes with t >= ts, ts the smallest power of two whose
   // subgrid fits in 128 KiB of shared memory
   const int64_t cap = (128 * 1024) / (int64_t)sizeof(T);
   int64_t ts = 1;
   while (cdiv(m[0], ts) * cdiv(m[1], ts) * cdiv(m[2], ts) > cap) ts <<= 1;
-  pl.ts = ts;
+  pl.ts = (int)ts;
   pl.nsmall = 0;
   while (pl.nsmall < pl.npass && (pl.p[pl.nsmall].origin || pl.p[pl.nsmall].t >= ts)) pl.nsmall++;
-  const size_t nsg = (size_t)(cdiv(m[0], ts) * cdiv(m[1], ts) * cdiv(m[2], ts));
-  const size_t smem = sizeof(T) * nsg + (DEC ? sizeof(uint16_t) * nsg : 0);
+  for (int k = 0; k < pl.npass; k++) {
+    pl.p[k].c2 = make_fastdiv((uint32_t)pl.p[k].cnt[2]);
+    pl.p[k].c1 = make_fastdiv((uint32_t)pl.p[k].cnt[1]);
+  }
+  for (int b = 0; b < 3; b++) {
+    pl.sm[b] = (int)cdiv(m[b], ts);
+    pl.bd[b] = make_fastdiv((uint32_t)a.geo.b[b]);
+  }
+  pl.fsm2 = make_fastdiv((uint32_t)pl.sm[2]);
+  pl.fsm1 = make_fastdiv((uint32_t)pl.sm[1]);
+  for (int k = 0; k < pl.nsmall; k++) {
+    const PassGeo& p = pl.p[k];
+    SubPass& q = pl.sp[k];
+    for (int b = 0; b < 3; b++) {
+      q.start[b] = (int)(p.start[b] / ts);
+      q.step[b] = (int)(p.step[b] / ts);  // 0 only for the origin, whose counts are 1
+    }
+    q.c2 = p.c2;
+    q.c1 = p.c1;
+    q.total = (int)p.total;
+    q.axis = p.axis;
+    q.t = (int)(p.t / ts);
+    q.st = p.axis == 0 ? pl.sm[1] * pl.sm[2] : (p.axis == 1 ? pl.sm[2] : 1);
+    q.m = pl.sm[p.axis];
+    q.origin = p.origin;
+  }
+  // the passes after the coarse phase stay in the single block while they are
+  // a few rounds of its threads each (a grid barrier costs more)
+  pl.nlocal = pl.nsmall;
+  {
+    int64_t rest = 0;
+    for (int k = pl.nsmall; k < pl.npass; k++) rest += pl.p[k].total;
+    if (rest <= kLocalPoints) pl.nlocal = pl.npass;
+  }
+  const size_t nsg = (size_t)pl.sm[0] * pl.sm[1] * pl.sm[2];
+  const size_t smem = (sizeof(T) + sizeof(uint16_t)) * nsg;
   {
     auto ck = k_base_coarse<T, DEC>;
     if (cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -346,7 +441,9 @@ static int run_coop(const BaseArgs& a, cudaStream_t s) {
     ck<<<1, 1024, smem, s>>>(a, pl);
     if (cudaGetLastError() != cudaSuccess) return STZ_ERR_CUDA;
   }
-  if (pl.nsmall == pl.npass) return STZ_OK;
+  if (pl.nlocal == pl.npass) return STZ_OK;
+  biggest = 1;
+  for (int k = pl.nlocal; k < pl.npass; k++) biggest = imax(biggest, pl.p[k].total);
   auto kern = k_base_coop<T, DEC>;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -363,7 +460,7 @@ static int run_coop(const BaseArgs& a, cudaStream_t s) {
   }
   if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
     cudaGetLastError();  // clear, then one launch per remaining pass
-    for (int k = pl.nsmall; k < pl.npass; k++) {
+    for (int k = pl.nlocal; k < pl.npass; k++) {
       const PassGeo& p = pl.p[k];
       ProfScope ps_(DEC ? "k_base_pass_dec" : "k_base_pass_enc", s);
       k_base_pass<T, DEC><<<(unsigned)cdiv(p.total, 256), 256, 0, s>>>(a, p);

@@ -41,6 +41,26 @@ constexpr uint32_t kStatCapacity = 2u;
 
 #define STZ_HD __host__ __device__ __forceinline__
 
+// Division of n in [0, 2^32) by a divisor d >= 1 fixed before the launch: a
+// multiply-high, an add and a shift (the round-up method of Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994:
+// with l = ceil(log2 d) and mul = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (mulhi(mul, n) + n) >> l exactly).
+struct FastDiv {
+  uint32_t d, mul, sh;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.sh = 0;
+  while ((1ull << f.sh) < d) f.sh++;
+  f.mul = (uint32_t)(((1ull << 32) * ((1ull << f.sh) - d)) / d + 1);
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  return (uint32_t)(((unsigned long long)__umulhi(n, f.mul) + n) >> f.sh);
+}
+
 STZ_HD int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 STZ_HD int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
 STZ_HD int64_t imax(int64_t a, int64_t b) { return a > b ? a : b; }

@@ -26,6 +26,8 @@ struct BaseArgs {
   int64_t nout;
   double two_eb;              // decode: 2 eb_1 in the field precision
   uint32_t* status;           // decode: corrupt flag
+  int region;                 // decode: only the box [rlo, rhi) of the level-1 grid is needed
+  int64_t rlo[3], rhi[3];
 };
 int launch_base(const BaseArgs& a, bool decode, cudaStream_t s);
 int launch_base_passes(const BaseArgs& a, bool decode, cudaStream_t s);

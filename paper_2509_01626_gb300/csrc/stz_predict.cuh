@@ -120,11 +120,11 @@ __device__ __forceinline__ T level_predict(const T* __restrict__ t, I base, cons
 // Base coder (level 1, SZ3-style 1D interpolation): point at index `idx` of
 // the level-1 grid, coordinate c along the pass axis (grid stride `st`
 // elements per unit), pass stride t, extent m along the axis.  Cubic when
-// -3t..+3t fit, else midpoint, else extrapolation, else copy.
-template <typename T>
-__device__ __forceinline__ T base_predict(const T* __restrict__ g1, int64_t idx, int64_t st,
-                                          int64_t c, int64_t t, int64_t m) {
-  const int64_t d = t * st;
+// -3t..+3t fit, else midpoint, else extrapolation, else copy.  I is the index
+// type (int for a grid held in shared memory).
+template <typename T, typename I>
+__device__ __forceinline__ T base_predict(const T* __restrict__ g1, I idx, I st, I c, I t, I m) {
+  const I d = t * st;
   T vm1 = g1[idx - d];
   bool p1 = c + t < m, m3 = c - 3 * t >= 0, p3 = c + 3 * t < m;
   if (m3 && p3) return cubic_1d(g1[idx - 3 * d], vm1, g1[idx + d], g1[idx + 3 * d]);

@@ -201,3 +201,32 @@ def test_full_size_512_grf(stzg, ora):
         r = stzg.decompress_region(comp, lo, hi, 3).cpu().numpy()
         sl = tuple(slice(a, b) for a, b in zip(lo, hi))
         assert np.array_equal(_bits(r), _bits(np.ascontiguousarray(recon[sl])))
+
+
+def test_region_dependencies_256_grf(stzg, ora):
+    """A region decode runs only the level-1 passes the box depends on (cut
+    backwards pass by pass, the box growing by the predictor's reach 3t);
+    small remainders run in the single coarse block, large ones grid-wide.
+    Corner, face, single-point, thin and almost-whole boxes at every level
+    equal slices of the oracle's full decode."""
+    shape = (256, 256, 256)
+    x = synth.grf(shape, synth.seed_for(2, 1))
+    ref = ora.compress(x, 1e-3, "rel")
+    full = ora.decompress(ref)
+    comp = torch.from_numpy(ref).cuda()
+    boxes = [((0, 0, 0), (1, 1, 1)), ((255, 255, 255), (256, 256, 256)),
+             ((0, 0, 0), (256, 256, 256)), ((1, 1, 1), (256, 256, 256)),
+             ((0, 0, 0), (255, 255, 255)), ((100, 0, 37), (101, 256, 38)),
+             ((0, 128, 0), (256, 129, 256)), ((3, 5, 7), (9, 250, 11)),
+             ((120, 120, 120), (136, 136, 136)), ((0, 0, 200), (256, 256, 256)),
+             ((250, 0, 0), (256, 6, 256))]
+    boxes += synth.random_boxes(shape, 8, 4321, 1, 200)
+    for level in (1, 2, 3):
+        s = 1 << (3 - level)
+        for lo, hi in boxes:
+            sl = tuple(slice(-(-a // s) * s, b, s) for a, b in zip(lo, hi))
+            want = np.ascontiguousarray(full[sl])
+            if want.size == 0:
+                continue
+            r = stzg.decompress_region(comp, lo, hi, level).cpu().numpy()
+            assert np.array_equal(_bits(r), _bits(want)), (lo, hi, level)
