@@ -192,17 +192,53 @@ __device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint1
   const Geo& geo = a.geo;
   const int ts = pl.ts, sm1 = pl.sm[1], sm2 = pl.sm[2];
   const int nsg = pl.sm[0] * sm1 * sm2;
-  // gather the subgrid's inputs, all loads in flight: the field values
-  // (compress) or the codes (decode)
-  for (int i = threadIdx.x; i < nsg; i += blockDim.x) {
-    const unsigned r = fdiv((unsigned)i, pl.fsm2), z = fdiv(r, pl.fsm1);
-    const int x = i - (int)r * sm2, y = (int)r - (int)z * sm1;
-    const int g0 = (int)z * ts, g1 = y * ts, g2 = x * ts;
+  // gather the subgrid's inputs, kGather independent loads in flight per
+  // thread: the field values (compress) or the codes (decode); an outlier's
+  // value is looked up here, off the passes' critical path
+  constexpr int kGather = 8;
+  for (int i0 = threadIdx.x; i0 < nsg; i0 += kGather * blockDim.x) {
+    int64_t src[kGather];
+    int pos[kGather];
+#pragma unroll
+    for (int u = 0; u < kGather; u++) {
+      const int i = i0 + u * blockDim.x;
+      const int ic = i < nsg ? i : 0;
+      const unsigned r = fdiv((unsigned)ic, pl.fsm2), z = fdiv(r, pl.fsm1);
+      const int x = ic - (int)r * sm2, y = (int)r - (int)z * sm1;
+      const int g0 = (int)z * ts, g1 = y * ts, g2 = x * ts;
+      if (!DEC) {
+        src[u] = (((int64_t)g0 * s1) * geo.n[1] + (int64_t)g1 * s1) * geo.n[2] + (int64_t)g2 * s1;
+      } else {
+        const Addr32 ad = addr0(geo.s[0], geo.b, pl.bd, (int)geo.bvol, a.sm, g0, g1, g2);
+        src[u] = ad.slot;
+        pos[u] = (int)ad.pos;
+      }
+    }
     if (!DEC) {
-      sg[i] = ((const T*)a.field)[(((int64_t)g0 * s1) * geo.n[1] + (int64_t)g1 * s1) * geo.n[2] +
-                                  (int64_t)g2 * s1];
+      T v[kGather];
+#pragma unroll
+      for (int u = 0; u < kGather; u++) v[u] = ((const T*)a.field)[src[u]];
+#pragma unroll
+      for (int u = 0; u < kGather; u++)
+        if (i0 + u * (int)blockDim.x < nsg) sg[i0 + u * blockDim.x] = v[u];
     } else {
-      sc[i] = a.codes[addr0(geo.s[0], geo.b, pl.bd, (int)geo.bvol, a.sm, g0, g1, g2).slot];
+      uint16_t c[kGather];
+#pragma unroll
+      for (int u = 0; u < kGather; u++) c[u] = a.codes[src[u]];
+#pragma unroll
+      for (int u = 0; u < kGather; u++) {
+        const int i = i0 + u * blockDim.x;
+        if (i >= nsg) continue;
+        sc[i] = c[u];
+        if (c[u] == 0) {
+          T v;
+          if (!find_outlier(a.opos, (const T*)a.oval, a.nout, (int64_t)pos[u], v)) {
+            v = T(0);
+            atomicOr(a.status, kStatCorrupt);
+          }
+          sg[i] = v;
+        }
+      }
     }
   }
   __syncthreads();
@@ -226,18 +262,8 @@ __device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint1
         sc[si] = (uint16_t)sym;
       } else {
         const int sym = sc[si];
-        T v;
-        if (sym == 0) {
-          const Addr32 ad =
-              addr0(geo.s[0], geo.b, pl.bd, (int)geo.bvol, a.sm, z * ts, y * ts, x * ts);
-          if (!find_outlier(a.opos, (const T*)a.oval, a.nout, ad.pos, v)) {
-            v = T(0);
-            atomicOr(a.status, kStatCorrupt);
-          }
-        } else {
-          v = dequantize(sym, pred, (T)a.two_eb, kRadius);
-        }
-        sg[si] = v;
+        if (sym != 0) sg[si] = dequantize(sym, pred, (T)a.two_eb, kRadius);
+        // an outlier's value was placed by the gather
       }
     }
     __syncthreads();
