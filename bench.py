@@ -138,29 +138,11 @@ def step_boxes(size):
     return box, slab
 
 
-def algorithmic_bytes(size, comp_bytes):
-    """Compulsory bytes per launch of the main kernels (512^3-style cube,
-    L = 3): every input read once, every output written once."""
-    n = size ** 3
-    m2 = -(-size // 2)
-    m1 = -(-size // 4)
-    g2, g1 = m2 ** 3, m1 ** 3
-    n3, n2 = n - g2, g2 - g1
-    return {
-        "k_range": 4 * n,
-        "k_level3_enc_f32": 4 * n3 + 4 * g2 + 2 * n3,
-        "k_level3_dec_f32": 2 * n3 + 4 * g2 + 4 * n,
-        "k_level2_enc_f32": 4 * n2 + 4 * g1 + 2 * n2 + 4 * g2,
-        "k_level2_dec_f32": 2 * n2 + 4 * g1 + 4 * g2,
-        "k_chunk_words": 2 * n,
-        "k_pack": 2 * n + comp_bytes,
-        "k_decode_chunks": comp_bytes + 2 * n,
-    }
-
-
-def traffic_from_profiles(kernel):
-    """ncu DRAM bytes per launch for `kernel`, if a capture of the current
-    source is committed under profiles/ (else None)."""
+def traffic_ratio(kernel):
+    """DRAM bytes per algorithmic byte of `kernel` from the committed ncu
+    capture summary, if that capture was taken of the current sources (else
+    None).  profiles/ncu_traffic.json: kernel -> {"sources": [...],
+    "sources_sha256": ..., "dram_bytes": D, "algo_bytes": A, "capture": ...}."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -169,13 +151,16 @@ def traffic_from_profiles(kernel):
     e = d.get(kernel)
     if not e:
         return None
-    src = os.path.join(ROOT, e["source"])
-    if not os.path.exists(src):
+    h = hashlib.sha256()
+    for src in e["sources"]:
+        full = os.path.join(ROOT, src)
+        if not os.path.exists(full):
+            return None
+        with open(full, "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != e["sources_sha256"]:
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if h != e["source_sha256"]:
-        return None
-    return float(e["dram_bytes_per_launch"])
+    return float(e["dram_bytes"]) / float(e["algo_bytes"])
 
 
 # ------------------------------------------------------------------ our arm
@@ -239,6 +224,11 @@ def run_ours(args, rank, world, local_rank):
     clocks.start()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     launches0 = stz.launch_count()
+    # per-kernel device times and algorithmic bytes over the timed steps
+    # (an event pair around every launch, on the launching stream)
+    if not args.no_profile:
+        stz.profile_reset()
+        stz.profile_enable(True)
     barrier()
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -250,6 +240,10 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     launches = stz.launch_count() - launches0
+    kernels = {}
+    if not args.no_profile:
+        stz.profile_enable(False)
+        kernels = stz.profile_read()
     ms_step = t0.elapsed_time(t1) / args.steps
     clk = clocks.stop()
     if dist:
@@ -275,17 +269,6 @@ def run_ours(args, rank, world, local_rank):
         stz.decompress_region(comp, lo, hi, int(lv), out=reg_out, workspace=ws, meta=meta)
         lat.append((time.perf_counter() - a) * 1e3)
     lat = np.array(lat)
-
-    # live per-kernel device times (CUDA events on the launching stream)
-    kernels = {}
-    if not args.no_profile:
-        stz.profile_reset()
-        stz.profile_enable(True)
-        for _ in range(args.steps):
-            step()
-        torch.cuda.synchronize()
-        stz.profile_enable(False)
-        kernels = stz.profile_read()
 
     # end to end through the same calls, host buffers, copies timed
     e2e = None
@@ -457,26 +440,29 @@ def main():
     value = world * fb / (r["ms_step"] * 1e-3) / 1e9
     op = r["op_ms"]
     kern = r["kernels"]
-    algo = algorithmic_bytes(args.size, r["comp_bytes"])
     breakdown = []
     total_ms = sum(v[1] for v in kern.values()) or 1.0
-    for name, (cnt, ms) in sorted(kern.items(), key=lambda kv: -kv[1][1]):
+    for name, (cnt, ms, nbytes) in sorted(kern.items(), key=lambda kv: -kv[1][1]):
         e = {"kernel": name, "launches_per_step": round(cnt / args.steps, 2),
              "ms_per_step": round(ms / args.steps, 4), "share": round(ms / total_ms, 4)}
-        if name in algo and cnt:
-            e["achieved_gbs"] = round(algo[name] / (ms / cnt * 1e-3) / 1e9, 1)
+        if nbytes > 0 and ms > 0:
+            e["achieved_gbs"] = round(nbytes / (ms * 1e-3) / 1e9, 1)
         breakdown.append(e)
+    # the dominant kernel with an algorithmic-byte figure: achieved = its
+    # bytes over all timed launches / its summed launch time
     roofline = None
-    cand = [b for b in breakdown if b["kernel"] in algo]
+    cand = [b for b in breakdown if "achieved_gbs" in b]
     if cand:
         top = cand[0]
-        cnt, ms = kern[top["kernel"]]
-        ach = algo[top["kernel"]] / (ms / cnt * 1e-3) / 1e9
+        cnt, ms, nbytes = kern[top["kernel"]]
+        ach = nbytes / (ms * 1e-3) / 1e9
+        ratio = traffic_ratio(top["kernel"])
         roofline = {"kernel": top["kernel"], "bound": "hbm", "achieved": round(ach, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                     "peak_source": f"{peak_kind} HBM copy bandwidth",
-                    "traffic": traffic_from_profiles(top["kernel"]),
-                    "algorithmic_bytes_per_launch": int(algo[top["kernel"]])}
+                    "traffic": None if ratio is None else int(ratio * nbytes / cnt),
+                    "algorithmic_bytes_per_launch": int(nbytes / cnt),
+                    "launches_per_step": round(cnt / args.steps, 2)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(r["x_host"], args.eb)

@@ -144,11 +144,14 @@ int stz_decompress_region(const void* comp_dev, size_t comp_bytes, const int64_t
  * Every kernel launch of the library is counted.  With profiling enabled an
  * event pair is recorded around each launch on its stream; stz_profile_read
  * waits for those events and returns, per kernel name, the number of timed
- * launches and their summed device time.  Off by default. */
+ * launches, their summed device time and their summed algorithmic bytes
+ * (what the launches must read and write at the least: inputs once, outputs
+ * once; 0 for kernels without such a figure).  Off by default. */
 typedef struct {
   char name[48];
   unsigned long long launches;
   double total_ms;
+  double algo_bytes;
 } stz_kernel_time;
 
 unsigned long long stz_launch_count(void);

@@ -489,13 +489,16 @@ int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype
   STZ_TRY(launch_sections(g, lay, books, word_off, dp, out, st));
   STZ_TRY(launch_pack(g, codes, enc, word_off, lay->s, out, dp, st));
   STZ_TRY(launch_outliers(g, codes, field_dev, chunk_out, out_off, lay, dp, out, st));
-  unsigned long long total = 0;
+  unsigned long long total = 0, payload_words = 0;
   uint32_t status = 0;
   STZ_TRY(cuda_ok(cudaMemcpyAsync(&total, &lay->total, 8, cudaMemcpyDeviceToHost, st)));
+  STZ_TRY(cuda_ok(cudaMemcpyAsync(&payload_words, word_off + g.total_chunks, 8,
+                                  cudaMemcpyDeviceToHost, st)));
   STZ_TRY(cuda_ok(cudaMemcpyAsync(&status, &dp->status, 4, cudaMemcpyDeviceToHost, st)));
   STZ_TRY(cuda_ok(cudaStreamSynchronize(st)));
 #undef STZ_TRY
   *out_bytes = (size_t)total;
+  prof_add_bytes("k_pack", 4.0 * (double)payload_words);
   (void)ps;
   if (status & kStatCapacity) return STZ_ERR_CAPACITY;
   return STZ_OK;
@@ -575,7 +578,7 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
   uint8_t* ws = (uint8_t*)ws_dev;
   DevParams* dp = (DevParams*)(ws + P.dp);
   uint16_t* codes = (uint16_t*)(ws + P.codes);
-  uint32_t* lut = (uint32_t*)(ws + P.lut);
+  uint16_t* lut = (uint16_t*)(ws + P.lut);
   uint32_t* status = &dp->status;
   const uint8_t* comp = (const uint8_t*)comp_dev;
   // decode tables
@@ -597,6 +600,7 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
   }
   const int ns_needed = 1 + 7 * (level - 1);
   int64_t nblocks = 0;
+  double dec_bytes = 0.0;
   for (int s = 0; s < ns_needed; s++) {
     if (g.s[s].nsym == 0) continue;
     tb.lut_sid[tb.nlut++] = s;
@@ -611,6 +615,10 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
     }
     jb.slot_base = sm.base;
     jb.nchunks_job = c;
+    // the job's share of the stream's codes (written) and payload (read)
+    if (H.d[s].nch > 0)
+      dec_bytes += (2.0 * (double)H.d[s].nsym + 4.0 * (double)H.d[s].pw) * (double)c /
+                   (double)H.d[s].nch;
     jb.block0 = nblocks;
     nblocks += cdiv(c * H.nsub, kDecThreads);
   }
@@ -622,7 +630,7 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
   } while (0)
   STZ_TRY(cuda_ok(cudaMemsetAsync(dp, 0, sizeof(DevParams), st)));
   STZ_TRY(launch_lut(tb, lut, status, st));
-  STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, st));
+  STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
   const uint8_t* sec0 = comp + H.d[0].sect_off;
   SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps, H.nsub);
   uint8_t* g1buf = ws + P.grid[1];

@@ -252,6 +252,12 @@ struct StreamIn {
 // ---- host helpers (stz_api.cu) ----
 void make_geo(const int64_t n[3], int ndim, int dtype, int L, const int b[3], Geo* g);
 
+// Symbols of all streams of a field.
+inline int64_t total_symbols(const Geo& g) {
+  int64_t n = 0;
+  for (int s = 0; s < g.nstreams; s++) n += g.s[s].nsym;
+  return n;
+}
 inline int cuda_ok(cudaError_t e) { return e == cudaSuccess ? STZ_OK : STZ_ERR_CUDA; }
 
 }  // namespace stz

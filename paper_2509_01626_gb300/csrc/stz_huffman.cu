@@ -407,7 +407,7 @@ int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = imin(g.total_chunks, (int64_t)sms * 8);
-  ProfScope ps_("k_chunk_words", s);
+  ProfScope ps_("k_chunk_words", s, 2.0 * (double)total_symbols(g));  // one read of the codes
   k_chunk_words<<<(unsigned)grid, 256, 0, s>>>(g, codes, enc, words);
   return cuda_ok(cudaGetLastError());
 }
@@ -647,14 +647,15 @@ int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = imin(g.total_chunks, (int64_t)sms * 8);
-  ProfScope ps_("k_pack", s);
+  // reads the codes; the payload it writes is added once its size is known
+  ProfScope ps_("k_pack", s, 2.0 * (double)total_symbols(g));
   k_pack<<<(unsigned)grid, 256, smem, s>>>(g, codes, enc, word_off, sect, out, dp);
   return cuda_ok(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------- decode tables
 __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables tb,
-                                             uint32_t* __restrict__ lut,
+                                             uint16_t* __restrict__ lut,
                                              uint32_t* __restrict__ status) {
   __shared__ int cnt[32];
   __shared__ uint32_t fcode[32];
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables t
   __shared__ int bad;
   const int sid = tb.lut_sid[blockIdx.x];
   const DecStream& d = tb.ds[sid];
-  uint32_t* t = lut + (int64_t)sid * kLutSize;
+  uint16_t* t = lut + (int64_t)sid * kLutSize;
   const int tid = threadIdx.x;
   if (tid < 32) cnt[tid] = 0;
   if (tid == 0) bad = 0;
@@ -705,12 +706,12 @@ __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables t
     const int L = lens[k], sym = syms[k];
     const uint32_t code = fcode[L] + (uint32_t)(k - fidx[L]);
     const uint32_t lo = code << (kMaxCodeLen - L), hi = (code + 1) << (kMaxCodeLen - L);
-    const uint32_t v = ((uint32_t)sym << 8) | (uint32_t)L;
+    const uint16_t v = (uint16_t)(sym | (L << 11));
     for (uint32_t i = lo; i < hi; i++) t[i] = v;
   }
 }
 
-int launch_lut(const DecTables& tb, uint32_t* lut, uint32_t* status, cudaStream_t s) {
+int launch_lut(const DecTables& tb, uint16_t* lut, uint32_t* status, cudaStream_t s) {
   if (tb.nlut == 0) return STZ_OK;
   ProfScope ps_("k_lut", s);
   k_lut<<<tb.nlut, 256, 0, s>>>(tb, lut, status);
@@ -718,111 +719,180 @@ int launch_lut(const DecTables& tb, uint32_t* lut, uint32_t* status, cudaStream_
 }
 
 // ---------------------------------------------------------------- chunk decode
-// One thread per sub-chunk: a chunk of n symbols is cut into nsub runs of
-// q = ceil(n / nsub) symbols whose start bits are stored, so every run decodes
-// independently.  A run that does not end exactly where the next one starts,
-// reads past its chunk, or meets an invalid code marks the container corrupt.
+// A chunk of n symbols is cut into nsub runs of q = ceil(n / nsub) symbols
+// whose start bits are stored, so every run decodes independently: one
+// thread per run, kDecThreads / nsub consecutive chunks of a job per block.
+// The block first copies its chunks' payload words into shared memory
+// (coalesced, two zero words after each chunk), in rounds of at most
+// kStageWords words when they do not fit at once, so the decode loop reads
+// only shared memory: a 32-bit window at bit `pos` of the word pair
+// (cur, nxt), looked up in the 16-bit table.  A run that does not end exactly
+// where the next one starts, reads past its chunk, or meets an invalid code
+// marks the container corrupt (its chunk's codes are then unspecified).
+// 4-byte asynchronous copy global -> shared (Ampere+ cp.async), and the wait
+// for all of this thread's copies
+__device__ __forceinline__ void cp_async4(uint32_t* dst_smem, const uint32_t* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+constexpr int kStageWords = 10240;                              // 40 KiB per block
+constexpr int kMaxChunkWords = (4096 * kMaxCodeLen + 31) / 32;  // bricks hold <= 4096 cells
+static_assert(kMaxChunkWords + 2 <= kStageWords, "a chunk must fit the stage");
+constexpr size_t kDecSmem = sizeof(uint32_t) * kStageWords + sizeof(uint16_t) * kLutSize +
+                            sizeof(unsigned long long) * kDecThreads +
+                            sizeof(uint32_t) * (kDecThreads + 1) + sizeof(uint32_t) * kDecThreads +
+                            sizeof(int) * kDecThreads;
+static_assert((sizeof(uint32_t) * kStageWords) % 16 == 0 &&
+                  (sizeof(uint32_t) * kStageWords + sizeof(uint16_t) * kLutSize) % 8 == 0,
+              "shared arrays of the chunk decoder must stay aligned");
+
 __global__ void __launch_bounds__(kDecThreads) k_decode_chunks(
     const __grid_constant__ Geo g, const __grid_constant__ DecTables tb,
-    const uint32_t* __restrict__ lut, uint16_t* __restrict__ codes,
+    const uint16_t* __restrict__ lut, uint16_t* __restrict__ codes,
     uint32_t* __restrict__ status) {
-  __shared__ uint32_t t[kLutSize];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  // arrays in order of alignment: 16-byte-loaded table, then 8-, then 4-byte
+  uint32_t* stage = (uint32_t*)dsm;
+  uint16_t* t = (uint16_t*)(stage + kStageWords);
+  unsigned long long* cw0 = (unsigned long long*)(t + kLutSize);  // chunk's first word
+  uint32_t* S = (uint32_t*)(cw0 + kDecThreads);                   // padded-size prefix sums
+  uint32_t* cjl = S + kDecThreads + 1;                            // chunk index in stream
+  int* ccnt = (int*)(cjl + kDecThreads);                          // symbols; -1: bad chunk
+  __shared__ uint32_t wsum[8];
+  const int tid = threadIdx.x;
   int jb = 0;
   for (int k = 1; k < tb.njobs; k++)
     if (tb.jobs[k].block0 <= (int64_t)blockIdx.x) jb = k;
   const DecChunkJob& job = tb.jobs[jb];
   const int sid = job.sid;
-  const uint32_t* src = lut + (int64_t)sid * kLutSize;
-  for (int i = threadIdx.x; i < kLutSize; i += blockDim.x) t[i] = src[i];
-  __syncthreads();
-  const DecStream& d = tb.ds[sid];
-  const int nsub = d.nsub;
-  const int64_t qq = ((int64_t)blockIdx.x - job.block0) * kDecThreads + threadIdx.x;
-  const int64_t q = qq / nsub;
-  const int u = (int)(qq - q * nsub);
-  if (q >= job.nchunks_job) return;
-  const StreamGeo& sg = g.s[sid];
-  const int q32 = (int)q, c1 = (int)job.cnt[1], c2 = (int)job.cnt[2];
-  const int r0 = q32 / (c1 * c2), rr = q32 - r0 * c1 * c2, r1 = rr / c2, r2 = rr - r1 * c2;
-  const int B0 = (int)job.lo[0] + r0, B1 = (int)job.lo[1] + r1, B2 = (int)job.lo[2] + r2;
-  const int64_t jl = ((int64_t)B0 * sg.nb[1] + B1) * sg.nb[2] + B2;
-  const int cnt = min(g.b[0], (int)sg.e[0] - B0 * g.b[0]) *
-                  min(g.b[1], (int)sg.e[1] - B1 * g.b[1]) * min(g.b[2], (int)sg.e[2] - B2 * g.b[2]);
-  const int per = (cnt + nsub - 1) / nsub;
-  const int64_t i0 = min(cnt, u * per), i1 = min(cnt, (u + 1) * per);
-  const uint32_t* coff = (const uint32_t*)(d.sect + d.off_chunks);
-  const uint16_t* soff = (const uint16_t*)(d.sect + d.off_subs) + jl * (nsub - 1);
-  const uint32_t* pay = (const uint32_t*)(d.sect + d.off_payload);
-  const uint64_t w0 = coff[jl];
-  const uint64_t w1 = jl + 1 < (int64_t)d.nchunks ? coff[jl + 1] : d.pw;
-  uint16_t* out = codes + (job.slot_base + q) * g.bvol;
-  const uint64_t cbits = w1 >= w0 ? (w1 - w0) * 32 : 0;
-  const uint64_t b0 = u == 0 ? 0 : soff[u - 1];
-  const uint64_t b1 = u + 1 < nsub ? soff[u] : cbits;
-  if (w0 > w1 || w1 > d.pw || b0 > b1 || b1 > cbits) {
-    atomicOr(status, kStatCorrupt);
-    for (int64_t i = i0; i < i1; i++) out[i] = 0;
-    return;
-  }
-  const uint32_t* wp = pay + w0 + (b0 >> 5);
-  const uint32_t* we = pay + w1;
-  unsigned long long buf = 0;
-  int nb = 0;
-  uint64_t consumed = 0;
-  uint32_t pre;  // the next payload word, loaded one refill ahead of its use
   {
-    const int sh = (int)(b0 & 31);
-    uint32_t word = wp < we ? *wp : 0u;
-    wp++;
-    pre = wp < we ? *wp : 0u;
-    buf = (unsigned long long)word << (32 + sh);
-    nb = 32 - sh;
+    const uint4* src = (const uint4*)(lut + (int64_t)sid * kLutSize);
+    for (int i = tid; i < kLutSize / 8; i += blockDim.x) ((uint4*)t)[i] = __ldg(src + i);
   }
-  bool badcode = false;
-  // decode one symbol: refill below 32 buffered bits, look up the next 12
-  auto next = [&]() -> uint32_t {
-    if (nb < 32) {
-      const uint32_t word = pre;
-      wp++;
-      pre = wp < we ? *wp : 0u;
-      buf |= (unsigned long long)word << (32 - nb);
-      nb += 32;
-    }
-    const uint32_t ent = t[buf >> (64 - kMaxCodeLen)];
-    int L = (int)(ent & 255u);
-    if (L == 0) {
-      badcode = true;
-      L = 1;
-    }
-    buf <<= L;
-    nb -= L;
-    consumed += (uint64_t)L;
-    return ent >> 8;
-  };
-  int64_t i = i0;
-  // 8 symbols per 16-byte store where the run start is 16-byte aligned
-  if ((((uintptr_t)(out + i)) & 15) == 0) {
-    for (; i + 8 <= i1; i += 8) {
-      uint32_t v[4];
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const uint32_t lo = next();
-        const uint32_t hi = next();
-        v[k] = lo | (hi << 16);
+  const DecStream& d = tb.ds[sid];
+  const StreamGeo& sg = g.s[sid];
+  const int nsub = d.nsub;
+  const int cpb = kDecThreads / nsub;  // chunks per block
+  const int64_t qb = ((int64_t)blockIdx.x - job.block0) * cpb;
+  const int nch = (int)min((int64_t)cpb, job.nchunks_job - qb);
+  const uint32_t* coff = (const uint32_t*)(d.sect + d.off_chunks);
+  const uint32_t* pay = (const uint32_t*)(d.sect + d.off_payload);
+  // the block's chunks: index in the stream, symbols, payload words
+  uint32_t psz = 0;
+  if (tid < nch) {
+    const int q32 = (int)(qb + tid), c1 = (int)job.cnt[1], c2 = (int)job.cnt[2];
+    const int r0 = q32 / (c1 * c2), rr = q32 - r0 * c1 * c2, r1 = rr / c2, r2 = rr - r1 * c2;
+    const int B0 = (int)job.lo[0] + r0, B1 = (int)job.lo[1] + r1, B2 = (int)job.lo[2] + r2;
+    const int64_t jl = ((int64_t)B0 * sg.nb[1] + B1) * sg.nb[2] + B2;
+    const int cnt = min(g.b[0], (int)sg.e[0] - B0 * g.b[0]) *
+                    min(g.b[1], (int)sg.e[1] - B1 * g.b[1]) *
+                    min(g.b[2], (int)sg.e[2] - B2 * g.b[2]);
+    const uint64_t w0 = coff[jl];
+    const uint64_t w1 = jl + 1 < (int64_t)d.nchunks ? coff[jl + 1] : d.pw;
+    const bool ok = w0 <= w1 && w1 <= d.pw && w1 - w0 <= (uint64_t)kMaxChunkWords;
+    cw0[tid] = w0;
+    cjl[tid] = (uint32_t)jl;
+    ccnt[tid] = ok ? cnt : -1;
+    psz = ok ? (uint32_t)(w1 - w0) + 2u : 0u;
+  }
+  uint32_t total;
+  const uint32_t excl = block_scan_256(psz, wsum, &total);
+  if (tid < nch) S[tid] = excl;
+  if (tid == 0) S[nch] = total;
+  // this thread's run
+  const int c = tid / nsub, u = tid - c * nsub;
+  bool bad = false;
+  int a = 0;
+  while (a < nch) {
+    __syncthreads();
+    const uint32_t base = S[a];
+    const int b = a + __syncthreads_count(tid >= a && tid < nch && S[tid + 1] - base <= kStageWords);
+    {
+      // copy chunks [a, b): one warp per chunk, lanes over its words, every
+      // copy asynchronous (none waits for the one before), then one wait
+      const int lane = tid & 31;
+      for (int cc = a + (tid >> 5); cc < b; cc += kDecThreads / 32) {
+        const uint32_t len = S[cc + 1] - S[cc];
+        uint32_t* dst = stage + (S[cc] - base);
+        const uint32_t* src = pay + cw0[cc];
+        for (uint32_t k = lane; k < len; k += 32) {
+          if (k + 2 < len) cp_async4(dst + k, src + k);
+          else dst[k] = 0u;
+        }
       }
-      *(uint4*)(out + i) = make_uint4(v[0], v[1], v[2], v[3]);
+      cp_async_wait_all();
     }
+    __syncthreads();
+    if (c >= a && c < b) {
+      const int cnt = ccnt[c];
+      const int per = (max(cnt, 0) + nsub - 1) / nsub;
+      const int i0 = min(max(cnt, 0), u * per), i1 = min(max(cnt, 0), (u + 1) * per);
+      uint16_t* out = codes + (job.slot_base + qb + c) * g.bvol;
+      const uint32_t words = S[c + 1] - S[c] - 2;  // garbage when the chunk is bad (unused)
+      const uint64_t cbits = (uint64_t)words * 32;
+      const uint16_t* soff = (const uint16_t*)(d.sect + d.off_subs) + (int64_t)cjl[c] * (nsub - 1);
+      const uint32_t b0 = u == 0 ? 0u : soff[u - 1];
+      const uint64_t b1 = u + 1 < nsub ? (uint64_t)soff[u] : cbits;
+      if (cnt < 0 || b0 > b1 || b1 > cbits) {
+        bad = true;
+        for (int i = i0; i < i1; i++) out[i] = 0;
+      } else {
+        const uint32_t* sp = stage + (S[c] - base);
+        const int lim = (int)words + 1;  // last staged (pad) word of the chunk
+        int k = (int)(b0 >> 5);
+        int pos = (int)(b0 & 31);
+        uint32_t cur = sp[k], nxt = sp[k + 1];
+        auto next = [&]() -> uint32_t {
+          const uint32_t win = __funnelshift_l(nxt, cur, pos);
+          const uint32_t ent = t[win >> (32 - kMaxCodeLen)];
+          int L = (int)(ent >> 11);
+          bad |= L == 0;
+          pos += L == 0 ? 1 : L;
+          if (pos >= 32) {
+            pos -= 32;
+            cur = nxt;
+            bad |= k + 1 >= lim;  // past the chunk's payload and first pad word
+            k = min(k + 1, lim - 1);
+            nxt = sp[k + 1];
+          }
+          return ent & 0x7FFu;
+        };
+        int i = i0;
+        // 8 symbols per 16-byte store where the run start is 16-byte aligned
+        if ((((uintptr_t)(out + i)) & 15) == 0) {
+          for (; i + 8 <= i1; i += 8) {
+            uint32_t v[4];
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+              const uint32_t lo = next();
+              v[m] = lo | (next() << 16);
+            }
+            *(uint4*)(out + i) = make_uint4(v[0], v[1], v[2], v[3]);
+          }
+        }
+        for (; i < i1; i++) out[i] = (uint16_t)next();
+        const uint64_t end = (uint64_t)k * 32 + (uint64_t)pos;
+        bad |= u + 1 < nsub ? end != b1 : end > b1;
+      }
+    }
+    a = b;
   }
-  for (; i < i1; i++) out[i] = (uint16_t)next();
-  const bool exact = u + 1 < nsub ? (b0 + consumed == b1) : (b0 + consumed <= b1);
-  if (badcode || !exact) atomicOr(status, kStatCorrupt);
+  if (bad) atomicOr(status, kStatCorrupt);
 }
 
-int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,
-                         uint16_t* codes, uint32_t* status, cudaStream_t s) {
+int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint16_t* lut,
+                         uint16_t* codes, uint32_t* status, double bytes, cudaStream_t s) {
   if (tb.nblocks == 0) return STZ_OK;
-  ProfScope ps_("k_decode_chunks", s);
-  k_decode_chunks<<<(unsigned)tb.nblocks, kDecThreads, 0, s>>>(g, tb, lut, codes, status);
+  static_assert(kDecThreads == 256, "block_scan_256 assumes 256 threads");
+  if (cudaFuncSetAttribute(k_decode_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kDecSmem) != cudaSuccess)
+    return STZ_ERR_CUDA;
+  ProfScope ps_("k_decode_chunks", s, bytes);
+  k_decode_chunks<<<(unsigned)tb.nblocks, kDecThreads, kDecSmem, s>>>(g, tb, lut, codes, status);
   return cuda_ok(cudaGetLastError());
 }
 

@@ -80,7 +80,8 @@ int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
                 const unsigned long long* word_off, const SectDev* sect, uint8_t* out,
                 const DevParams* dp, cudaStream_t s);
 
-// decode tables: lut[s][i] = sym << 8 | len for the top-12-bit index i
+// decode tables: lut[s][i] = sym | len << 11 for the top-12-bit window i
+// (len 0: no code starts with i)
 struct DecStream {
   const uint8_t* sect;        // section start in the container
   uint64_t nlive, nchunks, pw;
@@ -103,9 +104,10 @@ struct DecTables {
   int njobs;
   int64_t nblocks;            // thread blocks of the chunk decoder
 };
-int launch_lut(const DecTables& tb, uint32_t* lut, uint32_t* status, cudaStream_t s);
-int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,
-                         uint16_t* codes, uint32_t* status, cudaStream_t s);
+int launch_lut(const DecTables& tb, uint16_t* lut, uint32_t* status, cudaStream_t s);
+// bytes: the launch's algorithmic bytes (payload read, codes written)
+int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint16_t* lut,
+                         uint16_t* codes, uint32_t* status, double bytes, cudaStream_t s);
 
 // ---- stz_container.cu: layout, header, sections, outliers ----
 struct SectDev {

@@ -674,7 +674,7 @@ static int sm_count() {
 }
 
 template <typename T, bool DEC>
-static int run_level_generic(const LevelArgs& a, cudaStream_t s) {
+static int run_level_generic(const LevelArgs& a, double bytes, cudaStream_t s) {
   int64_t M[3];
   grid_extent(a.geo.n, a.geo.L, a.level - 1, M);
   int tvol = 1;
@@ -694,13 +694,13 @@ static int run_level_generic(const LevelArgs& a, cudaStream_t s) {
   char nm[48];
   snprintf(nm, sizeof(nm), "k_level%d_%s_%s", a.level, DEC ? "dec" : "enc",
            sizeof(T) == 4 ? "f32" : "f64");
-  ProfScope ps_(nm, s);
+  ProfScope ps_(nm, s, bytes);
   kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(a);
   return cuda_ok(cudaGetLastError());
 }
 
 template <typename T, bool DEC>
-static int run_level_fast(const LevelArgs& a, const int64_t M[3], cudaStream_t s) {
+static int run_level_fast(const LevelArgs& a, const int64_t M[3], double bytes, cudaStream_t s) {
   // interior cells exist only with M >= 4 on every axis
   if (M[0] < 4 || M[1] < 4 || M[2] < 4) return STZ_OK;
   size_t smem = 2 * (((size_t)(kFBZ + 3) * kFEZY * sizeof(T) + 15) & ~(size_t)15);
@@ -718,38 +718,44 @@ static int run_level_fast(const LevelArgs& a, const int64_t M[3], cudaStream_t s
   char nm[48];
   snprintf(nm, sizeof(nm), "k_level%d_%s_%s", a.level, DEC ? "dec" : "enc",
            sizeof(T) == 4 ? "f32" : "f64");
-  ProfScope ps_(nm, s);
+  ProfScope ps_(nm, s, bytes);
   kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(a);
   return cuda_ok(cudaGetLastError());
 }
 
-template <typename T, bool DEC>
-static int run_level_shell(const LevelArgs& a, const int64_t M[3], cudaStream_t s) {
-  ShellGeo sh;
-  memset(&sh, 0, sizeof(sh));
+// The cells of G_{l-1} whose fine points can fall in the fine box, and the
+// boundary cells among them (the shell kernel's).  Returns the box's cell
+// count (0: nothing to do); sh->nA + nB + nC is the shell's.
+static int64_t shell_geo(const LevelArgs& a, const int64_t M[3], ShellGeo* sh) {
+  memset(sh, 0, sizeof(*sh));
+  int64_t cells = 1;
   for (int d = 0; d < 3; d++) {
-    // needed cells: those whose points can fall in the fine box
-    sh.lo[d] = imax(0, a.flo[d] / 2);
-    sh.hi[d] = imin(M[d], cdiv(a.fhi[d], 2));
-    if (sh.hi[d] <= sh.lo[d]) return STZ_OK;
+    sh->lo[d] = imax(0, a.flo[d] / 2);
+    sh->hi[d] = imin(M[d], cdiv(a.fhi[d], 2));
+    if (sh->hi[d] <= sh->lo[d]) return 0;
+    cells *= sh->hi[d] - sh->lo[d];
     const int64_t cand[3] = {0, M[d] - 2, M[d] - 1};
-    sh.nb[d] = 0;
+    sh->nb[d] = 0;
     for (int k = 0; k < 3; k++) {
       const int64_t v = cand[k];
       bool dup = false;
-      for (int j = 0; j < sh.nb[d]; j++) dup = dup || sh.bv[d][j] == v;
+      for (int j = 0; j < sh->nb[d]; j++) dup = dup || sh->bv[d][j] == v;
       const bool boundary = !(v >= 1 && v <= M[d] - 3);
-      if (!dup && boundary && v >= sh.lo[d] && v < sh.hi[d]) sh.bv[d][sh.nb[d]++] = v;
+      if (!dup && boundary && v >= sh->lo[d] && v < sh->hi[d]) sh->bv[d][sh->nb[d]++] = v;
     }
-    sh.ilo[d] = imax(1, sh.lo[d]);
-    sh.ihi[d] = imax(sh.ilo[d], imin(M[d] - 2, sh.hi[d]));
+    sh->ilo[d] = imax(1, sh->lo[d]);
+    sh->ihi[d] = imax(sh->ilo[d], imin(M[d] - 2, sh->hi[d]));
   }
-  const int64_t nz = sh.hi[0] - sh.lo[0], ny = sh.hi[1] - sh.lo[1], nx = sh.hi[2] - sh.lo[2];
-  (void)nz;
-  const int64_t iz = sh.ihi[0] - sh.ilo[0], iy = sh.ihi[1] - sh.ilo[1];
-  sh.nA = sh.nb[0] * ny * nx;
-  sh.nB = iz * sh.nb[1] * nx;
-  sh.nC = iz * iy * sh.nb[2];
+  const int64_t ny = sh->hi[1] - sh->lo[1], nx = sh->hi[2] - sh->lo[2];
+  const int64_t iz = sh->ihi[0] - sh->ilo[0], iy = sh->ihi[1] - sh->ilo[1];
+  sh->nA = sh->nb[0] * ny * nx;
+  sh->nB = iz * sh->nb[1] * nx;
+  sh->nC = iz * iy * sh->nb[2];
+  return cells;
+}
+
+template <typename T, bool DEC>
+static int run_level_shell(const LevelArgs& a, const ShellGeo& sh, double bytes, cudaStream_t s) {
   const int64_t total = sh.nA + sh.nB + sh.nC;
   if (total == 0) return STZ_OK;
   const size_t smem = DEC ? 0 : sizeof(uint32_t) * 7 * kHistWords;
@@ -763,9 +769,19 @@ static int run_level_shell(const LevelArgs& a, const int64_t M[3], cudaStream_t 
   char nm[48];
   snprintf(nm, sizeof(nm), "k_level%d_shell_%s_%s", a.level, DEC ? "dec" : "enc",
            sizeof(T) == 4 ? "f32" : "f64");
-  ProfScope ps_(nm, s);
+  ProfScope ps_(nm, s, bytes);
   kern<<<(unsigned)grid, 256, smem, s>>>(a, sh);
   return cuda_ok(cudaGetLastError());
+}
+
+// Algorithmic bytes of one coarse cell (its 7 new points and the copied
+// coarse point): decoding reads 7 codes and the coarse value and writes 8
+// fine values; compressing reads 7 field values and the coarse value, writes
+// 7 codes and, below the finest level, 8 reconstructed values.
+template <typename T, bool DEC>
+static double cell_bytes(const LevelArgs& a) {
+  const double P = (double)sizeof(T);
+  return DEC ? 7 * 2 + P + 8 * P : 7 * P + P + 7 * 2 + (a.fine ? 8 * P : 0.0);
 }
 
 template <typename T, bool DEC>
@@ -777,10 +793,14 @@ static int run_level(const LevelArgs& a, cudaStream_t s) {
   const bool fast = a.geo.b[0] == kFBZ && a.geo.b[1] == kFBY && a.geo.b[2] == kFBX &&
                     2 * kFBZ * sl * a.geo.n[1] * a.geo.n[2] < ((int64_t)1 << 31) &&
                     2 * kFBZ * fe < ((int64_t)1 << 31);
-  if (!fast) return run_level_generic<T, DEC>(a, s);
-  int rc = run_level_fast<T, DEC>(a, M, s);
+  ShellGeo sh;
+  const int64_t cells = shell_geo(a, M, &sh);
+  const double bpc = cell_bytes<T, DEC>(a);
+  if (!fast) return run_level_generic<T, DEC>(a, (double)cells * bpc, s);
+  const int64_t nshell = sh.nA + sh.nB + sh.nC;
+  int rc = run_level_fast<T, DEC>(a, M, (double)(cells - nshell) * bpc, s);
   if (rc != STZ_OK) return rc;
-  return run_level_shell<T, DEC>(a, M, s);
+  return run_level_shell<T, DEC>(a, sh, (double)nshell * bpc, s);
 }
 
 int launch_level(const LevelArgs& a, bool decode, cudaStream_t s) {

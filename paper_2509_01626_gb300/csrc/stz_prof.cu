@@ -20,13 +20,14 @@ struct Rec {
   std::string name;
   cudaEvent_t a, b;
   bool done;
+  double bytes;
 };
 std::vector<Rec> g_recs;           // pending event pairs
 std::vector<cudaEvent_t> g_pool;   // reusable events
 struct Acc {
   std::string name;
   unsigned long long launches;
-  double ms;
+  double ms, bytes;
 };
 std::vector<Acc> g_acc;
 
@@ -50,10 +51,11 @@ void resolve_locked() {
       if (a.name == r.name) {
         a.launches++;
         a.ms += ms;
+        a.bytes += r.bytes;
         found = true;
         break;
       }
-    if (!found) g_acc.push_back({r.name, 1ull, (double)ms});
+    if (!found) g_acc.push_back({r.name, 1ull, (double)ms, r.bytes});
     g_pool.push_back(r.a);
     g_pool.push_back(r.b);
   }
@@ -61,7 +63,7 @@ void resolve_locked() {
 }
 }  // namespace
 
-void prof_begin(const char* name, cudaStream_t s, int* slot) {
+void prof_begin(const char* name, cudaStream_t s, int* slot, double bytes) {
   g_launches.fetch_add(1);
   *slot = -1;
   if (!g_enabled.load()) return;
@@ -71,6 +73,7 @@ void prof_begin(const char* name, cudaStream_t s, int* slot) {
   r.a = get_event();
   r.b = get_event();
   r.done = false;
+  r.bytes = bytes;
   cudaEventRecord(r.a, s);
   g_recs.push_back(r);
   *slot = (int)g_recs.size() - 1;
@@ -83,6 +86,16 @@ void prof_end(int slot, cudaStream_t s) {
     cudaEventRecord(g_recs[slot].b, s);
     g_recs[slot].done = true;
   }
+}
+
+void prof_add_bytes(const char* name, double bytes) {
+  if (!g_enabled.load()) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (size_t i = g_recs.size(); i-- > 0;)
+    if (g_recs[i].name == name) {
+      g_recs[i].bytes += bytes;
+      return;
+    }
 }
 
 }  // namespace stz
@@ -113,6 +126,7 @@ int stz_profile_read(stz_kernel_time* out, int max_entries) {
     strncpy(out[i].name, g_acc[i].name.c_str(), sizeof(out[i].name) - 1);
     out[i].launches = g_acc[i].launches;
     out[i].total_ms = g_acc[i].ms;
+    out[i].algo_bytes = g_acc[i].bytes;
   }
   return n;
 }

@@ -8,13 +8,20 @@
 
 namespace stz {
 
-void prof_begin(const char* name, cudaStream_t s, int* slot);
+// `bytes`: the launch's algorithmic bytes (every input it must read and
+// every output it must write, once), 0 where no figure is kept.
+void prof_begin(const char* name, cudaStream_t s, int* slot, double bytes);
 void prof_end(int slot, cudaStream_t s);
+// Adds algorithmic bytes to the latest timed launch of `name` (for a launch
+// whose sizes are known only after it ran).
+void prof_add_bytes(const char* name, double bytes);
 
 struct ProfScope {
   int slot;
   cudaStream_t s;
-  ProfScope(const char* name, cudaStream_t st) : slot(-1), s(st) { prof_begin(name, st, &slot); }
+  ProfScope(const char* name, cudaStream_t st, double bytes = 0.0) : slot(-1), s(st) {
+    prof_begin(name, st, &slot, bytes);
+  }
   ~ProfScope() { prof_end(slot, s); }
 };
 

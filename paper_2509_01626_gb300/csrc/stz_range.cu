@@ -169,7 +169,7 @@ int launch_range(const void* field, int dtype, int64_t n, DevParams* dp, cudaStr
   int64_t per = dtype == STZ_F32 ? 4 : 2;
   int64_t want = cdiv(cdiv(n, per), 256);
   int blocks = (int)imin(imax(want, 1), (int64_t)sms * 8);
-  ProfScope ps_("k_range", s);
+  ProfScope ps_("k_range", s, (double)n * (dtype == STZ_F32 ? 4 : 8));  // one read of the field
   if (dtype == STZ_F32) k_range<STZ_F32><<<blocks, 256, 0, s>>>(field, n, dp);
   else k_range<STZ_F64><<<blocks, 256, 0, s>>>(field, n, dp);
   return cuda_ok(cudaGetLastError());

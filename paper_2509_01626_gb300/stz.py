@@ -44,7 +44,7 @@ class _Info(ctypes.Structure):
 
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_ulonglong),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double)]
 
 
 _lib = None
@@ -253,8 +253,10 @@ def profile_reset() -> None:
 
 
 def profile_read() -> dict:
-    """{kernel name: (timed launches, total device ms)} since the last reset."""
+    """{kernel name: (timed launches, total device ms, total algorithmic
+    bytes)} since the last reset."""
     buf = (_KernelTime * 64)()
     n = lib().stz_profile_read(buf, 64)
-    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms),
+                                   float(buf[i].algo_bytes))
             for i in range(min(n, 64))}
