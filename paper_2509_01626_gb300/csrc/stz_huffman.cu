@@ -6,10 +6,12 @@
 // Code construction (one thread block per stream, all streams at once):
 // live symbols sorted by (frequency, symbol); two-queue Huffman merge with a
 // leaf winning ties; code counts per length; if the longest exceeds 12 the
-// counts are repaired as in ITU-T T.81 Annex K.3; lengths handed out by
+// longer codes are clamped to 12 and the Kraft excess is removed by moving
+// codes one length deeper, deepest lengths first; lengths handed out by
 // frequency rank; canonical codes by (length, symbol), MSB-first.
-// Decoding: 4096-entry table indexed by the next 12 bits, one thread per
-// chunk.
+// Decoding: each block stages its chunks' payload words in shared memory and
+// one thread decodes one sub-chunk through a 4096-entry table indexed by the
+// next 12 bits.
 #include "stz_kernels.cuh"
 #include "stz_prof.cuh"
 
