@@ -140,6 +140,36 @@ int stz_decompress_region(const void* comp_dev, size_t comp_bytes, const int64_t
                           const int64_t* hi, int level, void* out_dev, size_t out_cap,
                           int64_t* out_dims, void* ws_dev, size_t ws_bytes, void* stream);
 
+/*
+ * Region decompression without any device allocation, for callers that
+ * cannot obtain device memory at the point of the call: a plug-in (an I/O
+ * library filter, a visualisation reader) that its host application hands
+ * only the compressed input and the output buffer, or a latency-critical
+ * path that must not pay cudaMalloc's implicit device synchronisation.
+ * The paper has no counterpart; it is an addition of this library.
+ *
+ * Same arguments, output and errors as stz_decompress_region, minus the
+ * workspace: the scratch comes from one array of STZ_NOALLOC_SCRATCH_BYTES
+ * in the library's device memory, which every GPU that loads the library
+ * holds until the process exits.  A call whose decode needs more scratch
+ * than that returns STZ_ERR_CAPACITY before any work is queued (the level-1
+ * grid of the field is always decoded whole, so this covers fields up to
+ * about 512^3 f32 with boxes up to about 128^3).
+ *
+ * The first call on a device looks up that array's device address (with
+ * the device current); make that first call before any stream capture on
+ * the device.  The calling thread must have the stream's device current.
+ * All calls share the one array and it keeps the last call's contents
+ * (each call clears what must start at zero): calls whose work overlaps on
+ * the GPU -- on different streams, or from different host threads -- race
+ * and give wrong results.  Issue them on one stream, one after another.
+ * Allocates nothing: no cudaMalloc, no cudaFree.
+ */
+#define STZ_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int stz_decompress_region_noalloc(const void* comp_dev, size_t comp_bytes, const int64_t* lo,
+                                  const int64_t* hi, int level, void* out_dev, size_t out_cap,
+                                  int64_t* out_dims, void* stream);
+
 /* ---- tracing (no counterpart in the paper, which reports wall times only) ----
  * Every kernel launch of the library is counted.  With profiling enabled an
  * event pair is recorded around each launch on its stream; stz_profile_read

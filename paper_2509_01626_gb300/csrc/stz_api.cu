@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "stz_kernels.cuh"
 #include "stz_prof.cuh"
 
@@ -733,6 +735,45 @@ int stz_decompress_region(const void* comp_dev, size_t comp_bytes, const int64_t
   if (level < 1) return STZ_ERR_ARG;
   return decode_impl(comp_dev, comp_bytes, lo, hi, level, 0, out_dev, out_cap, out_dims, ws_dev,
                      ws_bytes, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------ region decode, no allocation
+// The scratch of stz_decompress_region_noalloc: one file-scope array in the
+// library's device memory.  Host code sees only a host-side stand-in under
+// this name, so its device address is looked up per device (with that
+// device current) and passed to the kernels like any workspace.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[STZ_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices];
+}  // namespace
+
+static int noalloc_scratch(void** ptr) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return STZ_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return STZ_ERR_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *ptr = g_noalloc_ptr[dev];
+  return STZ_OK;
+}
+
+int stz_decompress_region_noalloc(const void* comp_dev, size_t comp_bytes, const int64_t* lo,
+                                  const int64_t* hi, int level, void* out_dev, size_t out_cap,
+                                  int64_t* out_dims, void* stream) {
+  if (level < 1) return STZ_ERR_ARG;
+  void* ws = nullptr;
+  const int rc = noalloc_scratch(&ws);
+  if (rc != STZ_OK) return rc;
+  // decode_impl rejects a plan larger than the array before it queues work
+  // and clears the device parameters (status word) at its start
+  return decode_impl(comp_dev, comp_bytes, lo, hi, level, 0, out_dev, out_cap, out_dims, ws,
+                     STZ_NOALLOC_SCRATCH_BYTES, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
         L.stz_decompress_progressive.argtypes = [vp, sz, ctypes.c_int, vp, sz, i64p, vp, sz, vp]
         L.stz_decompress_region.argtypes = [vp, sz, i64p, i64p, ctypes.c_int, vp, sz, i64p, vp,
                                             sz, vp]
+        L.stz_decompress_region_noalloc.argtypes = [vp, sz, i64p, i64p, ctypes.c_int, vp, sz,
+                                                    i64p, vp]
         L.stz_launch_count.restype = ctypes.c_ulonglong
         L.stz_profile_enable.argtypes = [ctypes.c_int]
         L.stz_profile_read.argtypes = [ctypes.POINTER(_KernelTime), ctypes.c_int]
@@ -232,6 +234,32 @@ def decompress_region(comp: torch.Tensor, lo, hi, level: int | None = None,
                                      ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                                      _stream(stream))
     _check(rc, "stz_decompress_region")
+    oshape = _shape_out(od, inf["ndim"])
+    n = 1
+    for v in oshape:
+        n *= v
+    return out.reshape(-1)[:n].view(oshape)
+
+
+# Scratch bytes of decompress_region_noalloc (STZ_NOALLOC_SCRATCH_BYTES).
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def decompress_region_noalloc(comp: torch.Tensor, lo, hi, level: int, out: torch.Tensor,
+                              stream=None, meta: dict | None = None) -> torch.Tensor:
+    """stz_decompress_region_noalloc: like decompress_region, but the library
+    allocates nothing and takes no workspace -- its scratch is a fixed array
+    in the library's device memory.  For callers that cannot allocate device
+    memory when they decode; `out` must be given.  Calls share that array,
+    so issue them on one stream."""
+    inf = meta or info(comp)
+    od = (ctypes.c_int64 * 3)()
+    rc = lib().stz_decompress_region_noalloc(ctypes.c_void_p(comp.data_ptr()), comp.numel(),
+                                             _i64(lo), _i64(hi), int(level),
+                                             ctypes.c_void_p(out.data_ptr()),
+                                             out.numel() * out.element_size(), od,
+                                             _stream(stream))
+    _check(rc, "stz_decompress_region_noalloc")
     oshape = _shape_out(od, inf["ndim"])
     n = 1
     for v in oshape:
