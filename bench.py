@@ -56,6 +56,12 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-profile", action="store_true")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched-form section")
+    p.add_argument("--no-serve", action="store_true", help="skip the served-form section")
+    p.add_argument("--serve-fields", type=int, default=8)
+    p.add_argument("--serve-size", type=int, default=1024)
+    p.add_argument("--serve-requests", type=int, default=1000, help="requests per rate")
+    p.add_argument("--serve-rates", default="1000,5000,10000,50000")
     return p.parse_args()
 
 
@@ -127,6 +133,18 @@ def make_field(size, rank, device):
 
     return synth.grf((size, size, size), synth.seed_for(2, rank), slope=-3.0,
                      lognormal_sigma=1.5, dtype=np.float32, device=device)
+
+
+def reduce_max(value: float, device) -> float:
+    """Maximum of `value` over the ranks (the value itself with one rank)."""
+    import torch
+    import torch.distributed as tdist
+
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def step_boxes(size):
@@ -246,10 +264,7 @@ def run_ours(args, rank, world, local_rank):
         kernels = stz.profile_read()
     ms_step = t0.elapsed_time(t1) / args.steps
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = reduce_max(ms_step, dev)
     ops = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in evs])
     op_ms = ops.mean(axis=0)
 
@@ -309,10 +324,7 @@ def run_ours(args, rank, world, local_rank):
         b_.record(stream)
         torch.cuda.synchronize()
         e2e_ms = a.elapsed_time(b_) / args.steps
-        if dist:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = reduce_max(e2e_ms, dev)
         box_n = (bhi[0] - blo[0]) * (bhi[1] - blo[1]) * (bhi[2] - blo[2])
         d2h = comp_bytes + field_bytes + 4 * (p_out[1].numel() - 1) + 4 * (p_out[2].numel() - 1) \
             + 4 * box_n + 4 * size * size
@@ -334,6 +346,98 @@ def _gpu_uuid(local_rank):
         return s if s.startswith("GPU-") else "GPU-" + s
     except Exception:  # noqa: BLE001
         return str(local_rank)
+
+
+# ------------------------------------------------------------ batched form
+def run_batched(args, dev):
+    """The mixed batch of 64 uneven fields: the plain per-field loop (one
+    stz_compress each) against stz_compress_batch with the autotuned
+    arrangement; containers checked identical."""
+    import torch
+
+    from paper_2509_01626_gb300 import batch, synth
+
+    items = synth.batch_workload()
+    fields = [synth.make_batch_field(it, device=str(dev)) for it in items]
+    ebs = [it[4] for it in items]
+    bc = batch.BatchCompressor(fields, ebs, ["rel"] * len(fields), device=dev)
+    nbytes = bc.input_bytes
+    loop_ms = bc.time_ms(bc.loop, reps=3)
+    loop_sizes = bc.loop()
+    loop_out = [o[:n].clone() for o, n in zip(bc.outs, loop_sizes)]
+    best = bc.autotune(reps=2)
+    batch_ms = bc.time_ms(bc.run, reps=5)
+    bc.run()
+    sizes = bc.sizes()
+    identical = sizes == loop_sizes and all(
+        torch.equal(o[:n], r) for o, n, r in zip(bc.outs, sizes, loop_out))
+    del loop_out
+    out = {"workload": "64 fields: 40 3D f32 dims U[64,512] (sinusoids + noise), 16 2D f32 "
+                       "1800x3600 (banded), 8 3D f64 256^3 (smooth); rel eb from "
+                       "{1e-2,1e-3,1e-4}",
+           "input_gb": round(nbytes / 1e9, 3),
+           "loop_ms": round(loop_ms, 3), "loop_gbs": round(nbytes / (loop_ms * 1e-3) / 1e9, 2),
+           "batch_ms": round(batch_ms, 3),
+           "batch_gbs": round(nbytes / (batch_ms * 1e-3) / 1e9, 2),
+           "speedup": round(loop_ms / batch_ms, 3),
+           "autotuned": {"lanes": best.lanes, "sm_share_den": best.sm_share_den,
+                         "graph": best.use_graph},
+           "identical_to_loop": bool(identical),
+           "compression_ratio": round(nbytes / sum(sizes), 3),
+           "candidates": len(bc.tuning)}
+    del bc, fields
+    torch.cuda.empty_cache()
+    return out
+
+
+# ------------------------------------------------------------- served form
+def run_served(args, dev):
+    """Resident compressed fields; Poisson request streams of random boxes at
+    several rates, served by the continuous-batching loop and by the serial
+    per-request path."""
+    import torch
+
+    from paper_2509_01626_gb300 import serve, stz, synth
+
+    size = args.serve_size
+    shape = (size, size, size)
+    comps = []
+    ws = stz.alloc_workspace(shape, torch.float32, dev)
+    out = torch.empty(stz.compress_bound(shape, torch.float32), dtype=torch.uint8, device=dev)
+    raw = 0
+    for i in range(args.serve_fields):
+        x = synth.grf(shape, synth.seed_for(5, i), slope=-5.0 / 3.0, lognormal_sigma=None,
+                      dtype=np.float32, device=str(dev), white_source="torch", as_tensor=True)
+        comps.append(stz.compress(x, 1e-3, "rel", out=out, workspace=ws).clone())
+        raw += x.numel() * 4
+        del x
+        torch.cuda.empty_cache()
+    del out
+    resident = sum(c.numel() for c in comps)
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(min(16 << 30, free // 4))
+    srv = serve.Server(comps, budget_bytes=budget, max_edge=256, max_slots=32)
+    reg_out = torch.empty(256 ** 3 * 4, dtype=torch.uint8, device=dev)
+    rates = [float(r) for r in args.serve_rates.split(",") if r]
+    # warm both paths
+    warm = serve.poisson_requests([shape] * len(comps), 20, 1e5, synth.seed_for(5, 99))
+    srv.run(warm)
+    serve.serial(comps, warm, ws, reg_out, realtime=False)
+    per_rate = []
+    for k, rate in enumerate(rates):
+        reqs = serve.poisson_requests([shape] * len(comps), args.serve_requests, rate,
+                                      synth.seed_for(5, 200 + k))
+        res, wall = srv.run(reqs)
+        sres, swall = serve.serial(comps, reqs, ws, reg_out)
+        per_rate.append({"rate_rps": rate, "served": serve.latency_stats(res, wall),
+                         "serial": serve.latency_stats(sres, swall)})
+    out = {"workload": f"{len(comps)} resident {size}^3 f32 k^-5/3 GRFs (rel eb 1e-3); "
+                       "Poisson requests, box edge U[16,256] per axis, level U{1,2,3}",
+           "resident_gb": round(resident / 1e9, 3), "raw_gb": round(raw / 1e9, 3),
+           "slots": srv.nslots, "budget_gb": round(budget / 1e9, 2), "per_rate": per_rate}
+    del srv, comps, ws, reg_out
+    torch.cuda.empty_cache()
+    return out
 
 
 # --------------------------------------------------------------- oracle arm
@@ -463,6 +567,9 @@ def main():
                     "traffic": None if ratio is None else int(ratio * nbytes / cnt),
                     "algorithmic_bytes_per_launch": int(nbytes / cnt),
                     "launches_per_step": round(cnt / args.steps, 2)}
+    dev = torch.device("cuda", local_rank)
+    batched = None if args.no_batch else run_batched(args, dev)
+    served = None if args.no_serve else run_served(args, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(r["x_host"], args.eb)
@@ -486,6 +593,7 @@ def main():
         "compression_ratio": round(fb / r["comp_bytes"], 3),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": r["e2e"],
         "gpu_launches": int(r["launches"]), "clocks": r["clk"], "kernels": breakdown[:12],
+        "batched": batched, "served": served,
     }
     print(json.dumps(line), flush=True)
 

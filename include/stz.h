@@ -141,6 +141,89 @@ int stz_decompress_region(const void* comp_dev, size_t comp_bytes, const int64_t
                           int64_t* out_dims, void* ws_dev, size_t ws_bytes, void* stream);
 
 /*
+ * Batched form: compress n fields of any shapes and dtypes in one call.
+ * Each field's container is bit-identical to stz_compress's for the same
+ * field and bound (same stages and kernels); the call only arranges their
+ * launches: fields spread over `lanes` concurrent streams (largest first onto
+ * the least loaded lane), persistent kernels sized for SMs / sm_share_den,
+ * and with use_graph = 1 the whole batch captured once as a CUDA graph that
+ * later calls with the same job list replay with one graph launch (up to 8
+ * job lists are cached per process).  The paper compresses one field at a
+ * time (Sec. 4); this form has no counterpart there.
+ *
+ *   jobs[i]     one field: field_dev, dims/ndim/dtype, eb_mode/eb and its own
+ *               out_dev/out_cap and ws_dev/ws_bytes (>= stz_workspace_size),
+ *               all as for stz_compress; no two jobs may share a workspace
+ *   sizes_dev   device array of n u64 (8-byte aligned): receives the
+ *               container size of field i, with bit 63 set when out_cap was
+ *               too small (the low bits then hold the size needed)
+ *   opts        NULL for defaults (lanes 4, sm_share_den 1, no graph)
+ *   stream      the caller's stream; the batch is ordered after the work
+ *               queued on it before the call, and work queued after the call
+ *               waits for the whole batch
+ *
+ * Asynchronous: nothing is waited for.  Arguments are checked for every job
+ * before any work is queued (STZ_ERR_ARG / STZ_ERR_CAPACITY for a workspace
+ * that is too small).  Calls from several host threads are serialised.
+ */
+typedef struct {
+  const void* field_dev;
+  int64_t dims[3];
+  int ndim;
+  stz_dtype dtype;
+  stz_eb_mode eb_mode;
+  double eb;
+  void* out_dev;
+  size_t out_cap;
+  void* ws_dev;
+  size_t ws_bytes;
+} stz_field_job;
+
+typedef struct {
+  int lanes;         /* concurrent streams, 1..32 (0: 4) */
+  int sm_share_den;  /* persistent grids sized for SMs / den, 1..64 (0: 1) */
+  int use_graph;     /* 1: capture once, replay as one graph launch */
+} stz_batch_opts;
+
+int stz_compress_batch(int n, const stz_field_job* jobs, unsigned long long* sizes_dev,
+                       const stz_batch_opts* opts, void* stream);
+
+/* ---- serving support (no counterpart in the paper) ----
+ * A serving loop keeps containers resident and answers many region requests
+ * without waiting on the host per request: it parses each container's header
+ * once (the first STZ_HEADER_MAX_BYTES bytes, or the whole container if
+ * shorter, copied to the host), decodes each field's level-1 grid once with
+ * stz_decompress_progressive(level 1) and keeps it, and then issues
+ * stz_decompress_region_async for each request on a stream of its own. */
+#define STZ_HEADER_MAX_BYTES 1984
+
+/* Workspace bytes a region decode of [lo, hi) at `level` needs, given the
+ * header bytes; level1_given != 0 when the level-1 grid will be supplied.
+ * 0 on invalid arguments or a corrupt header. */
+size_t stz_region_workspace_size(const void* hdr_host, size_t hdr_bytes, size_t comp_bytes,
+                                 const int64_t* lo, const int64_t* hi, int level,
+                                 int level1_given);
+
+/*
+ * Region decode (as stz_decompress_region: Sec. 3.3 random access, values
+ * bitwise those of the full decode) that never waits on the host:
+ *   hdr_host, hdr_bytes  host copy of the container's first bytes (see above)
+ *   level1_dev           the field's decoded level-1 grid (output of
+ *                        stz_decompress_progressive at level 1, device), or
+ *                        NULL to decode the level-1 passes the box needs
+ *   status_dev           device u32 that receives 0, or a nonzero status when
+ *                        the container proved corrupt during the decode
+ * Arguments are checked on the host (STZ_ERR_ARG / STZ_ERR_CAPACITY /
+ * STZ_ERR_CORRUPT for a bad header) before any work is queued on `stream`.
+ * Calls on different streams with different workspaces may overlap.
+ */
+int stz_decompress_region_async(const void* comp_dev, size_t comp_bytes, const void* hdr_host,
+                                size_t hdr_bytes, const void* level1_dev, const int64_t* lo,
+                                const int64_t* hi, int level, void* out_dev, size_t out_cap,
+                                int64_t* out_dims, void* ws_dev, size_t ws_bytes,
+                                uint32_t* status_dev, void* stream);
+
+/*
  * Region decompression without any device allocation, for callers that
  * cannot obtain device memory at the point of the call: a plug-in (an I/O
  * library filter, a visualisation reader) that its host application hands

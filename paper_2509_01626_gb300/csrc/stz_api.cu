@@ -242,6 +242,9 @@ static int parse_hdr(const uint8_t* h, size_t avail, size_t comp_bytes, Hdr* H) 
   return STZ_OK;
 }
 
+static_assert(STZ_HEADER_MAX_BYTES == kHeaderBytes + kMaxStreams * kDirEntryBytes,
+              "header bytes a serving loop keeps on the host");
+
 static int read_hdr(const void* comp, size_t comp_bytes, int on_device, cudaStream_t st, Hdr* H) {
   if (!comp || comp_bytes < (size_t)kHeaderBytes) return STZ_ERR_CORRUPT;
   const size_t want = kHeaderBytes + (size_t)kMaxStreams * kDirEntryBytes;
@@ -268,7 +271,10 @@ struct DecPlan {
   size_t dp, grid[kMaxLevels + 1], codes, lut, total;
 };
 
-static void plan_decode(const Geo& g, int k, const int64_t lo[3], const int64_t hi[3], DecPlan* P) {
+// skip_l1: the caller supplies the decoded level-1 grid (no level-1 buffer,
+// no level-1 code slots).
+static void plan_decode(const Geo& g, int k, const int64_t lo[3], const int64_t hi[3], DecPlan* P,
+                        bool skip_l1 = false) {
   memset(P, 0, sizeof(*P));
   P->k = k;
   const int64_t sk = level_stride(g.L, k);
@@ -297,10 +303,10 @@ static void plan_decode(const Geo& g, int k, const int64_t lo[3], const int64_t 
   const StreamGeo& s0 = g.s[0];
   for (int a = 0; a < 3; a++) {
     P->sm[0].lo[a] = 0;
-    P->sm[0].cnt[a] = s0.nb[a];
+    P->sm[0].cnt[a] = skip_l1 ? 0 : s0.nb[a];
   }
   P->sm[0].base = 0;
-  nslots += s0.nchunks;
+  if (!skip_l1) nslots += s0.nchunks;
   for (int j = 2; j <= k; j++) {
     for (int a = 0; a < 3; a++) {
       const int64_t clo = P->A[j][a] / 2, chi = cdiv(P->B[j][a], 2);
@@ -326,7 +332,7 @@ static void plan_decode(const Geo& g, int k, const int64_t lo[3], const int64_t 
   size_t o = 0;
   P->dp = o;
   o += al256(sizeof(DevParams));
-  for (int j = 1; j < (k > 1 ? k : 2); j++) {
+  for (int j = skip_l1 ? 2 : 1; j < (k > 1 ? k : 2); j++) {
     P->grid[j] = o;
     int64_t e[3] = {P->B[j][0] - P->A[j][0], P->B[j][1] - P->A[j][1], P->B[j][2] - P->A[j][2]};
     o += al256(ps * (size_t)vol(e));
@@ -336,6 +342,149 @@ static void plan_decode(const Geo& g, int k, const int64_t lo[3], const int64_t 
   P->lut = o;
   o += al256(4 * (size_t)g.nstreams * kLutSize);
   P->total = o;
+}
+
+// ------------------------------------------------------------ launch share
+namespace {
+thread_local int tl_share_num = 1, tl_share_den = 1;
+}
+
+void set_launch_share(int num, int den) {
+  tl_share_num = num > 0 ? num : 1;
+  tl_share_den = den > 0 ? den : 1;
+}
+
+int launch_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int v = (int)((int64_t)sms * tl_share_num / tl_share_den);
+  return v > 0 ? v : 1;
+}
+
+// ------------------------------------------------------------- compression
+// Argument checks of stz_compress; fills the job (geometry, workspace plan).
+int compress_check(const void* field_dev, const int64_t* dims, int ndim, int dtype, int eb_mode,
+                   double eb, void* out_dev, size_t out_cap, void* ws_dev, size_t ws_bytes,
+                   CompressJob* j) {
+  int64_t n[3];
+  if (dims3(dims, ndim, n) != STZ_OK) return STZ_ERR_ARG;
+  if (dtype != STZ_F32 && dtype != STZ_F64) return STZ_ERR_ARG;
+  if (eb_mode != STZ_EB_ABS && eb_mode != STZ_EB_REL) return STZ_ERR_ARG;
+  if (!(eb > 0.0) || !isfinite(eb)) return STZ_ERR_ARG;
+  if (!field_dev || !out_dev || !ws_dev) return STZ_ERR_ARG;
+  if (((uintptr_t)field_dev % 16) || ((uintptr_t)out_dev % 8) || ((uintptr_t)ws_dev % 256))
+    return STZ_ERR_ARG;
+  memset(j, 0, sizeof(*j));
+  make_geo(n, ndim, dtype, kLevels, default_brick(ndim), &j->g);
+  if (ws_bytes < plan_compress(j->g).total) return STZ_ERR_CAPACITY;
+  j->field = field_dev;
+  j->eb_mode = eb_mode;
+  j->eb = eb;
+  j->out = out_dev;
+  j->out_cap = out_cap;
+  j->ws = ws_dev;
+  return STZ_OK;
+}
+
+// Queues every stage of one compression on st without waiting for it.
+// no_coop: run the level-1 passes as plain launches (no cooperative launch),
+// as needed inside a captured graph whose branches run concurrently.
+int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, CompressDev* d) {
+  const Geo& g = j.g;
+  const int64_t* n = g.n;
+  const int dtype = g.dtype;
+  const int eb_mode = j.eb_mode;
+  const double eb = j.eb;
+  const void* field_dev = j.field;
+  const size_t out_cap = j.out_cap;
+  WsPlan w = plan_compress(g);
+  uint8_t* ws = (uint8_t*)j.ws;
+  DevParams* dp = (DevParams*)(ws + w.dp);
+  uint16_t* codes = (uint16_t*)(ws + w.codes);
+  uint32_t* hist = (uint32_t*)(ws + w.hist);
+  uint32_t* chunk_out = (uint32_t*)(ws + w.chunk_out);
+  uint32_t* chunk_words = (uint32_t*)(ws + w.chunk_words);
+  unsigned long long* word_off = (unsigned long long*)(ws + w.word_off);
+  unsigned long long* out_off = (unsigned long long*)(ws + w.out_off);
+  uint16_t* enc = (uint16_t*)(ws + w.enc);
+  BookDev* books = (BookDev*)(ws + w.books);
+  LayoutDev* lay = (LayoutDev*)(ws + w.lay);
+  uint8_t* out = (uint8_t*)j.out;
+  int rc = STZ_OK;
+#define STZ_TRY(x)          \
+  do {                      \
+    rc = (x);               \
+    if (rc != STZ_OK) return rc; \
+  } while (0)
+  STZ_TRY(cuda_ok(cudaMemsetAsync(hist, 0, 4 * (size_t)g.nstreams * kAlphabet, st)));
+  STZ_TRY(cuda_ok(cudaMemsetAsync(chunk_out, 0, 4 * (size_t)g.total_chunks, st)));
+  STZ_TRY(launch_params_init(dp, st));
+  if (eb_mode == STZ_EB_REL) STZ_TRY(launch_range(field_dev, dtype, vol(n), dp, st));
+  STZ_TRY(launch_params(dp, dtype, eb_mode, eb, g.L, kRadius, st));
+  {
+    BaseArgs a;
+    memset(&a, 0, sizeof(a));
+    a.geo = g;
+    a.dp = dp;
+    a.field = field_dev;
+    a.g1 = ws + w.grid[1];
+    a.codes = codes;
+    a.chunk_outliers = chunk_out;
+    for (int d = 0; d < 3; d++) {
+      a.sm.lo[d] = 0;
+      a.sm.cnt[d] = g.s[0].nb[d];
+    }
+    a.sm.base = g.s[0].chunk0;
+    STZ_TRY(no_coop ? launch_base_nocoop(a, false, st) : launch_base(a, false, st));
+  }
+  STZ_TRY(launch_stream_hist(g, 0, codes, hist, st));
+  for (int l = 2; l <= g.L; l++) {
+    LevelArgs a;
+    memset(&a, 0, sizeof(a));
+    a.geo = g;
+    a.level = l;
+    a.dp = dp;
+    a.field = field_dev;
+    int64_t M[3], m[3];
+    grid_extent(g.n, g.L, l - 1, M);
+    grid_extent(g.n, g.L, l, m);
+    a.coarse = ws + w.grid[l - 1];
+    a.fine = l < g.L ? (void*)(ws + w.grid[l]) : nullptr;
+    for (int d = 0; d < 3; d++) {
+      a.clo[d] = 0;
+      a.chi[d] = M[d];
+      a.flo[d] = 0;
+      a.fhi[d] = m[d];
+      a.tlo[d] = 0;
+      a.tcnt[d] = cdiv(M[d], g.b[d]);
+    }
+    a.codes = codes;
+    a.chunk_outliers = chunk_out;
+    a.hist = hist;
+    for (int K = 1; K <= 7; K++) {
+      const StreamGeo& sg = g.s[1 + 7 * (l - 2) + K - 1];
+      for (int d = 0; d < 3; d++) {
+        a.sm[K].lo[d] = 0;
+        a.sm[K].cnt[d] = sg.nb[d];
+      }
+      a.sm[K].base = sg.chunk0;
+    }
+    STZ_TRY(launch_level(a, false, st));
+  }
+  STZ_TRY(launch_codebook(g, hist, enc, books, st));
+  STZ_TRY(launch_chunk_words(g, codes, enc, chunk_words, st));
+  STZ_TRY(launch_scan2(chunk_words, chunk_out, g.total_chunks,
+                       (unsigned long long*)(ws + w.scan_sums), word_off, out_off, st));
+  STZ_TRY(launch_layout(g, dp, eb_mode, word_off, out_off, books, lay, out, out_cap, st));
+  STZ_TRY(launch_sections(g, lay, books, word_off, dp, out, st));
+  STZ_TRY(launch_pack(g, codes, enc, word_off, lay->s, out, dp, st));
+  STZ_TRY(launch_outliers(g, codes, field_dev, chunk_out, out_off, lay, dp, out, st));
+#undef STZ_TRY
+  d->total = &lay->total;
+  d->payload_words = word_off + g.total_chunks;
+  d->status = &dp->status;
+  return STZ_OK;
 }
 
 }  // namespace stz
@@ -396,112 +545,27 @@ size_t stz_workspace_size(const int64_t* dims, int ndim, stz_dtype dtype) {
 int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype dtype,
                  stz_eb_mode eb_mode, double eb, void* out_dev, size_t out_cap,
                  size_t* out_bytes, void* ws_dev, size_t ws_bytes, void* stream) {
-  int64_t n[3];
-  if (dims3(dims, ndim, n) != STZ_OK) return STZ_ERR_ARG;
-  if (dtype != STZ_F32 && dtype != STZ_F64) return STZ_ERR_ARG;
-  if (eb_mode != STZ_EB_ABS && eb_mode != STZ_EB_REL) return STZ_ERR_ARG;
-  if (!(eb > 0.0) || !isfinite(eb)) return STZ_ERR_ARG;
-  if (!field_dev || !out_dev || !ws_dev || !out_bytes) return STZ_ERR_ARG;
-  const size_t ps = dtype == STZ_F32 ? 4 : 8;
-  if (((uintptr_t)field_dev % 16) || ((uintptr_t)out_dev % 8) || ((uintptr_t)ws_dev % 256))
-    return STZ_ERR_ARG;
+  if (!out_bytes) return STZ_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  Geo g;
-  make_geo(n, ndim, dtype, kLevels, default_brick(ndim), &g);
-  WsPlan w = plan_compress(g);
-  if (ws_bytes < w.total) return STZ_ERR_CAPACITY;
-  uint8_t* ws = (uint8_t*)ws_dev;
-  DevParams* dp = (DevParams*)(ws + w.dp);
-  uint16_t* codes = (uint16_t*)(ws + w.codes);
-  uint32_t* hist = (uint32_t*)(ws + w.hist);
-  uint32_t* chunk_out = (uint32_t*)(ws + w.chunk_out);
-  uint32_t* chunk_words = (uint32_t*)(ws + w.chunk_words);
-  unsigned long long* word_off = (unsigned long long*)(ws + w.word_off);
-  unsigned long long* out_off = (unsigned long long*)(ws + w.out_off);
-  uint16_t* enc = (uint16_t*)(ws + w.enc);
-  BookDev* books = (BookDev*)(ws + w.books);
-  LayoutDev* lay = (LayoutDev*)(ws + w.lay);
-  uint8_t* out = (uint8_t*)out_dev;
-  int rc = STZ_OK;
-#define STZ_TRY(x)          \
-  do {                      \
-    rc = (x);               \
-    if (rc != STZ_OK) return rc; \
-  } while (0)
-  STZ_TRY(cuda_ok(cudaMemsetAsync(hist, 0, 4 * (size_t)g.nstreams * kAlphabet, st)));
-  STZ_TRY(cuda_ok(cudaMemsetAsync(chunk_out, 0, 4 * (size_t)g.total_chunks, st)));
-  STZ_TRY(launch_params_init(dp, st));
-  if (eb_mode == STZ_EB_REL) STZ_TRY(launch_range(field_dev, dtype, vol(n), dp, st));
-  STZ_TRY(launch_params(dp, dtype, eb_mode, eb, g.L, kRadius, st));
-  {
-    BaseArgs a;
-    memset(&a, 0, sizeof(a));
-    a.geo = g;
-    a.dp = dp;
-    a.field = field_dev;
-    a.g1 = ws + w.grid[1];
-    a.codes = codes;
-    a.chunk_outliers = chunk_out;
-    for (int d = 0; d < 3; d++) {
-      a.sm.lo[d] = 0;
-      a.sm.cnt[d] = g.s[0].nb[d];
-    }
-    a.sm.base = g.s[0].chunk0;
-    STZ_TRY(launch_base(a, false, st));
-  }
-  STZ_TRY(launch_stream_hist(g, 0, codes, hist, st));
-  for (int l = 2; l <= g.L; l++) {
-    LevelArgs a;
-    memset(&a, 0, sizeof(a));
-    a.geo = g;
-    a.level = l;
-    a.dp = dp;
-    a.field = field_dev;
-    int64_t M[3], m[3];
-    grid_extent(g.n, g.L, l - 1, M);
-    grid_extent(g.n, g.L, l, m);
-    a.coarse = ws + w.grid[l - 1];
-    a.fine = l < g.L ? (void*)(ws + w.grid[l]) : nullptr;
-    for (int d = 0; d < 3; d++) {
-      a.clo[d] = 0;
-      a.chi[d] = M[d];
-      a.flo[d] = 0;
-      a.fhi[d] = m[d];
-      a.tlo[d] = 0;
-      a.tcnt[d] = cdiv(M[d], g.b[d]);
-    }
-    a.codes = codes;
-    a.chunk_outliers = chunk_out;
-    a.hist = hist;
-    for (int K = 1; K <= 7; K++) {
-      const StreamGeo& sg = g.s[1 + 7 * (l - 2) + K - 1];
-      for (int d = 0; d < 3; d++) {
-        a.sm[K].lo[d] = 0;
-        a.sm[K].cnt[d] = sg.nb[d];
-      }
-      a.sm[K].base = sg.chunk0;
-    }
-    STZ_TRY(launch_level(a, false, st));
-  }
-  STZ_TRY(launch_codebook(g, hist, enc, books, st));
-  STZ_TRY(launch_chunk_words(g, codes, enc, chunk_words, st));
-  STZ_TRY(launch_scan2(chunk_words, chunk_out, g.total_chunks,
-                       (unsigned long long*)(ws + w.scan_sums), word_off, out_off, st));
-  STZ_TRY(launch_layout(g, dp, eb_mode, word_off, out_off, books, lay, out, out_cap, st));
-  STZ_TRY(launch_sections(g, lay, books, word_off, dp, out, st));
-  STZ_TRY(launch_pack(g, codes, enc, word_off, lay->s, out, dp, st));
-  STZ_TRY(launch_outliers(g, codes, field_dev, chunk_out, out_off, lay, dp, out, st));
+  CompressJob j;
+  int rc = compress_check(field_dev, dims, ndim, dtype, eb_mode, eb, out_dev, out_cap, ws_dev,
+                          ws_bytes, &j);
+  if (rc != STZ_OK) return rc;
+  CompressDev d;
+  rc = compress_enqueue(j, false, st, &d);
+  if (rc != STZ_OK) return rc;
   unsigned long long total = 0, payload_words = 0;
   uint32_t status = 0;
-  STZ_TRY(cuda_ok(cudaMemcpyAsync(&total, &lay->total, 8, cudaMemcpyDeviceToHost, st)));
-  STZ_TRY(cuda_ok(cudaMemcpyAsync(&payload_words, word_off + g.total_chunks, 8,
-                                  cudaMemcpyDeviceToHost, st)));
-  STZ_TRY(cuda_ok(cudaMemcpyAsync(&status, &dp->status, 4, cudaMemcpyDeviceToHost, st)));
-  STZ_TRY(cuda_ok(cudaStreamSynchronize(st)));
-#undef STZ_TRY
+  if ((rc = cuda_ok(cudaMemcpyAsync(&total, d.total, 8, cudaMemcpyDeviceToHost, st))) != STZ_OK)
+    return rc;
+  if ((rc = cuda_ok(cudaMemcpyAsync(&payload_words, d.payload_words, 8, cudaMemcpyDeviceToHost,
+                                    st))) != STZ_OK)
+    return rc;
+  if ((rc = cuda_ok(cudaMemcpyAsync(&status, d.status, 4, cudaMemcpyDeviceToHost, st))) != STZ_OK)
+    return rc;
+  if ((rc = cuda_ok(cudaStreamSynchronize(st))) != STZ_OK) return rc;
   *out_bytes = (size_t)total;
   prof_add_bytes("k_pack", 4.0 * (double)payload_words);
-  (void)ps;
   if (status & kStatCapacity) return STZ_ERR_CAPACITY;
   return STZ_OK;
 }
@@ -529,14 +593,30 @@ int stz_info(const void* comp, size_t comp_bytes, int comp_on_device, stz_info_t
   return rc;
 }
 
-static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* lo_in,
+// Options of a decode beyond the plain calls: a header parsed beforehand (no
+// read-back from the device), a decoded level-1 grid to start from, and a
+// device word that receives the status instead of a wait at the end.
+struct DecOpts {
+  const Hdr* hdr;
+  const void* l1;
+  uint32_t* status_out;
+};
+
+static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* lo_in,
                        const int64_t* hi_in, int level, int whole, void* out_dev, size_t out_cap,
-                       int64_t* out_dims, void* ws_dev, size_t ws_bytes, cudaStream_t st) {
+                       int64_t* out_dims, void* ws_dev, size_t ws_bytes, cudaStream_t st,
+                       const DecOpts& o) {
   if (!comp_dev || !out_dev || !ws_dev) return STZ_ERR_ARG;
   if (((uintptr_t)comp_dev % 8) || ((uintptr_t)ws_dev % 256)) return STZ_ERR_ARG;
   Hdr H;
-  int rc = read_hdr(comp_dev, comp_bytes, 1, st, &H);
+  int rc = STZ_OK;
+  if (o.hdr)
+    H = *o.hdr;
+  else
+    rc = read_hdr(comp_dev, comp_bytes, 1, st, &H);
   if (rc != STZ_OK) return rc;
+  const bool have_l1 = o.l1 != nullptr;
+  if (have_l1 && ((uintptr_t)o.l1 % (H.dtype == STZ_F32 ? 4 : 8))) return STZ_ERR_ARG;
   if (level == 0) level = H.L;
   if (level < 1 || level > H.L) return STZ_ERR_ARG;
   const size_t ps = H.dtype == STZ_F32 ? 4 : 8;
@@ -561,7 +641,7 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
       if (lo[a] < 0 || hi[a] > g.n[a] || lo[a] >= hi[a]) return STZ_ERR_ARG;
   }
   DecPlan P;
-  plan_decode(g, level, lo, hi, &P);
+  plan_decode(g, level, lo, hi, &P, have_l1);
   int64_t od[3];
   for (int a = 0; a < 3; a++) od[a] = imax(0, P.OB[a] - P.OA[a]);
   if (out_dims) {
@@ -603,7 +683,7 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
   const int ns_needed = 1 + 7 * (level - 1);
   int64_t nblocks = 0;
   double dec_bytes = 0.0;
-  for (int s = 0; s < ns_needed; s++) {
+  for (int s = have_l1 ? 1 : 0; s < ns_needed; s++) {
     if (g.s[s].nsym == 0) continue;
     tb.lut_sid[tb.nlut++] = s;
     const SlotMap& sm = P.sm[s];
@@ -635,8 +715,8 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
   STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
   const uint8_t* sec0 = comp + H.d[0].sect_off;
   SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps, H.nsub);
-  uint8_t* g1buf = ws + P.grid[1];
-  {
+  uint8_t* g1buf = have_l1 ? (uint8_t*)o.l1 : ws + P.grid[1];
+  if (!have_l1) {
     BaseArgs a;
     memset(&a, 0, sizeof(a));
     a.geo = g;
@@ -708,11 +788,78 @@ static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* l
     a.status = status;
     STZ_TRY(launch_level(a, true, st));
   }
+  if (o.status_out) {
+    STZ_TRY(cuda_ok(cudaMemcpyAsync(o.status_out, status, 4, cudaMemcpyDeviceToDevice, st)));
+    return STZ_OK;
+  }
   uint32_t hstat = 0;
   STZ_TRY(cuda_ok(cudaMemcpyAsync(&hstat, status, 4, cudaMemcpyDeviceToHost, st)));
   STZ_TRY(cuda_ok(cudaStreamSynchronize(st)));
 #undef STZ_TRY
   return (hstat & kStatCorrupt) ? STZ_ERR_CORRUPT : STZ_OK;
+}
+
+static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* lo_in,
+                       const int64_t* hi_in, int level, int whole, void* out_dev, size_t out_cap,
+                       int64_t* out_dims, void* ws_dev, size_t ws_bytes, cudaStream_t st) {
+  DecOpts o;
+  memset(&o, 0, sizeof(o));
+  return decode_core(comp_dev, comp_bytes, lo_in, hi_in, level, whole, out_dev, out_cap, out_dims,
+                     ws_dev, ws_bytes, st, o);
+}
+
+// Box in the container's axis order (2D: y, x) to field coordinates (z, y, x).
+static void box3(const Hdr& H, const int64_t* lo_in, const int64_t* hi_in, int64_t lo[3],
+                 int64_t hi[3]) {
+  if (H.ndim == 3) {
+    for (int a = 0; a < 3; a++) {
+      lo[a] = lo_in[a];
+      hi[a] = hi_in[a];
+    }
+  } else {
+    lo[0] = 0;
+    hi[0] = 1;
+    lo[1] = lo_in[0];
+    hi[1] = hi_in[0];
+    lo[2] = lo_in[1];
+    hi[2] = hi_in[1];
+  }
+}
+
+size_t stz_region_workspace_size(const void* hdr_host, size_t hdr_bytes, size_t comp_bytes,
+                                 const int64_t* lo_in, const int64_t* hi_in, int level,
+                                 int level1_given) {
+  if (!hdr_host || !lo_in || !hi_in) return 0;
+  Hdr H;
+  if (parse_hdr((const uint8_t*)hdr_host, hdr_bytes, comp_bytes, &H) != STZ_OK) return 0;
+  if (level < 1 || level > H.L) return 0;
+  int64_t lo[3], hi[3];
+  box3(H, lo_in, hi_in, lo, hi);
+  Geo g;
+  make_geo(H.n, H.ndim, H.dtype, H.L, H.b, &g);
+  for (int a = 0; a < 3; a++)
+    if (lo[a] < 0 || hi[a] > g.n[a] || lo[a] >= hi[a]) return 0;
+  DecPlan P;
+  plan_decode(g, level, lo, hi, &P, level1_given != 0);
+  return P.total;
+}
+
+int stz_decompress_region_async(const void* comp_dev, size_t comp_bytes, const void* hdr_host,
+                                size_t hdr_bytes, const void* level1_dev, const int64_t* lo,
+                                const int64_t* hi, int level, void* out_dev, size_t out_cap,
+                                int64_t* out_dims, void* ws_dev, size_t ws_bytes,
+                                uint32_t* status_dev, void* stream) {
+  if (!hdr_host || !status_dev || level < 1) return STZ_ERR_ARG;
+  if ((uintptr_t)status_dev % 4) return STZ_ERR_ARG;
+  Hdr H;
+  const int rc = parse_hdr((const uint8_t*)hdr_host, hdr_bytes, comp_bytes, &H);
+  if (rc != STZ_OK) return rc;
+  DecOpts o;
+  o.hdr = &H;
+  o.l1 = level1_dev;
+  o.status_out = status_dev;
+  return decode_core(comp_dev, comp_bytes, lo, hi, level, 0, out_dev, out_cap, out_dims, ws_dev,
+                     ws_bytes, (cudaStream_t)stream, o);
 }
 
 int stz_decompress_full(const void* comp_dev, size_t comp_bytes, void* out_dev, size_t out_cap,

@@ -329,7 +329,7 @@ template <typename T, bool DEC>
 static int run_passes(const BaseArgs& a, cudaStream_t s);
 
 template <typename T, bool DEC>
-static int run_coop(const BaseArgs& a, cudaStream_t s) {
+static int run_coop(const BaseArgs& a, cudaStream_t s, bool allow_coop = true) {
   int64_t m[3];
   grid_extent(a.geo.n, a.geo.L, 1, m);
   if (m[0] * m[1] * m[2] >= ((int64_t)1 << 31)) return STZ_ERR_ARG;  // 32-bit level-1 indexing
@@ -478,8 +478,8 @@ static int run_coop(const BaseArgs& a, cudaStream_t s) {
   if (per_sm < 1) return STZ_ERR_CUDA;
   int64_t blocks = imin((int64_t)sms * imin(per_sm, 4), imax(1, cdiv(biggest, 256)));
   void* args[] = {(void*)&a, (void*)&pl};
-  cudaError_t e;
-  {
+  cudaError_t e = cudaErrorNotSupported;
+  if (allow_coop) {
     ProfScope ps_(DEC ? "k_base_coop_dec" : "k_base_coop_enc", s);
     e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)blocks), dim3(256), args, 0,
                                     s);
@@ -553,6 +553,12 @@ int launch_base(const BaseArgs& a, bool decode, cudaStream_t s) {
   if (a.geo.dtype == STZ_F32)
     return decode ? run_coop<float, true>(a, s) : run_coop<float, false>(a, s);
   return decode ? run_coop<double, true>(a, s) : run_coop<double, false>(a, s);
+}
+
+int launch_base_nocoop(const BaseArgs& a, bool decode, cudaStream_t s) {
+  if (a.geo.dtype == STZ_F32)
+    return decode ? run_coop<float, true>(a, s, false) : run_coop<float, false>(a, s, false);
+  return decode ? run_coop<double, true>(a, s, false) : run_coop<double, false>(a, s, false);
 }
 
 // One launch per pass (kept for comparison and for devices without

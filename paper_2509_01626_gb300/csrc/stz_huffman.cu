@@ -405,9 +405,7 @@ __global__ void __launch_bounds__(256) k_chunk_words(const __grid_constant__ Geo
 int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc, uint32_t* words,
                        cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = launch_sms();
   const int64_t grid = imin(g.total_chunks, (int64_t)sms * 8);
   ProfScope ps_("k_chunk_words", s, 2.0 * (double)total_symbols(g));  // one read of the codes
   k_chunk_words<<<(unsigned)grid, 256, 0, s>>>(g, codes, enc, words);
@@ -645,9 +643,7 @@ int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
       cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess)
     return STZ_ERR_CUDA;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = launch_sms();
   const int64_t grid = imin(g.total_chunks, (int64_t)sms * 8);
   // reads the codes; the payload it writes is added once its size is known
   ProfScope ps_("k_pack", s, 2.0 * (double)total_symbols(g));

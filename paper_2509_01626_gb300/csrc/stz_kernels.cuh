@@ -31,6 +31,9 @@ struct BaseArgs {
 };
 int launch_base(const BaseArgs& a, bool decode, cudaStream_t s);
 int launch_base_passes(const BaseArgs& a, bool decode, cudaStream_t s);
+// the coarse single-block phase, then one plain launch per remaining pass (no
+// cooperative launch: for graphs whose branches run concurrently)
+int launch_base_nocoop(const BaseArgs& a, bool decode, cudaStream_t s);
 
 // ---- stz_level.cu: levels 2..L (multi-dimensional cubic prediction) ----
 struct LevelArgs {
@@ -129,5 +132,32 @@ int launch_sections(const Geo& g, const LayoutDev* lay, const BookDev* books,
 int launch_outliers(const Geo& g, const uint16_t* codes, const void* field,
                     const uint32_t* chunk_outliers, const unsigned long long* out_off,
                     const LayoutDev* lay, const DevParams* dp, uint8_t* out, cudaStream_t s);
+
+// ---- stz_api.cu: one compression as a queue of launches ----
+struct CompressJob {
+  Geo g;
+  const void* field;
+  int eb_mode;
+  double eb;
+  void* out;
+  size_t out_cap;
+  void* ws;
+};
+// device words a queued compression leaves behind
+struct CompressDev {
+  const unsigned long long* total;          // container bytes
+  const unsigned long long* payload_words;  // payload words of all chunks
+  const uint32_t* status;                   // kStat* bits
+};
+int compress_check(const void* field_dev, const int64_t* dims, int ndim, int dtype, int eb_mode,
+                   double eb, void* out_dev, size_t out_cap, void* ws_dev, size_t ws_bytes,
+                   CompressJob* j);
+int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, CompressDev* d);
+
+// SMs that one launch sizes a persistent grid for: all of them, unless the
+// calling thread set a share (the batched form runs several fields' kernels
+// side by side and gives each a part of the GPU).
+int launch_sms();
+void set_launch_share(int num, int den);
 
 }  // namespace stz

@@ -666,12 +666,7 @@ __global__ void __launch_bounds__(256) k_level_shell(const __grid_constant__ Lev
 }
 
 // ---------------------------------------------------------------- launchers
-static int sm_count() {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms;
-}
+static int sm_count() { return launch_sms(); }
 
 template <typename T, bool DEC>
 static int run_level_generic(const LevelArgs& a, double bytes, cudaStream_t s) {

@@ -64,8 +64,12 @@ void resolve_locked() {
 }  // namespace
 
 void prof_begin(const char* name, cudaStream_t s, int* slot, double bytes) {
-  g_launches.fetch_add(1);
   *slot = -1;
+  // a launch into a graph being captured runs when the graph does: it is
+  // counted at each graph launch (prof_count_launches), and never timed
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
+  g_launches.fetch_add(1);
   if (!g_enabled.load()) return;
   std::lock_guard<std::mutex> lk(g_mu);
   Rec r;
@@ -78,6 +82,8 @@ void prof_begin(const char* name, cudaStream_t s, int* slot, double bytes) {
   g_recs.push_back(r);
   *slot = (int)g_recs.size() - 1;
 }
+
+void prof_count_launches(unsigned long long n) { g_launches.fetch_add(n); }
 
 void prof_end(int slot, cudaStream_t s) {
   if (slot < 0) return;

@@ -163,9 +163,7 @@ int launch_params_init(DevParams* dp, cudaStream_t s) {
 }
 
 int launch_range(const void* field, int dtype, int64_t n, DevParams* dp, cudaStream_t s) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = launch_sms();
   int64_t per = dtype == STZ_F32 ? 4 : 2;
   int64_t want = cdiv(cdiv(n, per), 256);
   int blocks = (int)imin(imax(want, 1), (int64_t)sms * 8);

@@ -1,0 +1,185 @@
+"""Served form: a request loop over compressed fields resident on the device.
+
+Region requests (box, level) arrive over time.  ``Server.run`` admits them
+as slots free up -- the device-memory budget is carved into slots, each with
+a workspace and an output buffer large enough for the largest request -- and
+launches every admitted request at once, each on its slot's stream, through
+``stz_decompress_region_async``: no host wait per request, so requests that
+arrive while others are on the GPU join the next launches and their kernels
+overlap with the running ones (continuous batching).  Each field's level-1
+grid is decoded once when the field is loaded and reused by every request
+(it is bitwise what each request would decode), and its header is parsed
+from a host copy.  Completion is polled with events; latency = completion
+time - arrival time, on the host clock.
+
+``serial`` is the plain path for comparison: one synchronous
+``stz_decompress_region`` per request, in arrival order.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+import torch
+
+from . import stz
+
+
+@dataclasses.dataclass
+class Request:
+    arrival: float            # seconds after the start of the run
+    field: int
+    lo: tuple
+    hi: tuple
+    level: int
+
+
+@dataclasses.dataclass
+class Result:
+    request: Request
+    latency: float            # seconds, arrival to completion seen by the host
+    shape: tuple
+    status: int
+    out: torch.Tensor | None  # kept when the server was asked to
+
+
+class _Field:
+    def __init__(self, comp: torch.Tensor, cache_level1: bool):
+        self.comp = comp
+        self.meta = stz.info(comp)
+        self.hdr = stz.header_bytes(comp)
+        self.level1 = stz.decompress_progressive(comp, 1).clone() if cache_level1 else None
+
+
+def poisson_requests(shapes, n: int, rate: float, seed: int, emin: int = 16, emax: int = 256,
+                     levels=(1, 2, 3)) -> list[Request]:
+    """n requests with exponential inter-arrival gaps (rate per second), a
+    uniformly chosen field, per-axis box edge uniform in [emin, emax]
+    (clipped to the field) with origin uniform inside, and a uniform level."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    out = []
+    for i in range(n):
+        f = int(rng.integers(0, len(shapes)))
+        lo, hi = [], []
+        for d in shapes[f]:
+            e = int(min(d, rng.integers(emin, emax + 1)))
+            o = int(rng.integers(0, d - e + 1))
+            lo.append(o)
+            hi.append(o + e)
+        lv = int(levels[int(rng.integers(0, len(levels)))])
+        out.append(Request(float(t[i]), f, tuple(lo), tuple(hi), lv))
+    return out
+
+
+class Server:
+    def __init__(self, containers, budget_bytes: int, max_edge: int = 256, max_slots: int = 32,
+                 cache_level1: bool = True, device=None):
+        self.device = device or containers[0].device
+        self.max_edge = int(max_edge)
+        self.fields = [_Field(c, cache_level1) for c in containers]
+        # the largest request: a max_edge box at full resolution.  Where a box
+        # sits changes how many bricks (of at most 16 cells = 64 points at
+        # level 2) it touches, so the workspace is sized for a box 128 points
+        # wider, which covers every placement; the output for max_edge.
+        slot_ws, slot_out = 0, 0
+        for f in self.fields:
+            shape = f.meta["shape"]
+            lo = tuple(0 for _ in shape)
+            hi = tuple(min(max_edge + 128, d) for d in shape)
+            L = f.meta["levels"]
+            ws = stz.region_workspace_size(f.hdr, f.comp.numel(), lo, hi, L,
+                                           f.level1 is not None)
+            if ws == 0:
+                raise ValueError("cannot size the region workspace")
+            npts = 1
+            for d in shape:
+                npts *= min(max_edge, d)
+            slot_ws = max(slot_ws, ws)
+            slot_out = max(slot_out, npts * (8 if f.meta["dtype"] == torch.float64 else 4))
+        self.slot_bytes = slot_ws + slot_out
+        self.nslots = int(max(1, min(max_slots, budget_bytes // self.slot_bytes)))
+        self.ws = [torch.empty(slot_ws, dtype=torch.uint8, device=self.device)
+                   for _ in range(self.nslots)]
+        self.outs = [torch.empty(slot_out, dtype=torch.uint8, device=self.device)
+                     for _ in range(self.nslots)]
+        self.status = torch.zeros(self.nslots, dtype=torch.int32, device=self.device)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.nslots)]
+        self.events = [torch.cuda.Event() for _ in range(self.nslots)]
+
+    def _launch(self, slot: int, r: Request):
+        f = self.fields[r.field]
+        if any(b - a > self.max_edge for a, b in zip(r.lo, r.hi)):
+            raise ValueError(f"box edge above the server's maximum {self.max_edge}: {r}")
+        dt = f.meta["dtype"]
+        out = self.outs[slot].view(dt)
+        shape = stz.decompress_region_async(f.comp, f.hdr, r.lo, r.hi, r.level, out,
+                                            self.ws[slot], self.status[slot:slot + 1],
+                                            level1=f.level1, stream=self.streams[slot])
+        self.events[slot].record(self.streams[slot])
+        return shape
+
+    def run(self, requests, keep_outputs: bool = False, realtime: bool = True):
+        """Serve the requests (sorted by arrival); returns the results in
+        completion order and the wall time of the run."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting = collections.deque()
+        free = list(range(self.nslots - 1, -1, -1))
+        inflight = {}
+        results = []
+        t0 = time.perf_counter()
+        while pending or waiting or inflight:
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0].arrival <= now):
+                waiting.append(pending.popleft())
+            # admit every waiting request a slot is free for, and launch them
+            while waiting and free:
+                r = waiting.popleft()
+                slot = free.pop()
+                inflight[slot] = (r, self._launch(slot, r))
+            # completions
+            done = [s for s in inflight if self.events[s].query()]
+            if done:
+                now = time.perf_counter() - t0
+                for s in done:
+                    r, shape = inflight.pop(s)
+                    out = None
+                    if keep_outputs:
+                        n = int(np.prod(shape)) if len(shape) else 0
+                        out = self.outs[s].view(self.fields[r.field].meta["dtype"])[:n] \
+                            .reshape(shape).clone()
+                    st = int(self.status[s].item()) if keep_outputs else 0
+                    results.append(Result(r, now - r.arrival, shape, st, out))
+                    free.append(s)
+        wall = time.perf_counter() - t0
+        return results, wall
+
+
+def serial(containers, requests, workspace: torch.Tensor, out: torch.Tensor,
+           realtime: bool = True, keep_outputs: bool = False):
+    """Plain per-request path: one synchronous stz_decompress_region each, in
+    arrival order.  Returns results and wall time."""
+    metas = [stz.info(c) for c in containers]
+    results = []
+    t0 = time.perf_counter()
+    for r in sorted(requests, key=lambda r: r.arrival):
+        if realtime:
+            while time.perf_counter() - t0 < r.arrival:
+                pass
+        m = metas[r.field]
+        y = stz.decompress_region(containers[r.field], r.lo, r.hi, r.level,
+                                  out=out.view(m["dtype"]), workspace=workspace, meta=m)
+        now = time.perf_counter() - t0
+        results.append(Result(r, now - r.arrival, tuple(y.shape), 0,
+                              y.clone() if keep_outputs else None))
+    return results, time.perf_counter() - t0
+
+
+def latency_stats(results, wall: float) -> dict:
+    lat = np.array([r.latency for r in results]) * 1e3
+    return {"requests": len(results), "throughput_rps": round(len(results) / wall, 1),
+            "p50_ms": round(float(np.percentile(lat, 50)), 4),
+            "p99_ms": round(float(np.percentile(lat, 99)), 4),
+            "mean_ms": round(float(lat.mean()), 4)}

@@ -42,6 +42,28 @@ class _Info(ctypes.Structure):
     ]
 
 
+class FieldJob(ctypes.Structure):
+    """stz_field_job: one field of a stz_compress_batch call."""
+    _fields_ = [
+        ("field_dev", ctypes.c_void_p),
+        ("dims", ctypes.c_int64 * 3),
+        ("ndim", ctypes.c_int),
+        ("dtype", ctypes.c_int),
+        ("eb_mode", ctypes.c_int),
+        ("eb", ctypes.c_double),
+        ("out_dev", ctypes.c_void_p),
+        ("out_cap", ctypes.c_size_t),
+        ("ws_dev", ctypes.c_void_p),
+        ("ws_bytes", ctypes.c_size_t),
+    ]
+
+
+class BatchOpts(ctypes.Structure):
+    """stz_batch_opts: launch arrangement of a batch (never changes bytes)."""
+    _fields_ = [("lanes", ctypes.c_int), ("sm_share_den", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_ulonglong),
                 ("total_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double)]
@@ -75,6 +97,13 @@ def lib() -> ctypes.CDLL:
                                             sz, vp]
         L.stz_decompress_region_noalloc.argtypes = [vp, sz, i64p, i64p, ctypes.c_int, vp, sz,
                                                     i64p, vp]
+        L.stz_compress_batch.argtypes = [ctypes.c_int, ctypes.POINTER(FieldJob), vp,
+                                         ctypes.POINTER(BatchOpts), vp]
+        L.stz_region_workspace_size.restype = sz
+        L.stz_region_workspace_size.argtypes = [vp, sz, sz, i64p, i64p, ctypes.c_int,
+                                                ctypes.c_int]
+        L.stz_decompress_region_async.argtypes = [vp, sz, vp, sz, vp, i64p, i64p, ctypes.c_int,
+                                                  vp, sz, i64p, vp, sz, vp, vp]
         L.stz_launch_count.restype = ctypes.c_ulonglong
         L.stz_profile_enable.argtypes = [ctypes.c_int]
         L.stz_profile_read.argtypes = [ctypes.POINTER(_KernelTime), ctypes.c_int]
@@ -149,6 +178,19 @@ def compress(field: torch.Tensor, eb: float, mode: str = "rel", out: torch.Tenso
                             _stream(stream))
     _check(rc, "stz_compress")
     return out[: nbytes.value]
+
+
+def compress_batch(jobs, sizes_dev: torch.Tensor, opts: BatchOpts | None = None,
+                   stream=None) -> None:
+    """stz_compress_batch over a ctypes array of FieldJob; asynchronous.
+    sizes_dev: int64 CUDA tensor of len(jobs) entries receiving the sizes
+    (bit 63 set: that field's out_cap was too small)."""
+    if sizes_dev.dtype != torch.int64 or not sizes_dev.is_cuda or sizes_dev.numel() < len(jobs):
+        raise ValueError("sizes_dev must be an int64 CUDA tensor with one entry per job")
+    rc = lib().stz_compress_batch(len(jobs), jobs, ctypes.c_void_p(sizes_dev.data_ptr()),
+                                  ctypes.byref(opts) if opts is not None else None,
+                                  _stream(stream))
+    _check(rc, "stz_compress_batch")
 
 
 def info(comp: torch.Tensor) -> dict:
@@ -265,6 +307,38 @@ def decompress_region_noalloc(comp: torch.Tensor, lo, hi, level: int, out: torch
     for v in oshape:
         n *= v
     return out.reshape(-1)[:n].view(oshape)
+
+
+HEADER_MAX_BYTES = 1984  # STZ_HEADER_MAX_BYTES
+
+
+def header_bytes(comp: torch.Tensor) -> bytes:
+    """Host copy of a container's header and directory (one read)."""
+    n = min(comp.numel(), HEADER_MAX_BYTES)
+    return bytes(comp[:n].cpu().numpy().tobytes())
+
+
+def region_workspace_size(hdr: bytes, comp_bytes: int, lo, hi, level: int,
+                          level1_given: bool) -> int:
+    return int(lib().stz_region_workspace_size(hdr, len(hdr), int(comp_bytes), _i64(lo), _i64(hi),
+                                               int(level), 1 if level1_given else 0))
+
+
+def decompress_region_async(comp: torch.Tensor, hdr: bytes, lo, hi, level: int,
+                            out: torch.Tensor, workspace: torch.Tensor, status: torch.Tensor,
+                            level1: torch.Tensor | None = None, stream=None):
+    """stz_decompress_region_async: queues the decode on `stream` and returns
+    the output shape (slowest first) without waiting; `status` (int32 CUDA
+    tensor, one entry) becomes nonzero if the container proved corrupt."""
+    od = (ctypes.c_int64 * 3)()
+    rc = lib().stz_decompress_region_async(
+        ctypes.c_void_p(comp.data_ptr()), comp.numel(), hdr, len(hdr),
+        ctypes.c_void_p(level1.data_ptr()) if level1 is not None else None,
+        _i64(lo), _i64(hi), int(level), ctypes.c_void_p(out.data_ptr()),
+        out.numel() * out.element_size(), od, ctypes.c_void_p(workspace.data_ptr()),
+        workspace.numel(), ctypes.c_void_p(status.data_ptr()), _stream(stream))
+    _check(rc, "stz_decompress_region_async")
+    return tuple(int(v) for v in od[: len(lo)])
 
 
 def launch_count() -> int:

@@ -57,18 +57,23 @@ def sinusoids(shape, seed: int, n_terms: int = 16, fmin: float = 1.0, fmax: floa
 
 
 def grf(shape, seed: int, slope: float = -3.0, lognormal_sigma: float | None = 1.5,
-        dtype=np.float32, device: str = "cpu") -> np.ndarray:
+        dtype=np.float32, device: str = "cpu", white_source: str = "numpy",
+        as_tensor: bool = False):
     """Gaussian random field with P(k) ~ k**slope (k = 0 removed), unit
     standard deviation; with lognormal_sigma set, returns exp(sigma * g).
-    White noise from PCG64; the FFT filter runs in float64 with torch on
-    `device` (numpy when torch is absent)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    white = rng.standard_normal(size=shape)
+    White noise from PCG64 (white_source "numpy") or from a torch generator
+    on `device` seeded with `seed` ("torch", for fields too large to draw on
+    the host); the FFT filter runs in float64 with torch on `device` (numpy
+    when torch is absent).  as_tensor: return the torch tensor on `device`."""
     try:
         import torch
 
-        t = torch.from_numpy(white).to(device)
-        del white
+        if white_source == "torch":
+            gen = torch.Generator(device=device).manual_seed(int(seed))
+            t = torch.randn(shape, generator=gen, dtype=torch.float64, device=device)
+        else:
+            rng = np.random.Generator(np.random.PCG64(seed))
+            t = torch.from_numpy(rng.standard_normal(size=shape)).to(device)
         spec = torch.fft.rfftn(t)
         del t
         ks = []
@@ -92,8 +97,11 @@ def grf(shape, seed: int, slope: float = -3.0, lognormal_sigma: float | None = 1
         g = (g - g.mean()) / g.std()
         if lognormal_sigma is not None:
             g = torch.exp(lognormal_sigma * g)
-        return g.to(torch.float64 if dtype == np.float64 else torch.float32).cpu().numpy()
+        g = g.to(torch.float64 if dtype == np.float64 else torch.float32)
+        return g if as_tensor else g.cpu().numpy()
     except ImportError:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        white = rng.standard_normal(size=shape)
         spec = np.fft.rfftn(white)
         ks = []
         for a, n in enumerate(shape):
@@ -140,3 +148,80 @@ def random_boxes(shape, n: int, seed: int, emin: int, emax: int):
             hi.append(o + e)
         boxes.append((tuple(lo), tuple(hi)))
     return boxes
+
+
+def sinusoids_device(shape, seed: int, n_terms: int = 16, fmin: float = 1.0, fmax: float = 8.0,
+                     noise: float = 1e-3, dtype=np.float32, device: str = "cuda"):
+    """The recipe of ``sinusoids`` evaluated with torch on `device` (for
+    large fields): the terms' frequencies, amplitudes and phases are drawn
+    from PCG64 in the same order; the noise comes from a torch generator on
+    `device` seeded with `seed`.  Returns a torch tensor."""
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = len(shape)
+    ax = [torch.arange(n, dtype=torch.float64, device=device) / n for n in shape]
+    out = torch.zeros(shape, dtype=torch.float64, device=device)
+    for _ in range(n_terms):
+        f = rng.uniform(fmin, fmax, size=d)
+        amp = rng.normal()
+        phi = rng.uniform(0.0, 2.0 * np.pi)
+        ph = None
+        for a in range(d):
+            view = [1] * d
+            view[a] = -1
+            v = (2.0 * np.pi * float(f[a]) * ax[a]).view(view)
+            ph = v if ph is None else ph + v
+        out += float(amp) * torch.sin(ph + float(phi))
+    if noise > 0:
+        gen = torch.Generator(device=device).manual_seed(int(seed))
+        out += noise * torch.randn(shape, generator=gen, dtype=torch.float64, device=device)
+    return out.to(torch.float64 if dtype == np.float64 else torch.float32)
+
+
+def banded2d_device(shape, seed: int, n_terms: int = 8, dtype=np.float32, device: str = "cuda"):
+    """The recipe of ``banded2d`` evaluated with torch on `device`."""
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ny, nx = shape
+    y = (torch.arange(ny, dtype=torch.float64, device=device) / ny)[:, None]
+    x = (torch.arange(nx, dtype=torch.float64, device=device) / nx)[None, :]
+    out = torch.zeros(shape, dtype=torch.float64, device=device)
+    for _ in range(n_terms):
+        fy, fx = rng.uniform(1.0, 8.0, size=2)
+        amp = rng.normal()
+        phi = rng.uniform(0, 2 * np.pi)
+        out += float(amp) * torch.sin(2 * np.pi * (float(fy) * y + float(fx) * x) + float(phi))
+    m = int(rng.integers(2, 9))
+    out += float(rng.normal()) * torch.cos(np.pi * y * m) * torch.ones_like(x)
+    return out.to(torch.float64 if dtype == np.float64 else torch.float32)
+
+
+def batch_workload(seed_index: int = 0):
+    """The mixed batch: 40 3D float32 fields with each dim uniform in
+    [64, 512] (8-term sinusoid sums with 1e-3 noise), 16 2D float32 fields
+    1800 x 3600 (sinusoids with latitude bands), 8 3D float64 fields 256^3
+    (smooth 4-term sums); per-field relative bound from {1e-2, 1e-3, 1e-4}.
+    Returns a list of (kind, shape, dtype, seed, eb)."""
+    rng = np.random.Generator(np.random.PCG64(seed_for(3, 1000 + seed_index)))
+    items = []
+    for i in range(40):
+        shape = tuple(int(v) for v in rng.integers(64, 513, size=3))
+        items.append(("sin3d", shape, np.float32, seed_for(3, i)))
+    for i in range(16):
+        items.append(("band2d", (1800, 3600), np.float32, seed_for(3, 40 + i)))
+    for i in range(8):
+        items.append(("smooth3d", (256, 256, 256), np.float64, seed_for(3, 56 + i)))
+    ebs = rng.choice(np.array([1e-2, 1e-3, 1e-4]), size=len(items))
+    return [it + (float(eb),) for it, eb in zip(items, ebs)]
+
+
+def make_batch_field(item, device: str = "cuda"):
+    kind, shape, dtype, seed, _ = item
+    if kind == "sin3d":
+        return sinusoids_device(shape, seed, n_terms=8, noise=1e-3, dtype=dtype, device=device)
+    if kind == "band2d":
+        return banded2d_device(shape, seed, dtype=dtype, device=device)
+    return sinusoids_device(shape, seed, n_terms=4, fmin=1.0, fmax=3.0, noise=0.0, dtype=dtype,
+                            device=device)

@@ -101,3 +101,45 @@ def test_host_header_parser_rejects_corruption(stzmod):
         assert rc in (0, stzmod.ERR_CORRUPT, stzmod.ERR_ARG)
         hits += rc != 0
     assert hits > 100
+
+
+def test_batch_argument_errors_need_no_gpu(stzmod):
+    L = stzmod.lib()
+    jobs = (stzmod.FieldJob * 2)()
+    sizes = ctypes.c_void_p(256)
+    assert L.stz_compress_batch(0, jobs, sizes, None, None) == stzmod.ERR_ARG
+    assert L.stz_compress_batch(2, None, sizes, None, None) == stzmod.ERR_ARG
+    assert L.stz_compress_batch(2, jobs, None, None, None) == stzmod.ERR_ARG
+    o = stzmod.BatchOpts()
+    o.lanes = 33
+    assert L.stz_compress_batch(2, jobs, sizes, ctypes.byref(o), None) == stzmod.ERR_ARG
+    # zeroed jobs (no dims, null pointers) are rejected before any CUDA call
+    o.lanes = 2
+    assert L.stz_compress_batch(2, jobs, sizes, ctypes.byref(o), None) == stzmod.ERR_ARG
+
+
+def test_region_sizes_and_async_errors_need_no_gpu(stzmod):
+    L = stzmod.lib()
+    comp = np.fromfile(os.path.join(GOLDEN, "sin3d_f32_22x19x27.stz"), dtype=np.uint8)
+    hdr = bytes(comp[:stzmod.HEADER_MAX_BYTES].tobytes())
+    full = stzmod.region_workspace_size(hdr, comp.size, (0, 0, 0), (22, 19, 27), 3, False)
+    cached = stzmod.region_workspace_size(hdr, comp.size, (0, 0, 0), (22, 19, 27), 3, True)
+    small = stzmod.region_workspace_size(hdr, comp.size, (2, 3, 4), (6, 7, 8), 3, True)
+    assert full > cached > small > 0
+    assert stzmod.region_workspace_size(hdr, comp.size, (0, 0, 0), (23, 19, 27), 3, False) == 0
+    assert stzmod.region_workspace_size(hdr, comp.size, (0, 0, 0), (2, 2, 2), 4, False) == 0
+    assert stzmod.region_workspace_size(b"xxxx" + hdr[4:], comp.size, (0, 0, 0), (2, 2, 2), 3,
+                                        False) == 0
+    # header checks and box checks happen before any CUDA call
+    lo = (ctypes.c_int64 * 3)(0, 0, 0)
+    hi = (ctypes.c_int64 * 3)(2, 2, 2)
+    od = (ctypes.c_int64 * 3)()
+    dev = ctypes.c_void_p(1 << 20)
+    bad = b"xxxx" + hdr[4:]
+    assert L.stz_decompress_region_async(dev, comp.size, bad, len(bad), None, lo, hi, 3, dev,
+                                         64, od, dev, 1 << 20, dev, None) == stzmod.ERR_CORRUPT
+    assert L.stz_decompress_region_async(dev, comp.size, None, 0, None, lo, hi, 3, dev, 64, od,
+                                         dev, 1 << 20, dev, None) == stzmod.ERR_ARG
+    hi_bad = (ctypes.c_int64 * 3)(2, 2, 99)
+    assert L.stz_decompress_region_async(dev, comp.size, hdr, len(hdr), None, lo, hi_bad, 3, dev,
+                                         64, od, dev, 1 << 20, dev, None) == stzmod.ERR_ARG
