@@ -344,71 +344,87 @@ __device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t* wsum, u
   return x - v + (w > 0 ? wsum[w - 1] : 0u);
 }
 
-// 8 consecutive symbols of a chunk per thread: codes and lengths
-__device__ __forceinline__ int load8(const uint16_t* c, int i0, int64_t cnt, const uint16_t* e,
-                                     uint32_t (&code)[8], uint32_t (&len)[8]) {
-  uint16_t sym[8];
-  if (i0 + 8 <= cnt) {
-    const uint4 v = *(const uint4*)(c + i0);
+
+// Encode tables of every stream in shared memory (g.nstreams x 2R u16).
+__device__ __forceinline__ void stage_enc(const Geo& g, const uint16_t* __restrict__ enc,
+                                          uint16_t* senc) {
+  const int n16 = g.nstreams * kAlphabet / 8;
+  for (int i = threadIdx.x; i < n16; i += blockDim.x)
+    ((uint4*)senc)[i] = __ldg((const uint4*)enc + i);
+  __syncthreads();
+}
+
+// Up to 8 symbols [i, min(i + 8, end)) of a chunk: their encode entries
+// (code << 4 | length; 0 past the end).
+__device__ __forceinline__ void enc8(const uint16_t* __restrict__ c, int i, int end,
+                                     const uint16_t* e, uint32_t (&ent)[8]) {
+  if (i + 8 <= end) {
+    const uint4 v = __ldg((const uint4*)(c + i));
     const uint32_t u[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      sym[2 * k] = (uint16_t)(u[k] & 0xFFFFu);
-      sym[2 * k + 1] = (uint16_t)(u[k] >> 16);
+      ent[2 * k] = e[u[k] & 0xFFFFu];
+      ent[2 * k + 1] = e[u[k] >> 16];
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < 8; k++) sym[k] = i0 + k < cnt ? c[i0 + k] : (uint16_t)0xFFFF;
+    for (int k = 0; k < 8; k++) ent[k] = i + k < end ? (uint32_t)e[__ldg(c + i + k)] : 0u;
   }
-  int bits = 0;
+}
+
+// One warp per chunk; lane l owns the chunk's symbols [64 l, 64 l + 64).
+constexpr int kLaneSyms = 64;
+static_assert(32 * kLaneSyms >= kBrick3D[0] * kBrick3D[1] * kBrick3D[2] &&
+                  32 * kLaneSyms >= kBrick2D[0] * kBrick2D[1] * kBrick2D[2],
+              "a warp covers a brick");
+
+// Bits of this lane's symbols.
+__device__ __forceinline__ uint32_t lane_bits(const uint16_t* __restrict__ c, int s0, int s1,
+                                              const uint16_t* e) {
+  uint32_t bits = 0;
+  for (int i = s0; i < s1; i += 8) {
+    uint32_t ent[8];
+    enc8(c, i, s1, e, ent);
 #pragma unroll
-  for (int k = 0; k < 8; k++) {
-    const uint32_t ent = sym[k] == 0xFFFF ? 0u : (uint32_t)__ldg(e + sym[k]);
-    code[k] = ent >> 4;
-    len[k] = ent & 15u;
-    bits += (int)len[k];
+    for (int k = 0; k < 8; k++) bits += ent[k] & 15u;
   }
   return bits;
 }
 
-// payload words per chunk: one block per chunk, 8 symbols per thread
+// payload words per chunk
 __global__ void __launch_bounds__(256) k_chunk_words(const __grid_constant__ Geo g,
                                                      const uint16_t* __restrict__ codes,
                                                      const uint16_t* __restrict__ enc,
                                                      uint32_t* __restrict__ words) {
-  __shared__ uint32_t wsum[2][8];
-  __shared__ int s_sid[2], s_cnt[2];
-  int par = 0;
-  for (int64_t j = blockIdx.x; j < g.total_chunks; j += gridDim.x, par ^= 1) {
-    if (threadIdx.x == 0) chunk_sid_cnt(g, j, s_sid[par], s_cnt[par]);
-    __syncthreads();
-    const int sid = s_sid[par];
-    const int64_t cnt = s_cnt[par];
-    const uint16_t* c = codes + j * g.bvol;
-    const uint16_t* e = enc + (int64_t)sid * kAlphabet;
-    uint32_t bits = 0;
-    for (int i0 = threadIdx.x * 8; i0 < cnt; i0 += 256 * 8) {
-      uint32_t code[8], len[8];
-      bits += (uint32_t)load8(c, i0, cnt, e, code, len);
-    }
+  extern __shared__ __align__(16) uint16_t senc[];
+  stage_enc(g, enc, senc);
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < g.total_chunks;
+       j += nwarps) {
+    int sid, cnt;
+    chunk_sid_cnt(g, j, sid, cnt);
+    const int s0 = lane * kLaneSyms, s1 = min(cnt, s0 + kLaneSyms);
+    uint32_t bits = lane_bits(codes + j * g.bvol, s0, s1, senc + sid * kAlphabet);
     for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
-    if ((threadIdx.x & 31) == 0) wsum[par][threadIdx.x >> 5] = bits;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t t = 0;
-      for (int k = 0; k < 8; k++) t += wsum[par][k];
-      words[j] = (t + 31) >> 5;
-    }
+    if (lane == 0) words[j] = (bits + 31) >> 5;
   }
 }
+
+static int enc_smem(const Geo& g) { return (int)(sizeof(uint16_t) * (size_t)g.nstreams * kAlphabet); }
 
 int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc, uint32_t* words,
                        cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
+  if (g.bvol > 32 * kLaneSyms) return STZ_ERR_ARG;
+  const int smem = enc_smem(g);
+  if (cudaFuncSetAttribute(k_chunk_words, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
+    return STZ_ERR_CUDA;
   const int sms = launch_sms();
-  const int64_t grid = imin(g.total_chunks, (int64_t)sms * 8);
+  const int64_t grid = imin(cdiv(g.total_chunks, 8), (int64_t)sms * 3);
   ProfScope ps_("k_chunk_words", s, 2.0 * (double)total_symbols(g));  // one read of the codes
-  k_chunk_words<<<(unsigned)grid, 256, 0, s>>>(g, codes, enc, words);
+  k_chunk_words<<<(unsigned)grid, 256, smem, s>>>(g, codes, enc, words);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -547,6 +563,14 @@ int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long 
 // (at most 96) bits in registers and ORs them into at most 4 words of the
 // chunk held in shared memory; the words are stored with coalesced writes.
 // The sub-chunk offsets are the bit positions of symbols u * ceil(n / 4).
+// Payload of every chunk.  One warp per chunk: each lane counts its
+// symbols' bits, a warp scan gives each lane its first bit, then each lane
+// appends its codes serially to a 64-bit accumulator and stores the 32-bit
+// words that fill.  A word that straddles two lanes' runs (only the first
+// word of a lane whose run does not start on a word) is stored by the lane
+// before, which ORs in the part the later lane hands it by shuffle.  Every
+// lane but the chunk's last holds 64 symbols, so at least 64 bits: only
+// neighbouring lanes ever share a word.
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
                                               const uint16_t* __restrict__ codes,
                                               const uint16_t* __restrict__ enc,
@@ -554,83 +578,73 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
                                               const SectDev* __restrict__ sect,
                                               uint8_t* __restrict__ out,
                                               const DevParams* __restrict__ dp) {
-  extern __shared__ uint32_t wbuf[];
-  __shared__ uint32_t wsum[8];
-  __shared__ int s_sid, s_cnt;
+  extern __shared__ __align__(16) uint16_t senc[];
   if (dp->status & kStatCapacity) return;
-  for (int64_t j = blockIdx.x; j < g.total_chunks; j += gridDim.x) {
-    __syncthreads();  // the previous chunk's words are written out
-    if (threadIdx.x == 0) chunk_sid_cnt(g, j, s_sid, s_cnt);
-    __syncthreads();
-    const int sid = s_sid;
-    const int cnt = s_cnt;
-    const int nw = (int)(word_off[j + 1] - word_off[j]);
-    for (int i = threadIdx.x; i < nw; i += 256) wbuf[i] = 0;
+  stage_enc(g, enc, senc);
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < g.total_chunks;
+       j += nwarps) {
+    int sid, cnt;
+    chunk_sid_cnt(g, j, sid, cnt);
+    const uint16_t* e = senc + sid * kAlphabet;
     const uint16_t* c = codes + j * g.bvol;
-    const uint16_t* e = enc + (int64_t)sid * kAlphabet;
+    const int s0 = lane * kLaneSyms, s1 = min(cnt, s0 + kLaneSyms);
+    const uint32_t bits = lane_bits(c, s0, s1, e);
+    uint32_t incl = bits;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t p = incl - bits;  // first bit of this lane, from the chunk start
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     const SectDev& sd = sect[sid];
-    const int q = (cnt + kNSub - 1) / kNSub;
     uint16_t* so =
         (uint16_t*)(out + sd.sect_off + sd.off_subs) + (j - g.s[sid].chunk0) * (kNSub - 1);
-    uint32_t base = 0;
-    for (int r0 = 0; r0 < cnt; r0 += 256 * 8) {
-      const int i0 = r0 + threadIdx.x * 8;
-      uint32_t code[8], len[8];
-      const uint32_t bits = (uint32_t)load8(c, i0, cnt, e, code, len);
-      uint32_t total;
-      __syncthreads();  // wbuf zeroed; scan scratch free
-      const uint32_t p = base + block_scan_256(bits, wsum, &total);
-      // sub-chunk starts inside this thread's 8 symbols
-#pragma unroll
-      for (int u = 1; u < kNSub; u++) {
-        const int b = u * q;
-        if (b >= i0 && b < i0 + 8 && b < cnt) {
-          uint32_t off = p;
-#pragma unroll
-          for (int k = 0; k < 8; k++)
-            if (k < b - i0) off += len[k];
-          so[u - 1] = (uint16_t)off;
-        }
-      }
-      // the thread's bit string, left-aligned in 128 bits (hi:lo)
-      unsigned long long hi = 0, lo = 0;
+    uint32_t* dst = (uint32_t*)(out + sd.sect_off + sd.off_payload) + (word_off[j] - sd.word0);
+    const int q = (cnt + kNSub - 1) / kNSub;
+    if (lane == 0)
+      for (int u = 1; u < kNSub; u++)
+        if (u * q >= cnt) so[u - 1] = (uint16_t)total;
+    uint32_t widx = p >> 5, nacc = p & 31u, run = p, first_part = 0;
+    bool first_pending = nacc != 0;
+    unsigned long long acc = 0;
+    for (int i = s0; i < s1; i += 8) {
+      uint32_t ent[8];
+      enc8(c, i, s1, e, ent);
 #pragma unroll
       for (int k = 0; k < 8; k++) {
-        const uint32_t L = len[k];
-        if (L) {
-          hi = (hi << L) | (lo >> (64 - L));
-          lo = (lo << L) | code[k];
-        }
-      }
-      if (bits) {
-        const uint32_t sh = 128u - bits;  // left-align
-        if (sh >= 64) {
-          hi = lo << (sh - 64);
-          lo = 0;
-        } else if (sh > 0) {
-          hi = (hi << sh) | (lo >> (64 - sh));
-          lo <<= sh;
-        }
-        const uint32_t r = p & 31u, wi = p >> 5;
-        if (r) {  // shift right by r into 160 bits: hi:lo:x
-          lo = (lo >> r) | (hi << (64 - r));
-          hi >>= r;
-        }
-        const uint32_t wds[4] = {(uint32_t)(hi >> 32), (uint32_t)hi, (uint32_t)(lo >> 32),
-                                 (uint32_t)lo};
-        const uint32_t nwt = (r + bits + 31) >> 5;
+        const uint32_t L = ent[k] & 15u;
+        if (L == 0) continue;  // past the end
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-          if (k < (int)nwt && wds[k]) atomicOr(&wbuf[wi + k], wds[k]);
+        for (int u = 1; u < kNSub; u++)
+          if (i + k == u * q) so[u - 1] = (uint16_t)run;
+        run += L;
+        acc = (acc << L) | (ent[k] >> 4);
+        nacc += L;
+        if (nacc >= 32) {
+          nacc -= 32;
+          const uint32_t w = (uint32_t)(acc >> nacc);
+          if (first_pending) {
+            first_part = w;
+            first_pending = false;
+          } else {
+            dst[widx] = w;
+          }
+          widx++;
+        }
       }
-      base += total;
     }
-    if (threadIdx.x == 0)
-      for (int u = 1; u < kNSub; u++)
-        if (u * q >= cnt) so[u - 1] = (uint16_t)base;
-    __syncthreads();
-    uint32_t* dst = (uint32_t*)(out + sd.sect_off + sd.off_payload) + (word_off[j] - sd.word0);
-    for (int i = threadIdx.x; i < nw; i += 256) dst[i] = wbuf[i];
+    bool has_last = nacc > 0 && s1 > s0;
+    uint32_t last = has_last ? (uint32_t)(acc << (32u - nacc)) : 0u;
+    if (has_last && first_pending) {  // the lane's whole run lies in its first word
+      first_part = last;
+      has_last = false;
+    }
+    uint32_t from_next = __shfl_down_sync(0xffffffffu, first_part, 1);
+    if (lane == 31) from_next = 0;
+    if (has_last) dst[widx] = last | from_next;
   }
 }
 
@@ -638,13 +652,13 @@ int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
                 const unsigned long long* word_off, const SectDev* sect, uint8_t* out,
                 const DevParams* dp, cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
-  const size_t smem = sizeof(uint32_t) * (size_t)((g.bvol * kMaxCodeLen + 31) / 32 + 1);
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
+  if (g.bvol > 32 * kLaneSyms) return STZ_ERR_ARG;
+  const int smem = enc_smem(g);
+  if (cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
     return STZ_ERR_CUDA;
   const int sms = launch_sms();
-  const int64_t grid = imin(g.total_chunks, (int64_t)sms * 8);
+  const int64_t grid = imin(cdiv(g.total_chunks, 8), (int64_t)sms * 3);
   // reads the codes; the payload it writes is added once its size is known
   ProfScope ps_("k_pack", s, 2.0 * (double)total_symbols(g));
   k_pack<<<(unsigned)grid, 256, smem, s>>>(g, codes, enc, word_off, sect, out, dp);
