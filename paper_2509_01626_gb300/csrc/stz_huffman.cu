@@ -345,30 +345,22 @@ __device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t* wsum, u
 }
 
 
-// Encode tables of every stream in shared memory (g.nstreams x 2R u16).
-__device__ __forceinline__ void stage_enc(const Geo& g, const uint16_t* __restrict__ enc,
-                                          uint16_t* senc) {
-  const int n16 = g.nstreams * kAlphabet / 8;
-  for (int i = threadIdx.x; i < n16; i += blockDim.x)
-    ((uint4*)senc)[i] = __ldg((const uint4*)enc + i);
-  __syncthreads();
-}
-
 // Up to 8 symbols [i, min(i + 8, end)) of a chunk: their encode entries
-// (code << 4 | length; 0 past the end).
+// (code << 4 | length; 0 past the end).  The tables (4 KiB per stream) are
+// read through the read-only cache.
 __device__ __forceinline__ void enc8(const uint16_t* __restrict__ c, int i, int end,
-                                     const uint16_t* e, uint32_t (&ent)[8]) {
+                                     const uint16_t* __restrict__ e, uint32_t (&ent)[8]) {
   if (i + 8 <= end) {
     const uint4 v = __ldg((const uint4*)(c + i));
     const uint32_t u[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      ent[2 * k] = e[u[k] & 0xFFFFu];
-      ent[2 * k + 1] = e[u[k] >> 16];
+      ent[2 * k] = __ldg(e + (u[k] & 0xFFFFu));
+      ent[2 * k + 1] = __ldg(e + (u[k] >> 16));
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < 8; k++) ent[k] = i + k < end ? (uint32_t)e[__ldg(c + i + k)] : 0u;
+    for (int k = 0; k < 8; k++) ent[k] = i + k < end ? (uint32_t)__ldg(e + __ldg(c + i + k)) : 0u;
   }
 }
 
@@ -378,9 +370,9 @@ static_assert(32 * kLaneSyms >= kBrick3D[0] * kBrick3D[1] * kBrick3D[2] &&
                   32 * kLaneSyms >= kBrick2D[0] * kBrick2D[1] * kBrick2D[2],
               "a warp covers a brick");
 
-// Bits of this lane's symbols.
-__device__ __forceinline__ uint32_t lane_bits(const uint16_t* __restrict__ c, int s0, int s1,
-                                              const uint16_t* e) {
+// Bits of the symbols [s0, s1) of a chunk.
+__device__ __forceinline__ uint32_t run_bits(const uint16_t* __restrict__ c, int s0, int s1,
+                                             const uint16_t* __restrict__ e) {
   uint32_t bits = 0;
   for (int i = s0; i < s1; i += 8) {
     uint32_t ent[8];
@@ -396,35 +388,23 @@ __global__ void __launch_bounds__(256) k_chunk_words(const __grid_constant__ Geo
                                                      const uint16_t* __restrict__ codes,
                                                      const uint16_t* __restrict__ enc,
                                                      uint32_t* __restrict__ words) {
-  extern __shared__ __align__(16) uint16_t senc[];
-  stage_enc(g, enc, senc);
   const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < g.total_chunks;
-       j += nwarps) {
-    int sid, cnt;
-    chunk_sid_cnt(g, j, sid, cnt);
-    const int s0 = lane * kLaneSyms, s1 = min(cnt, s0 + kLaneSyms);
-    uint32_t bits = lane_bits(codes + j * g.bvol, s0, s1, senc + sid * kAlphabet);
-    for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
-    if (lane == 0) words[j] = (bits + 31) >> 5;
-  }
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= g.total_chunks) return;
+  int sid, cnt;
+  chunk_sid_cnt(g, j, sid, cnt);
+  const int s0 = lane * kLaneSyms, s1 = min(cnt, s0 + kLaneSyms);
+  uint32_t bits = run_bits(codes + j * g.bvol, s0, s1, enc + (int64_t)sid * kAlphabet);
+  for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+  if (lane == 0) words[j] = (bits + 31) >> 5;
 }
-
-static int enc_smem(const Geo& g) { return (int)(sizeof(uint16_t) * (size_t)g.nstreams * kAlphabet); }
 
 int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc, uint32_t* words,
                        cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
   if (g.bvol > 32 * kLaneSyms) return STZ_ERR_ARG;
-  const int smem = enc_smem(g);
-  if (cudaFuncSetAttribute(k_chunk_words, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-      cudaSuccess)
-    return STZ_ERR_CUDA;
-  const int sms = launch_sms();
-  const int64_t grid = imin(cdiv(g.total_chunks, 8), (int64_t)sms * 3);
   ProfScope ps_("k_chunk_words", s, 2.0 * (double)total_symbols(g));  // one read of the codes
-  k_chunk_words<<<(unsigned)grid, 256, smem, s>>>(g, codes, enc, words);
+  k_chunk_words<<<(unsigned)cdiv(g.total_chunks, 8), 256, 0, s>>>(g, codes, enc, words);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -565,12 +545,13 @@ int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long 
 // The sub-chunk offsets are the bit positions of symbols u * ceil(n / 4).
 // Payload of every chunk.  One warp per chunk: each lane counts its
 // symbols' bits, a warp scan gives each lane its first bit, then each lane
-// appends its codes serially to a 64-bit accumulator and stores the 32-bit
-// words that fill.  A word that straddles two lanes' runs (only the first
-// word of a lane whose run does not start on a word) is stored by the lane
-// before, which ORs in the part the later lane hands it by shuffle.  Every
-// lane but the chunk's last holds 64 symbols, so at least 64 bits: only
-// neighbouring lanes ever share a word.
+// appends its codes, two at a time, to a 64-bit accumulator and stores the
+// 32-bit words that fill.  A word that straddles two lanes' runs (only the
+// first word of a lane whose run does not start on a word) is stored by the
+// lane before, which ORs in the part the later lane hands it by shuffle.
+// Every lane but the chunk's last holds 64 symbols, so at least 64 bits: only
+// neighbouring lanes ever share a word.  The lanes holding a sub-chunk start
+// sum the lengths before it for the sub-chunk's bit offset.
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
                                               const uint16_t* __restrict__ codes,
                                               const uint16_t* __restrict__ enc,
@@ -578,74 +559,73 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
                                               const SectDev* __restrict__ sect,
                                               uint8_t* __restrict__ out,
                                               const DevParams* __restrict__ dp) {
-  extern __shared__ __align__(16) uint16_t senc[];
   if (dp->status & kStatCapacity) return;
-  stage_enc(g, enc, senc);
   const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < g.total_chunks;
-       j += nwarps) {
-    int sid, cnt;
-    chunk_sid_cnt(g, j, sid, cnt);
-    const uint16_t* e = senc + sid * kAlphabet;
-    const uint16_t* c = codes + j * g.bvol;
-    const int s0 = lane * kLaneSyms, s1 = min(cnt, s0 + kLaneSyms);
-    const uint32_t bits = lane_bits(c, s0, s1, e);
-    uint32_t incl = bits;
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= g.total_chunks) return;
+  int sid, cnt;
+  chunk_sid_cnt(g, j, sid, cnt);
+  const uint16_t* e = enc + (int64_t)sid * kAlphabet;
+  const uint16_t* c = codes + j * g.bvol;
+  const int s0 = lane * kLaneSyms, s1 = min(cnt, s0 + kLaneSyms);
+  const uint32_t bits = run_bits(c, s0, s1, e);
+  uint32_t incl = bits;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t p = incl - bits;  // first bit of this lane, from the chunk start
+  const SectDev& sd = sect[sid];
+  uint16_t* so =
+      (uint16_t*)(out + sd.sect_off + sd.off_subs) + (j - g.s[sid].chunk0) * (kNSub - 1);
+  uint32_t* dst = (uint32_t*)(out + sd.sect_off + sd.off_payload) + (word_off[j] - sd.word0);
+  const int q = (cnt + kNSub - 1) / kNSub;
+#pragma unroll
+  for (int u = 1; u < kNSub; u++) {
+    const int bnd = u * q;
+    if (bnd >= cnt) {
+      if (lane == 31) so[u - 1] = (uint16_t)incl;  // the chunk's total
+    } else if (bnd >= s0 && bnd < s1) {
+      so[u - 1] = (uint16_t)(p + run_bits(c, s0, bnd, e));
     }
-    const uint32_t p = incl - bits;  // first bit of this lane, from the chunk start
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    const SectDev& sd = sect[sid];
-    uint16_t* so =
-        (uint16_t*)(out + sd.sect_off + sd.off_subs) + (j - g.s[sid].chunk0) * (kNSub - 1);
-    uint32_t* dst = (uint32_t*)(out + sd.sect_off + sd.off_payload) + (word_off[j] - sd.word0);
-    const int q = (cnt + kNSub - 1) / kNSub;
-    if (lane == 0)
-      for (int u = 1; u < kNSub; u++)
-        if (u * q >= cnt) so[u - 1] = (uint16_t)total;
-    uint32_t widx = p >> 5, nacc = p & 31u, run = p, first_part = 0;
-    bool first_pending = nacc != 0;
-    unsigned long long acc = 0;
-    for (int i = s0; i < s1; i += 8) {
-      uint32_t ent[8];
-      enc8(c, i, s1, e, ent);
+  }
+  uint32_t widx = p >> 5, nacc = p & 31u, first_part = 0;
+  bool first_pending = nacc != 0;
+  unsigned long long acc = 0;
+  for (int i = s0; i < s1; i += 8) {
+    uint32_t ent[8];
+    enc8(c, i, s1, e, ent);
 #pragma unroll
-      for (int k = 0; k < 8; k++) {
-        const uint32_t L = ent[k] & 15u;
-        if (L == 0) continue;  // past the end
-#pragma unroll
-        for (int u = 1; u < kNSub; u++)
-          if (i + k == u * q) so[u - 1] = (uint16_t)run;
-        run += L;
-        acc = (acc << L) | (ent[k] >> 4);
-        nacc += L;
-        if (nacc >= 32) {
-          nacc -= 32;
-          const uint32_t w = (uint32_t)(acc >> nacc);
-          if (first_pending) {
-            first_part = w;
-            first_pending = false;
-          } else {
-            dst[widx] = w;
-          }
-          widx++;
+    for (int k = 0; k < 8; k += 2) {
+      // two codes joined (at most 24 bits); past the end both are empty
+      const uint32_t L1 = ent[k + 1] & 15u;
+      const uint32_t L = (ent[k] & 15u) + L1;
+      const uint32_t code = ((ent[k] >> 4) << L1) | (ent[k + 1] >> 4);
+      acc = (acc << L) | code;
+      nacc += L;  // below 32 + 24: at most one word fills
+      if (nacc >= 32) {
+        nacc -= 32;
+        const uint32_t w = (uint32_t)(acc >> nacc);
+        if (first_pending) {
+          first_part = w;
+          first_pending = false;
+        } else {
+          dst[widx] = w;
         }
+        widx++;
       }
     }
-    bool has_last = nacc > 0 && s1 > s0;
-    uint32_t last = has_last ? (uint32_t)(acc << (32u - nacc)) : 0u;
-    if (has_last && first_pending) {  // the lane's whole run lies in its first word
-      first_part = last;
-      has_last = false;
-    }
-    uint32_t from_next = __shfl_down_sync(0xffffffffu, first_part, 1);
-    if (lane == 31) from_next = 0;
-    if (has_last) dst[widx] = last | from_next;
   }
+  bool has_last = nacc > 0 && s1 > s0;
+  const uint32_t last = has_last ? (uint32_t)(acc << (32u - nacc)) : 0u;
+  if (has_last && first_pending) {  // the lane's whole run lies in its first word
+    first_part = last;
+    has_last = false;
+  }
+  uint32_t from_next = __shfl_down_sync(0xffffffffu, first_part, 1);
+  if (lane == 31) from_next = 0;
+  if (has_last) dst[widx] = last | from_next;
 }
 
 int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
@@ -653,15 +633,9 @@ int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
                 const DevParams* dp, cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
   if (g.bvol > 32 * kLaneSyms) return STZ_ERR_ARG;
-  const int smem = enc_smem(g);
-  if (cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-      cudaSuccess)
-    return STZ_ERR_CUDA;
-  const int sms = launch_sms();
-  const int64_t grid = imin(cdiv(g.total_chunks, 8), (int64_t)sms * 3);
   // reads the codes; the payload it writes is added once its size is known
   ProfScope ps_("k_pack", s, 2.0 * (double)total_symbols(g));
-  k_pack<<<(unsigned)grid, 256, smem, s>>>(g, codes, enc, word_off, sect, out, dp);
+  k_pack<<<(unsigned)cdiv(g.total_chunks, 8), 256, 0, s>>>(g, codes, enc, word_off, sect, out, dp);
   return cuda_ok(cudaGetLastError());
 }
 
