@@ -593,6 +593,40 @@ int stz_info(const void* comp, size_t comp_bytes, int comp_on_device, stz_info_t
   return rc;
 }
 
+// A second stream per caller stream (and device): a decode runs the level-1
+// reconstruction there, beside the chunk decoding of the finer levels, joined
+// back by events before the finer levels need it.
+namespace {
+struct SideStream {
+  int dev;
+  cudaStream_t key, s;
+  cudaEvent_t fork, join;
+};
+std::mutex g_side_mu;
+SideStream g_side[64];
+int g_nside = 0;
+}  // namespace
+
+static const SideStream* side_of(cudaStream_t st) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  for (int i = 0; i < g_nside; i++)
+    if (g_side[i].dev == dev && g_side[i].key == st) return &g_side[i];
+  if (g_nside == 64) return nullptr;
+  SideStream e;
+  e.dev = dev;
+  e.key = st;
+  if (cudaStreamCreateWithFlags(&e.s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  if (cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e.join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  g_side[g_nside] = e;
+  return &g_side[g_nside++];
+}
+
 // Options of a decode beyond the plain calls: a header parsed beforehand (no
 // read-back from the device), a decoded level-1 grid to start from, and a
 // device word that receives the status instead of a wait at the end.
@@ -681,15 +715,19 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     d.nsub = H.nsub;
   }
   const int ns_needed = 1 + 7 * (level - 1);
-  int64_t nblocks = 0;
-  double dec_bytes = 0.0;
+  // chunk jobs: stream 0 (level 1) in tb0, the finer levels in tb, so that
+  // level 1 can be reconstructed while the finer levels' chunks decode
+  DecTables tb0 = tb;
+  int64_t nblocks = 0, nblocks0 = 0;
+  double dec_bytes = 0.0, dec_bytes0 = 0.0;
   for (int s = have_l1 ? 1 : 0; s < ns_needed; s++) {
     if (g.s[s].nsym == 0) continue;
     tb.lut_sid[tb.nlut++] = s;
     const SlotMap& sm = P.sm[s];
     const int64_t c = sm.cnt[0] * sm.cnt[1] * sm.cnt[2];
     if (c == 0) continue;
-    DecChunkJob& jb = tb.jobs[tb.njobs++];
+    DecTables& t = s == 0 ? tb0 : tb;
+    DecChunkJob& jb = t.jobs[t.njobs++];
     jb.sid = s;
     for (int a = 0; a < 3; a++) {
       jb.lo[a] = sm.lo[a];
@@ -698,13 +736,16 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     jb.slot_base = sm.base;
     jb.nchunks_job = c;
     // the job's share of the stream's codes (written) and payload (read)
-    if (H.d[s].nch > 0)
-      dec_bytes += (2.0 * (double)H.d[s].nsym + 4.0 * (double)H.d[s].pw) * (double)c /
-                   (double)H.d[s].nch;
-    jb.block0 = nblocks;
-    nblocks += cdiv(c * H.nsub, kDecThreads);
+    const double jbytes = H.d[s].nch > 0 ? (2.0 * (double)H.d[s].nsym + 4.0 * (double)H.d[s].pw) *
+                                               (double)c / (double)H.d[s].nch
+                                         : 0.0;
+    int64_t& nb = s == 0 ? nblocks0 : nblocks;
+    (s == 0 ? dec_bytes0 : dec_bytes) += jbytes;
+    jb.block0 = nb;
+    nb += cdiv(c * H.nsub, kDecThreads);
   }
   tb.nblocks = nblocks;
+  tb0.nblocks = nblocks0;
 #define STZ_TRY(x)               \
   do {                           \
     rc = (x);                    \
@@ -712,7 +753,15 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
   } while (0)
   STZ_TRY(cuda_ok(cudaMemsetAsync(dp, 0, sizeof(DevParams), st)));
   STZ_TRY(launch_lut(tb, lut, status, st));
-  STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
+  STZ_TRY(launch_decode_chunks(g, tb0, lut, codes, status, dec_bytes0, st));
+  // level 1 on the side stream when finer levels follow (joined below)
+  const SideStream* side = (!have_l1 && level > 1) ? side_of(st) : nullptr;
+  cudaStream_t st1 = st;
+  if (side) {
+    STZ_TRY(cuda_ok(cudaEventRecord(side->fork, st)));
+    STZ_TRY(cuda_ok(cudaStreamWaitEvent(side->s, side->fork, 0)));
+    st1 = side->s;
+  }
   const uint8_t* sec0 = comp + H.d[0].sect_off;
   SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps, H.nsub);
   uint8_t* g1buf = have_l1 ? (uint8_t*)o.l1 : ws + P.grid[1];
@@ -740,7 +789,12 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
       whole = whole && a.rlo[d] == 0 && a.rhi[d] == m1[d];
     }
     a.region = whole ? 0 : 1;
-    STZ_TRY(launch_base(a, true, st));
+    STZ_TRY(launch_base(a, true, st1));
+  }
+  STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
+  if (side) {
+    STZ_TRY(cuda_ok(cudaEventRecord(side->join, side->s)));
+    STZ_TRY(cuda_ok(cudaStreamWaitEvent(st, side->join, 0)));
   }
   if (level == 1) {
     int64_t m1[3];

@@ -110,7 +110,8 @@ struct CellAddr {
 
 STZ_HD CellAddr cell_addr(const StreamGeo& sg, const int32_t b[3], int64_t bvol,
                           const SlotMap& sm, int64_t c0, int64_t c1, int64_t c2) {
-  int64_t B0 = c0 / b[0], B1 = c1 / b[1], B2 = c2 / b[2];
+  // cells per axis are below 2^30: 32-bit divisions
+  int64_t B0 = (int32_t)c0 / b[0], B1 = (int32_t)c1 / b[1], B2 = (int32_t)c2 / b[2];
   int64_t l0 = imin(b[0], sg.e[0] - B0 * b[0]);
   int64_t l1 = imin(b[1], sg.e[1] - B1 * b[1]);
   int64_t l2 = imin(b[2], sg.e[2] - B2 * b[2]);

@@ -302,8 +302,9 @@ struct TileInfo {
 __device__ __forceinline__ void tile_info(const LevelArgs& a, int64_t tt, TileInfo& ti) {
   const Geo& geo = a.geo;
   const int l = a.level;
-  const int64_t Tb[3] = {a.tlo[0] + tt / (a.tcnt[1] * a.tcnt[2]),
-                         a.tlo[1] + (tt / a.tcnt[2]) % a.tcnt[1], a.tlo[2] + tt % a.tcnt[2]};
+  // tile counts and brick coordinates fit in 32 bits (cells per axis < 2^30)
+  const int t32 = (int)tt, n2 = (int)a.tcnt[2], n12 = (int)a.tcnt[1] * n2;
+  const int64_t Tb[3] = {a.tlo[0] + t32 / n12, a.tlo[1] + (t32 % n12) / n2, a.tlo[2] + t32 % n2};
   const int c0[3] = {(int)Tb[0] * kFBZ, (int)Tb[1] * kFBY, (int)Tb[2] * kFBX};
   const int tid = threadIdx.x;
   if (tid < 3) ti.c0[tid] = c0[tid];
@@ -332,8 +333,9 @@ __device__ __forceinline__ void tile_info(const LevelArgs& a, int64_t tt, TileIn
 // Issue the copies of tile tt's coarse grid (with halo) into `tile`.
 template <typename T>
 __device__ __forceinline__ void tile_prefetch(const LevelArgs& a, int64_t tt, T* tile) {
-  const int64_t Tb[3] = {a.tlo[0] + tt / (a.tcnt[1] * a.tcnt[2]),
-                         a.tlo[1] + (tt / a.tcnt[2]) % a.tcnt[1], a.tlo[2] + tt % a.tcnt[2]};
+  // tile counts and brick coordinates fit in 32 bits (cells per axis < 2^30)
+  const int t32 = (int)tt, n2 = (int)a.tcnt[2], n12 = (int)a.tcnt[1] * n2;
+  const int64_t Tb[3] = {a.tlo[0] + t32 / n12, a.tlo[1] + (t32 % n12) / n2, a.tlo[2] + t32 % n2};
   const int c0[3] = {(int)Tb[0] * kFBZ - 1, (int)Tb[1] * kFBY - 1, (int)Tb[2] * kFBX - 1};
   const T* coarse = (const T*)a.coarse;
   const int clo0 = (int)a.clo[0], clo1 = (int)a.clo[1], clo2 = (int)a.clo[2];
@@ -478,108 +480,6 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
   }
 }
 
-// A tile whose 8 x 16 x 16 cells are all interior, whose 7 bricks are whole
-// and (decoding) whose fine points all lie in the output box: the common
-// case.  Same arithmetic as fast_tile, without per-point bounds tests, with
-// the z walk unrolled (the register window rotates by renaming) and the
-// 7 code slots of a cell at fixed offsets lz * 256 + tid.
-template <typename T, bool DEC>
-__device__ __forceinline__ void fast_tile_in(const LevelArgs& a, const T* __restrict__ tile,
-                                             const TileInfo& ti, const QConst<T>& q, T two_eb,
-                                             uint32_t* hist, int xdz, int xdy, int xdx, int fe2,
-                                             int fdz) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int ly = tid >> 4, lx = tid & 15;
-  const int c0z = ti.c0[0], cy = ti.c0[1] + ly, cx = ti.c0[2] + lx;
-  const int tb = (kFEY + ly + 1) * kFEX + (lx + 1);
-  constexpr int kCell = kFBY * kFBX;
-  uint16_t* cp[7];
-#pragma unroll
-  for (int K = 1; K <= 7; K++) cp[K - 1] = a.codes + ti.slot[K] + tid;
-  const T* xp = DEC ? nullptr
-                    : (const T*)a.field + (int64_t)(2 * c0z) * xdz + (int64_t)(2 * cy) * xdy +
-                          (int64_t)(2 * cx) * xdx;
-  T* fp = a.fine ? (T*)a.fine + ((int64_t)(2 * c0z - (int)a.flo[0]) * (a.fhi[1] - a.flo[1]) +
-                                 (2 * cy - (int)a.flo[1])) *
-                                    (int64_t)fe2 +
-                       (2 * cx - (int)a.flo[2])
-                 : nullptr;
-  int off[7];  // offset of sub-block K's point from the cell's even point
-#pragma unroll
-  for (int K = 1; K <= 7; K++)
-    off[K - 1] = ((K >> 2) & 1) * xdz + ((K >> 1) & 1) * xdy + (K & 1) * xdx;
-  int foff[7];
-#pragma unroll
-  for (int K = 1; K <= 7; K++)
-    foff[K - 1] = ((K >> 2) & 1) * fdz + ((K >> 1) & 1) * fe2 + (K & 1);
-  T xv[7];
-  int cv[7];
-#pragma unroll
-  for (int K = 0; K < 7; K++) {
-    if (!DEC) xv[K] = __ldg(xp + off[K]);
-    else cv[K] = cp[K][0];
-  }
-  T w0[12], w1[12], w2[12], w3[12];
-  load_plane(w0, tile, tb - kFEZY);
-  load_plane(w1, tile, tb);
-  load_plane(w2, tile, tb + kFEZY);
-#pragma unroll
-  for (int lz = 0; lz < kFBZ; lz++) {
-    load_plane(w3, tile, tb + (lz + 2) * kFEZY);
-    T xn[7];
-    int cn[7];
-    if (lz + 1 < kFBZ) {
-#pragma unroll
-      for (int K = 0; K < 7; K++) {
-        if (!DEC) xn[K] = __ldg(xp + (int64_t)(2 * (lz + 1)) * xdz + off[K]);
-        else cn[K] = cp[K][(lz + 1) * kCell];
-      }
-    }
-    T p[7];
-    cell_predict(w0, w1, w2, w3, p);
-    T* fpl = fp ? fp + (int64_t)(2 * lz) * fdz : nullptr;
-    if (fpl) fpl[0] = w1[1];  // the coarse point itself
-#pragma unroll
-    for (int K = 0; K < 7; K++) {
-      if (!DEC) {
-        T xq;
-        const int sym = quantize_sel(xv[K], p[K], q, kRadius, xq);
-        cp[K][lz * kCell] = (uint16_t)sym;
-        if (fpl) fpl[foff[K]] = xq;
-        if (sym == 0) atomicAdd(&a.chunk_outliers[ti.chunk[K + 1]], 1u);
-        const unsigned bm = __ballot_sync(0xffffffffu, sym == kRadius);
-        uint32_t* h = hist + K * kHistWords;
-        if (lane == 0) atomicAdd(&h[kRadius >> 1], (uint32_t)__popc(bm));
-        if (sym != kRadius) atomicAdd(&h[sym >> 1], 1u << ((sym & 1) * 16));
-      } else {
-        const int sym = cv[K];
-        T val;
-        if (sym != 0) {
-          val = dequantize(sym, p[K], two_eb, kRadius);
-        } else if (!find_outlier(a.opos[K + 1], (const T*)a.oval[K + 1], a.nout[K + 1],
-                                 ti.pos[K + 1] + lz * kCell + tid, val)) {
-          val = T(0);
-          atomicOr(a.status, kStatCorrupt);
-        }
-        fpl[foff[K]] = val;
-      }
-    }
-    if (lz + 1 < kFBZ) {
-#pragma unroll
-      for (int K = 0; K < 7; K++) {
-        if (!DEC) xv[K] = xn[K];
-        else cv[K] = cn[K];
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 12; j++) {
-      w0[j] = w1[j];
-      w1[j] = w2[j];
-      w2[j] = w3[j];
-    }
-  }
-}
-
 template <typename T, bool DEC>
 __global__ void __launch_bounds__(kLevelThreads, 2) k_level_fast(const __grid_constant__ LevelArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -625,18 +525,7 @@ __global__ void __launch_bounds__(kLevelThreads, 2) k_level_fast(const __grid_co
 #pragma unroll
     for (int K = 1; K <= 7; K++)
       full = full && ti.l[K][0] == kFBZ && ti.l[K][1] == kFBY && ti.l[K][2] == kFBX;
-    // every cell interior (1 <= c <= M-3), and decoding: every fine point of
-    // the tile (2c .. 2c+1) inside the output box
-    bool in = full;
-    const int cb[3] = {kFBZ, kFBY, kFBX};
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-      in = in && ti.c0[d] >= 1 && ti.c0[d] + cb[d] - 1 <= M[d] - 3;
-      if (DEC) in = in && 2 * ti.c0[d] >= a.flo[d] && 2 * (ti.c0[d] + cb[d]) <= a.fhi[d];
-    }
-    if (in)
-      fast_tile_in<T, DEC>(a, tiles[b], ti, q, two_eb, hist, xdz, xdy, xdx, fe2, fdz);
-    else if (full)
+    if (full)
       fast_tile<T, DEC, true>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2, fdz);
     else
       fast_tile<T, DEC, false>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2, fdz);
