@@ -593,38 +593,67 @@ int stz_info(const void* comp, size_t comp_bytes, int comp_on_device, stz_info_t
   return rc;
 }
 
-// A second stream per caller stream (and device): a decode runs the level-1
-// reconstruction there, beside the chunk decoding of the finer levels, joined
-// back by events before the finer levels need it.
+// Parsed headers of recently decoded containers, by device, address and
+// size.  A plain decode of a container seen before starts its launches at
+// once from the cached header instead of waiting for a read-back; it copies
+// the header bytes back beside its final status word and, if they differ
+// from the cached ones (another container now sits at that address), decodes
+// again with the fresh header.  A stale header cannot lead a decode outside
+// its buffers: its sections lie within the same comp_bytes, and the output
+// and workspace sizes are checked against the plan it gives.
 namespace {
-struct SideStream {
+struct HdrCacheEntry {
   int dev;
-  cudaStream_t key, s;
-  cudaEvent_t fork, join;
+  const void* ptr;
+  size_t bytes, nraw;
+  unsigned long long last;
+  Hdr H;
+  uint8_t raw[kHeaderBytes + kMaxStreams * kDirEntryBytes];
 };
-std::mutex g_side_mu;
-SideStream g_side[64];
-int g_nside = 0;
+constexpr int kHdrCache = 16;
+std::mutex g_hc_mu;
+HdrCacheEntry g_hc[kHdrCache];
+int g_nhc = 0;
+unsigned long long g_hc_tick = 0;
+thread_local uint8_t* tl_hdr_pinned = nullptr;  // read-back buffer of this thread
 }  // namespace
 
-static const SideStream* side_of(cudaStream_t st) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-  std::lock_guard<std::mutex> lk(g_side_mu);
-  for (int i = 0; i < g_nside; i++)
-    if (g_side[i].dev == dev && g_side[i].key == st) return &g_side[i];
-  if (g_nside == 64) return nullptr;
-  SideStream e;
-  e.dev = dev;
-  e.key = st;
-  if (cudaStreamCreateWithFlags(&e.s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-  if (cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&e.join, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
+static bool hdr_cache_get(int dev, const void* ptr, size_t bytes, Hdr* H, uint8_t* raw,
+                          size_t* nraw) {
+  std::lock_guard<std::mutex> lk(g_hc_mu);
+  for (int i = 0; i < g_nhc; i++) {
+    HdrCacheEntry& e = g_hc[i];
+    if (e.dev == dev && e.ptr == ptr && e.bytes == bytes) {
+      e.last = ++g_hc_tick;
+      *H = e.H;
+      memcpy(raw, e.raw, e.nraw);
+      *nraw = e.nraw;
+      return true;
+    }
   }
-  g_side[g_nside] = e;
-  return &g_side[g_nside++];
+  return false;
+}
+
+static void hdr_cache_put(int dev, const void* ptr, size_t bytes, const Hdr& H, const uint8_t* raw,
+                          size_t nraw) {
+  std::lock_guard<std::mutex> lk(g_hc_mu);
+  int slot = -1;
+  for (int i = 0; i < g_nhc; i++)
+    if (g_hc[i].dev == dev && g_hc[i].ptr == ptr && g_hc[i].bytes == bytes) slot = i;
+  if (slot < 0 && g_nhc < kHdrCache) slot = g_nhc++;
+  if (slot < 0) {
+    slot = 0;
+    for (int i = 1; i < g_nhc; i++)
+      if (g_hc[i].last < g_hc[slot].last) slot = i;
+  }
+  HdrCacheEntry& e = g_hc[slot];
+  e.dev = dev;
+  e.ptr = ptr;
+  e.bytes = bytes;
+  e.H = H;
+  e.nraw = nraw;
+  memcpy(e.raw, raw, nraw);
+  e.last = ++g_hc_tick;
 }
 
 // Options of a decode beyond the plain calls: a header parsed beforehand (no
@@ -634,27 +663,58 @@ struct DecOpts {
   const Hdr* hdr;
   const void* l1;
   uint32_t* status_out;
+  bool no_cache;  // read the header back even when it is cached
 };
 
 static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* lo_in,
                        const int64_t* hi_in, int level, int whole, void* out_dev, size_t out_cap,
                        int64_t* out_dims, void* ws_dev, size_t ws_bytes, cudaStream_t st,
                        const DecOpts& o) {
+  const int level_in = level;
   if (!comp_dev || !out_dev || !ws_dev) return STZ_ERR_ARG;
   if (((uintptr_t)comp_dev % 8) || ((uintptr_t)ws_dev % 256)) return STZ_ERR_ARG;
   Hdr H;
   int rc = STZ_OK;
-  if (o.hdr)
+  // plain calls: the header from the cache (checked at the end), else read
+  const size_t nraw = comp_bytes < (size_t)STZ_HEADER_MAX_BYTES ? comp_bytes
+                                                                : (size_t)STZ_HEADER_MAX_BYTES;
+  uint8_t raw[STZ_HEADER_MAX_BYTES];
+  size_t nraw_cached = 0;
+  int dev = -1;
+  bool cached = false;
+  if (o.hdr) {
     H = *o.hdr;
-  else
-    rc = read_hdr(comp_dev, comp_bytes, 1, st, &H);
+  } else {
+    if (cudaGetDevice(&dev) != cudaSuccess) return STZ_ERR_CUDA;
+    cached = !o.no_cache && hdr_cache_get(dev, comp_dev, comp_bytes, &H, raw, &nraw_cached);
+    if (!cached) {
+      if (!comp_dev || comp_bytes < (size_t)kHeaderBytes) return STZ_ERR_CORRUPT;
+      if (cudaMemcpyAsync(raw, comp_dev, nraw, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return STZ_ERR_CUDA;
+      rc = parse_hdr(raw, nraw, comp_bytes, &H);
+      if (rc == STZ_OK) hdr_cache_put(dev, comp_dev, comp_bytes, H, raw, nraw);
+    }
+  }
   if (rc != STZ_OK) return rc;
+  // a return decided from a cached header before any launch: decide it again
+  // from the header read back
+#define STZ_EARLY(x)                                                                       \
+  do {                                                                                     \
+    if (cached) {                                                                          \
+      DecOpts o2 = o;                                                                      \
+      o2.no_cache = true;                                                                  \
+      return decode_core(comp_dev, comp_bytes, lo_in, hi_in, level_in, whole, out_dev,     \
+                         out_cap, out_dims, ws_dev, ws_bytes, st, o2);                     \
+    }                                                                                      \
+    return (x);                                                                            \
+  } while (0)
   const bool have_l1 = o.l1 != nullptr;
-  if (have_l1 && ((uintptr_t)o.l1 % (H.dtype == STZ_F32 ? 4 : 8))) return STZ_ERR_ARG;
+  if (have_l1 && ((uintptr_t)o.l1 % (H.dtype == STZ_F32 ? 4 : 8))) STZ_EARLY(STZ_ERR_ARG);
   if (level == 0) level = H.L;
-  if (level < 1 || level > H.L) return STZ_ERR_ARG;
+  if (level < 1 || level > H.L) STZ_EARLY(STZ_ERR_ARG);
   const size_t ps = H.dtype == STZ_F32 ? 4 : 8;
-  if ((uintptr_t)out_dev % ps) return STZ_ERR_ARG;
+  if ((uintptr_t)out_dev % ps) STZ_EARLY(STZ_ERR_ARG);
   Geo g;
   make_geo(H.n, H.ndim, H.dtype, H.L, H.b, &g);
   int64_t lo[3] = {0, 0, 0}, hi[3] = {g.n[0], g.n[1], g.n[2]};
@@ -672,7 +732,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
       hi[2] = hi_in[1];
     }
     for (int a = 0; a < 3; a++)
-      if (lo[a] < 0 || hi[a] > g.n[a] || lo[a] >= hi[a]) return STZ_ERR_ARG;
+      if (lo[a] < 0 || hi[a] > g.n[a] || lo[a] >= hi[a]) STZ_EARLY(STZ_ERR_ARG);
   }
   DecPlan P;
   plan_decode(g, level, lo, hi, &P, have_l1);
@@ -688,9 +748,9 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     }
   }
   const int64_t npts = od[0] * od[1] * od[2];
-  if (npts == 0) return STZ_OK;
-  if ((size_t)npts * ps > out_cap) return STZ_ERR_CAPACITY;
-  if (P.total > ws_bytes) return STZ_ERR_CAPACITY;
+  if (npts == 0) STZ_EARLY(STZ_OK);
+  if ((size_t)npts * ps > out_cap) STZ_EARLY(STZ_ERR_CAPACITY);
+  if (P.total > ws_bytes) STZ_EARLY(STZ_ERR_CAPACITY);
   uint8_t* ws = (uint8_t*)ws_dev;
   DevParams* dp = (DevParams*)(ws + P.dp);
   uint16_t* codes = (uint16_t*)(ws + P.codes);
@@ -715,19 +775,15 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     d.nsub = H.nsub;
   }
   const int ns_needed = 1 + 7 * (level - 1);
-  // chunk jobs: stream 0 (level 1) in tb0, the finer levels in tb, so that
-  // level 1 can be reconstructed while the finer levels' chunks decode
-  DecTables tb0 = tb;
-  int64_t nblocks = 0, nblocks0 = 0;
-  double dec_bytes = 0.0, dec_bytes0 = 0.0;
+  int64_t nblocks = 0;
+  double dec_bytes = 0.0;
   for (int s = have_l1 ? 1 : 0; s < ns_needed; s++) {
     if (g.s[s].nsym == 0) continue;
     tb.lut_sid[tb.nlut++] = s;
     const SlotMap& sm = P.sm[s];
     const int64_t c = sm.cnt[0] * sm.cnt[1] * sm.cnt[2];
     if (c == 0) continue;
-    DecTables& t = s == 0 ? tb0 : tb;
-    DecChunkJob& jb = t.jobs[t.njobs++];
+    DecChunkJob& jb = tb.jobs[tb.njobs++];
     jb.sid = s;
     for (int a = 0; a < 3; a++) {
       jb.lo[a] = sm.lo[a];
@@ -736,16 +792,13 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     jb.slot_base = sm.base;
     jb.nchunks_job = c;
     // the job's share of the stream's codes (written) and payload (read)
-    const double jbytes = H.d[s].nch > 0 ? (2.0 * (double)H.d[s].nsym + 4.0 * (double)H.d[s].pw) *
-                                               (double)c / (double)H.d[s].nch
-                                         : 0.0;
-    int64_t& nb = s == 0 ? nblocks0 : nblocks;
-    (s == 0 ? dec_bytes0 : dec_bytes) += jbytes;
-    jb.block0 = nb;
-    nb += cdiv(c * H.nsub, kDecThreads);
+    if (H.d[s].nch > 0)
+      dec_bytes += (2.0 * (double)H.d[s].nsym + 4.0 * (double)H.d[s].pw) * (double)c /
+                   (double)H.d[s].nch;
+    jb.block0 = nblocks;
+    nblocks += cdiv(c * H.nsub, kDecThreads);
   }
   tb.nblocks = nblocks;
-  tb0.nblocks = nblocks0;
 #define STZ_TRY(x)               \
   do {                           \
     rc = (x);                    \
@@ -753,15 +806,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
   } while (0)
   STZ_TRY(cuda_ok(cudaMemsetAsync(dp, 0, sizeof(DevParams), st)));
   STZ_TRY(launch_lut(tb, lut, status, st));
-  STZ_TRY(launch_decode_chunks(g, tb0, lut, codes, status, dec_bytes0, st));
-  // level 1 on the side stream when finer levels follow (joined below)
-  const SideStream* side = (!have_l1 && level > 1) ? side_of(st) : nullptr;
-  cudaStream_t st1 = st;
-  if (side) {
-    STZ_TRY(cuda_ok(cudaEventRecord(side->fork, st)));
-    STZ_TRY(cuda_ok(cudaStreamWaitEvent(side->s, side->fork, 0)));
-    st1 = side->s;
-  }
+  STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
   const uint8_t* sec0 = comp + H.d[0].sect_off;
   SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps, H.nsub);
   uint8_t* g1buf = have_l1 ? (uint8_t*)o.l1 : ws + P.grid[1];
@@ -789,12 +834,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
       whole = whole && a.rlo[d] == 0 && a.rhi[d] == m1[d];
     }
     a.region = whole ? 0 : 1;
-    STZ_TRY(launch_base(a, true, st1));
-  }
-  STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
-  if (side) {
-    STZ_TRY(cuda_ok(cudaEventRecord(side->join, side->s)));
-    STZ_TRY(cuda_ok(cudaStreamWaitEvent(st, side->join, 0)));
+    STZ_TRY(launch_base(a, true, st));
   }
   if (level == 1) {
     int64_t m1[3];
@@ -847,10 +887,31 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     return STZ_OK;
   }
   uint32_t hstat = 0;
+  if (cached) {  // read the header bytes back beside the status (pinned: no wait)
+    if (!tl_hdr_pinned &&
+        cudaMallocHost((void**)&tl_hdr_pinned, STZ_HEADER_MAX_BYTES) != cudaSuccess) {
+      tl_hdr_pinned = nullptr;
+      return STZ_ERR_NOMEM;
+    }
+    STZ_TRY(cuda_ok(cudaMemcpyAsync(tl_hdr_pinned, comp_dev, nraw, cudaMemcpyDeviceToHost, st)));
+  }
   STZ_TRY(cuda_ok(cudaMemcpyAsync(&hstat, status, 4, cudaMemcpyDeviceToHost, st)));
   STZ_TRY(cuda_ok(cudaStreamSynchronize(st)));
 #undef STZ_TRY
+  if (cached && (nraw != nraw_cached || memcmp(tl_hdr_pinned, raw, nraw) != 0)) {
+    // another container at this address: decode again from its own header
+    Hdr F;
+    memcpy(raw, tl_hdr_pinned, nraw);
+    rc = parse_hdr(raw, nraw, comp_bytes, &F);
+    if (rc != STZ_OK) return rc;
+    hdr_cache_put(dev, comp_dev, comp_bytes, F, raw, nraw);
+    DecOpts o2 = o;
+    o2.hdr = &F;
+    return decode_core(comp_dev, comp_bytes, lo_in, hi_in, level, whole, out_dev, out_cap,
+                       out_dims, ws_dev, ws_bytes, st, o2);
+  }
   return (hstat & kStatCorrupt) ? STZ_ERR_CORRUPT : STZ_OK;
+#undef STZ_EARLY
 }
 
 static int decode_impl(const void* comp_dev, size_t comp_bytes, const int64_t* lo_in,

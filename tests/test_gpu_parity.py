@@ -230,3 +230,29 @@ def test_region_dependencies_256_grf(stzg, ora):
                 continue
             r = stzg.decompress_region(comp, lo, hi, level).cpu().numpy()
             assert np.array_equal(_bits(r), _bits(want)), (lo, hi, level)
+
+
+def test_header_cache_follows_new_container(stzg, ora):
+    """Decodes of a device buffer reuse its parsed header; when another
+    container is written to the same address (same size passed), the decode
+    still returns the new container's values, also when its shape differs."""
+    xa = synth.sinusoids((40, 36, 52), 31)
+    xb = synth.sinusoids((40, 36, 52), 32) * 3.0
+    xc = synth.sinusoids((24, 60, 33), 33)
+    ca, cb, cc = (ora.compress(x, 1e-3) for x in (xa, xb, xc))
+    cap = max(ca.size, cb.size, cc.size)
+    buf = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    out = torch.empty(max(xa.size, xc.size), dtype=torch.float32, device="cuda")
+    ws = stzg.alloc_workspace((40, 60, 52), torch.float32)
+    for _ in range(2):
+        for c, x in ((ca, xa), (cb, xb), (cc, xc), (ca, xa)):
+            buf.zero_()
+            buf[: c.size].copy_(torch.from_numpy(c))
+            meta = {"shape": x.shape, "dtype": torch.float32, "ndim": 3, "levels": 3}
+            y = stzg.decompress_full(buf, out=out[: x.size], workspace=ws,
+                                     meta=meta).cpu().numpy()
+            assert np.array_equal(_bits(y), _bits(ora.decompress(c)))
+            r = stzg.decompress_region(buf, (2, 3, 4), (20, 30, 31), 2, out=out, workspace=ws,
+                                       meta=meta).cpu().numpy()
+            assert np.array_equal(_bits(r), _bits(ora.decompress_region(c, (2, 3, 4),
+                                                                        (20, 30, 31), 2)))
