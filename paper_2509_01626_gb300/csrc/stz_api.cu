@@ -478,8 +478,8 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
                        (unsigned long long*)(ws + w.scan_sums), word_off, out_off, st));
   STZ_TRY(launch_layout(g, dp, eb_mode, word_off, out_off, books, lay, out, out_cap, st));
   STZ_TRY(launch_sections(g, lay, books, word_off, dp, out, st));
-  STZ_TRY(launch_pack(g, codes, enc, word_off, lay->s, out, dp, st));
-  STZ_TRY(launch_outliers(g, codes, field_dev, chunk_out, out_off, lay, dp, out, st));
+  STZ_TRY(launch_pack(g, codes, enc, word_off, lay->s, out, dp, field_dev, chunk_out, out_off,
+                      st));
 #undef STZ_TRY
   d->total = &lay->total;
   d->payload_words = word_off + g.total_chunks;

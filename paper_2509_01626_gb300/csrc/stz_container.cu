@@ -156,67 +156,4 @@ int launch_sections(const Geo& g, const LayoutDev* lay, const BookDev* books,
   return cuda_ok(cudaGetLastError());
 }
 
-// Outlier lists: one warp per chunk holding outliers (symbol 0) lists them in
-// stream order (ballot compaction) with the raw value of the field there.
-template <typename T>
-__global__ void __launch_bounds__(256) k_outliers(const __grid_constant__ Geo g,
-                                                  const uint16_t* __restrict__ codes,
-                                                  const T* __restrict__ field,
-                                                  const uint32_t* __restrict__ chunk_outliers,
-                                                  const unsigned long long* __restrict__ out_off,
-                                                  const LayoutDev* __restrict__ lay,
-                                                  const DevParams* __restrict__ dp,
-                                                  uint8_t* __restrict__ out) {
-  if (dp->status & kStatCapacity) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < g.total_chunks;
-       j += nw) {
-    if (chunk_outliers[j] == 0) continue;
-    int sid = 0;
-    for (int s = 1; s < g.nstreams; s++)
-      if (g.s[s].nchunks > 0 && g.s[s].chunk0 <= j) sid = s;
-    const StreamGeo& sg = g.s[sid];
-    const SectDev& d = lay->s[sid];
-    uint32_t* opos = (uint32_t*)(out + d.sect_off + d.off_opos);
-    T* oval = (T*)(out + d.sect_off + d.off_oval);
-    int64_t B[3], l[3], start;
-    chunk_brick(sg, g.b, j - sg.chunk0, B, l, &start);
-    const int64_t cnt = l[0] * l[1] * l[2];
-    const int64_t s = level_stride(g.L, sg.level);
-    unsigned long long k = out_off[j] - d.out0;
-    const uint16_t* c = codes + j * g.bvol;
-    for (int64_t i0 = 0; i0 < cnt; i0 += 32) {
-      const int64_t i = i0 + lane;
-      const bool hit = i < cnt && c[i] == 0;
-      const unsigned bm = __ballot_sync(0xffffffffu, hit);
-      if (hit) {
-        const int64_t lz = i / (l[1] * l[2]), ly = (i / l[2]) % l[1], lx = i % l[2];
-        int64_t p[3] = {B[0] * g.b[0] + lz, B[1] * g.b[1] + ly, B[2] * g.b[2] + lx};
-        if (sg.level > 1)
-          for (int a = 0; a < 3; a++) p[a] = 2 * p[a] + sg.o[a];
-        const int64_t f = ((p[0] * s) * g.n[1] + p[1] * s) * g.n[2] + p[2] * s;
-        const unsigned long long kk = k + __popc(bm & ((1u << lane) - 1u));
-        opos[kk] = (uint32_t)(start + i);
-        oval[kk] = field[f];
-      }
-      k += __popc(bm);
-    }
-  }
-}
-
-int launch_outliers(const Geo& g, const uint16_t* codes, const void* field,
-                    const uint32_t* chunk_outliers, const unsigned long long* out_off,
-                    const LayoutDev* lay, const DevParams* dp, uint8_t* out, cudaStream_t s) {
-  int64_t blocks = imax(1, imin(cdiv(g.total_chunks * 32, 256), 2048));
-  ProfScope ps_("k_outliers", s);
-  if (g.dtype == STZ_F32)
-    k_outliers<float><<<(unsigned)blocks, 256, 0, s>>>(g, codes, (const float*)field,
-                                                       chunk_outliers, out_off, lay, dp, out);
-  else
-    k_outliers<double><<<(unsigned)blocks, 256, 0, s>>>(g, codes, (const double*)field,
-                                                        chunk_outliers, out_off, lay, dp, out);
-  return cuda_ok(cudaGetLastError());
-}
-
 }  // namespace stz

@@ -552,13 +552,17 @@ int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long 
 // Every lane but the chunk's last holds 64 symbols, so at least 64 bits: only
 // neighbouring lanes ever share a word.  The lanes holding a sub-chunk start
 // sum the lengths before it for the sub-chunk's bit offset.
+template <typename T>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
                                               const uint16_t* __restrict__ codes,
                                               const uint16_t* __restrict__ enc,
                                               const unsigned long long* __restrict__ word_off,
                                               const SectDev* __restrict__ sect,
                                               uint8_t* __restrict__ out,
-                                              const DevParams* __restrict__ dp) {
+                                              const DevParams* __restrict__ dp,
+                                              const T* __restrict__ field,
+                                              const uint32_t* __restrict__ chunk_outliers,
+                                              const unsigned long long* __restrict__ out_off) {
   if (dp->status & kStatCapacity) return;
   const int lane = threadIdx.x & 31;
   const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -626,16 +630,52 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
   uint32_t from_next = __shfl_down_sync(0xffffffffu, first_part, 1);
   if (lane == 31) from_next = 0;
   if (has_last) dst[widx] = last | from_next;
+  // the chunk's outliers (symbol 0): stream position and raw value, in stream
+  // order from the chunk's offset in the stream's outlier list
+  if (chunk_outliers[j] == 0) return;
+  uint32_t nz = 0;
+  for (int i = s0; i < s1; i++) nz += __ldg(c + i) == 0;
+  uint32_t zincl = nz;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, zincl, o);
+    if (lane >= o) zincl += y;
+  }
+  if (nz == 0) return;
+  const StreamGeo& sg = g.s[sid];
+  int64_t B[3], l[3], start;
+  chunk_brick(sg, g.b, j - sg.chunk0, B, l, &start);
+  const int64_t st = level_stride(g.L, sg.level);
+  uint32_t* opos = (uint32_t*)(out + sd.sect_off + sd.off_opos);
+  T* oval = (T*)(out + sd.sect_off + sd.off_oval);
+  unsigned long long k = out_off[j] - sd.out0 + (zincl - nz);
+  for (int i = s0; i < s1; i++) {
+    if (__ldg(c + i) != 0) continue;
+    const int64_t lz = i / (l[1] * l[2]), ly = (i / l[2]) % l[1], lx = i % l[2];
+    int64_t pt[3] = {B[0] * g.b[0] + lz, B[1] * g.b[1] + ly, B[2] * g.b[2] + lx};
+    if (sg.level > 1)
+      for (int a = 0; a < 3; a++) pt[a] = 2 * pt[a] + sg.o[a];
+    opos[k] = (uint32_t)(start + i);
+    oval[k] = field[((pt[0] * st) * g.n[1] + pt[1] * st) * g.n[2] + pt[2] * st];
+    k++;
+  }
 }
 
 int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
                 const unsigned long long* word_off, const SectDev* sect, uint8_t* out,
-                const DevParams* dp, cudaStream_t s) {
+                const DevParams* dp, const void* field, const uint32_t* chunk_outliers,
+                const unsigned long long* out_off, cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
   if (g.bvol > 32 * kLaneSyms) return STZ_ERR_ARG;
+  const unsigned grid = (unsigned)cdiv(g.total_chunks, 8);
   // reads the codes; the payload it writes is added once its size is known
   ProfScope ps_("k_pack", s, 2.0 * (double)total_symbols(g));
-  k_pack<<<(unsigned)cdiv(g.total_chunks, 8), 256, 0, s>>>(g, codes, enc, word_off, sect, out, dp);
+  if (g.dtype == STZ_F32)
+    k_pack<float><<<grid, 256, 0, s>>>(g, codes, enc, word_off, sect, out, dp,
+                                       (const float*)field, chunk_outliers, out_off);
+  else
+    k_pack<double><<<grid, 256, 0, s>>>(g, codes, enc, word_off, sect, out, dp,
+                                        (const double*)field, chunk_outliers, out_off);
   return cuda_ok(cudaGetLastError());
 }
 

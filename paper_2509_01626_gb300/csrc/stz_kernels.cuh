@@ -77,11 +77,12 @@ int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc,
 // sums: 2 * ceil(n / 4096) scratch entries
 int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* sums,
                  unsigned long long* oa, unsigned long long* ob, cudaStream_t s);
-// pack every chunk's codes into the container payload
+// pack every chunk's codes into the container payload and list its outliers
 struct SectDev;  // stz_container.cu
 int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
                 const unsigned long long* word_off, const SectDev* sect, uint8_t* out,
-                const DevParams* dp, cudaStream_t s);
+                const DevParams* dp, const void* field, const uint32_t* chunk_outliers,
+                const unsigned long long* out_off, cudaStream_t s);
 
 // decode tables: lut[s][i] = sym | len << 11 for the top-12-bit window i
 // (len 0: no code starts with i)
@@ -129,9 +130,6 @@ int launch_layout(const Geo& g, const DevParams* dp, int eb_mode,
 int launch_sections(const Geo& g, const LayoutDev* lay, const BookDev* books,
                     const unsigned long long* word_off, const DevParams* dp, uint8_t* out,
                     cudaStream_t s);
-int launch_outliers(const Geo& g, const uint16_t* codes, const void* field,
-                    const uint32_t* chunk_outliers, const unsigned long long* out_off,
-                    const LayoutDev* lay, const DevParams* dp, uint8_t* out, cudaStream_t s);
 
 // ---- stz_api.cu: one compression as a queue of launches ----
 struct CompressJob {
