@@ -122,15 +122,18 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
     }
     return;
   }
-  // two-queue merge (sequential, one thread).  The next leaf weights are kept
-  // in registers two ahead so the loop carries no shared-memory latency.
+  // two-queue merge (sequential, one thread).  The heads of both queues are
+  // kept in registers three deep (the next weights are loaded two picks
+  // before they can be needed), so the loop carries no shared-memory latency.
   if (tid == 0) {
     // weights fit in 32 bits: a stream has fewer than 2^31 symbols
     int i = 0, j = 0;
     uint32_t lw = (uint32_t)(key[0] >> 11);
     uint32_t lw1 = nl > 1 ? (uint32_t)(key[1] >> 11) : 0u;
     uint32_t lw2 = nl > 2 ? (uint32_t)(key[2] >> 11) : 0u;
-    uint32_t jw = 0, jw1 = 0;  // internal queue head and the node after it
+    // internal nodes j, j+1, j+2 (those created so far; the rest are set
+    // when created)
+    uint32_t jw = 0, jw1 = 0, jw2 = 0;
     for (int k = 0; k < nl - 1; k++) {
       uint32_t wsum = 0;
 #pragma unroll
@@ -149,7 +152,8 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
           par_int[j] = (uint16_t)k;
           j++;
           jw = jw1;
-          jw1 = j + 1 < k ? iw[j + 1] : 0u;
+          jw1 = jw2;
+          jw2 = j + 2 < k ? iw[j + 2] : 0u;
         }
       }
       iw[k] = wsum;
@@ -157,6 +161,8 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
         jw = wsum;  // the queue was empty: its head is the new node
       } else if (j + 1 == k) {
         jw1 = wsum;
+      } else if (j + 2 == k) {
+        jw2 = wsum;
       }
     }
   }
@@ -693,7 +699,6 @@ __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables t
   const int tid = threadIdx.x;
   if (tid < 32) cnt[tid] = 0;
   if (tid == 0) bad = 0;
-  for (int i = tid; i < kLutSize; i += blockDim.x) t[i] = 0;
   __syncthreads();
   const uint16_t* syms = (const uint16_t*)(d.sect + d.off_syms);
   const uint8_t* lens = d.sect + d.off_lens;
@@ -724,16 +729,23 @@ __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables t
     if (kraft > kLutSize) bad = 1;
   }
   __syncthreads();
-  if (bad) {
+  if (bad) {  // an empty table: every lookup then flags the chunk as corrupt
+    for (int i = tid; i < kLutSize; i += blockDim.x) t[i] = 0;
     if (tid == 0) atomicOr(status, kStatCorrupt);
     return;
   }
-  for (int64_t k = tid; k < (int64_t)d.nlive; k += blockDim.x) {
-    const int L = lens[k], sym = syms[k];
-    const uint32_t code = fcode[L] + (uint32_t)(k - fidx[L]);
-    const uint32_t lo = code << (kMaxCodeLen - L), hi = (code + 1) << (kMaxCodeLen - L);
-    const uint16_t v = (uint16_t)(sym | (L << 11));
-    for (uint32_t i = lo; i < hi; i++) t[i] = v;
+  // each window i of the table: the one length L whose L-bit prefix of i
+  // falls in that length's range of canonical codes (0: no code starts so)
+  for (int i = tid; i < kLutSize; i += blockDim.x) {
+    uint16_t v = 0;
+    for (int L = 1; L <= kMaxCodeLen; L++) {
+      const uint32_t r = ((uint32_t)i >> (kMaxCodeLen - L)) - fcode[L];
+      if (r < (uint32_t)cnt[L]) {
+        v = (uint16_t)(syms[fidx[L] + (int)r] | (L << 11));
+        break;
+      }
+    }
+    t[i] = v;
   }
 }
 
