@@ -146,11 +146,17 @@ struct CompressDev {
   const unsigned long long* total;          // container bytes
   const unsigned long long* payload_words;  // payload words of all chunks
   const uint32_t* status;                   // kStat* bits
+  const unsigned long long* result;         // the three above, gathered (k_result)
 };
 int compress_check(const void* field_dev, const int64_t* dims, int ndim, int dtype, int eb_mode,
                    double eb, void* out_dev, size_t out_cap, void* ws_dev, size_t ws_bytes,
                    CompressJob* j);
 int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, CompressDev* d);
+// stz_compress's launch sequence as a graph captured once per argument tuple
+// and replayed
+int compress_graph_launch(const CompressJob& j, const void* field, const int64_t dims[3], int ndim,
+                          int dtype, int eb_mode, double eb, void* out, size_t out_cap, void* ws,
+                          size_t ws_bytes, cudaStream_t st, CompressDev* d);
 
 // SMs that one launch sizes a persistent grid for: all of them, unless the
 // calling thread set a share (the batched form runs several fields' kernels

@@ -85,6 +85,8 @@ void prof_begin(const char* name, cudaStream_t s, int* slot, double bytes) {
 
 void prof_count_launches(unsigned long long n) { g_launches.fetch_add(n); }
 
+bool prof_enabled() { return g_enabled.load() != 0; }
+
 void prof_end(int slot, cudaStream_t s) {
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_mu);

@@ -12,6 +12,8 @@ namespace stz {
 // every output it must write, once), 0 where no figure is kept.
 void prof_begin(const char* name, cudaStream_t s, int* slot, double bytes);
 void prof_end(int slot, cudaStream_t s);
+// Whether per-launch event timing is on.
+bool prof_enabled();
 // Adds n kernel launches to the counter (one replay of a captured graph).
 void prof_count_launches(unsigned long long n);
 // Adds algorithmic bytes to the latest timed launch of `name` (for a launch
