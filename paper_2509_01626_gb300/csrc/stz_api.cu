@@ -48,6 +48,62 @@ void make_geo(const int64_t n[3], int ndim, int dtype, int L, const int b[3], Ge
   g->total_chunks = chunk0;
 }
 
+// ------------------------------------------------------------- read-backs
+// The few bytes a call returns to the host (status word, container size,
+// header) are written by a one-block kernel into mapped pinned host memory:
+// no copy engine is involved, so these reads never queue behind large
+// host<->device copies the caller has in flight on other streams.
+__global__ void k_readback(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// Zero fill of device words by a kernel (not cudaMemsetAsync, which may be
+// carried out by a copy engine and then wait behind the caller's copies).
+__global__ void k_zero(uint32_t* __restrict__ p, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0u;
+}
+
+static int zero_words(void* p, int64_t nwords, cudaStream_t st) {
+  if (nwords <= 0) return STZ_OK;
+  const int64_t blocks = imin(cdiv(nwords, 256), 1024);
+  ProfScope ps_("k_zero", st);
+  k_zero<<<(unsigned)blocks, 256, 0, st>>>((uint32_t*)p, nwords);
+  return cuda_ok(cudaGetLastError());
+}
+
+namespace {
+constexpr int kReadbackBytes = 4096;
+thread_local uint8_t* tl_rb_host = nullptr;  // mapped, pinned, portable
+thread_local uint8_t* tl_rb_dev = nullptr;   // its device address
+}  // namespace
+
+// Queues a copy of n (<= 4096 - off) device bytes to offset off of this
+// thread's read-back buffer; *host receives where they will be on the host.
+static int readback(const void* src, int n, int off, cudaStream_t st, const uint8_t** host) {
+  if (!tl_rb_host) {
+    if (cudaHostAlloc((void**)&tl_rb_host, kReadbackBytes,
+                      cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+      tl_rb_host = nullptr;
+      return STZ_ERR_NOMEM;
+    }
+    if (cudaHostGetDevicePointer((void**)&tl_rb_dev, tl_rb_host, 0) != cudaSuccess) {
+      cudaFreeHost(tl_rb_host);
+      tl_rb_host = nullptr;
+      return STZ_ERR_CUDA;
+    }
+  }
+  if (n <= 0 || off < 0 || off + n > kReadbackBytes) return STZ_ERR_ARG;
+  {
+    ProfScope ps_("k_readback", st);
+    k_readback<<<1, 256, 0, st>>>((const uint8_t*)src, tl_rb_dev + off, n);
+  }
+  if (cudaGetLastError() != cudaSuccess) return STZ_ERR_CUDA;
+  *host = tl_rb_host + off;
+  return STZ_OK;
+}
+
 static size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 static int64_t vol(const int64_t e[3]) { return e[0] * e[1] * e[2]; }
 
@@ -253,8 +309,11 @@ static int read_hdr(const void* comp, size_t comp_bytes, int on_device, cudaStre
   const size_t n = comp_bytes < want ? comp_bytes : want;
   uint8_t buf[kHeaderBytes + kMaxStreams * kDirEntryBytes];
   if (on_device) {
-    if (cudaMemcpyAsync(buf, comp, n, cudaMemcpyDeviceToHost, st) != cudaSuccess) return STZ_ERR_CUDA;
+    const uint8_t* h = nullptr;
+    const int rc = readback(comp, (int)n, 0, st, &h);
+    if (rc != STZ_OK) return rc;
     if (cudaStreamSynchronize(st) != cudaSuccess) return STZ_ERR_CUDA;
+    memcpy(buf, h, n);
   } else {
     memcpy(buf, comp, n);
   }
@@ -431,8 +490,8 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
     rc = (x);               \
     if (rc != STZ_OK) return rc; \
   } while (0)
-  STZ_TRY(cuda_ok(cudaMemsetAsync(hist, 0, 4 * (size_t)g.nstreams * kAlphabet, st)));
-  STZ_TRY(cuda_ok(cudaMemsetAsync(chunk_out, 0, 4 * (size_t)g.total_chunks, st)));
+  STZ_TRY(zero_words(hist, (int64_t)g.nstreams * kAlphabet, st));
+  STZ_TRY(zero_words(chunk_out, g.total_chunks, st));
   STZ_TRY(launch_params_init(dp, st));
   if (eb_mode == STZ_EB_REL) STZ_TRY(launch_range(field_dev, dtype, vol(n), dp, st));
   STZ_TRY(launch_params(dp, dtype, eb_mode, eb, g.L, kRadius, st));
@@ -535,7 +594,6 @@ CompGraph g_cg[kCompGraphs];
 int g_ncg = 0;
 unsigned long long g_cg_tick = 0;
 cudaStream_t g_cap_stream[64];
-thread_local unsigned long long* tl_result_pinned = nullptr;  // read-back of k_result
 
 unsigned long long graph_kernels(cudaGraph_t g) {
   size_t n = 0;
@@ -700,18 +758,15 @@ int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype
                                ws_dev, ws_bytes, st, &d);
   }
   if (rc != STZ_OK) return rc;
-  if (!tl_result_pinned &&
-      cudaMallocHost((void**)&tl_result_pinned, 4 * sizeof(unsigned long long)) != cudaSuccess) {
-    tl_result_pinned = nullptr;
-    return STZ_ERR_NOMEM;
-  }
-  if ((rc = cuda_ok(cudaMemcpyAsync(tl_result_pinned, d.result, 3 * sizeof(unsigned long long),
-                                    cudaMemcpyDeviceToHost, st))) != STZ_OK)
+  const uint8_t* hres = nullptr;
+  if ((rc = readback(d.result, 3 * (int)sizeof(unsigned long long), 0, st, &hres)) != STZ_OK)
     return rc;
   if ((rc = cuda_ok(cudaStreamSynchronize(st))) != STZ_OK) return rc;
-  *out_bytes = (size_t)tl_result_pinned[0];
-  prof_add_bytes("k_pack", 4.0 * (double)tl_result_pinned[1]);
-  if (tl_result_pinned[2] & kStatCapacity) return STZ_ERR_CAPACITY;
+  unsigned long long r[3];
+  memcpy(r, hres, sizeof(r));
+  *out_bytes = (size_t)r[0];
+  prof_add_bytes("k_pack", 4.0 * (double)r[1]);
+  if (r[2] & kStatCapacity) return STZ_ERR_CAPACITY;
   return STZ_OK;
 }
 
@@ -760,7 +815,6 @@ std::mutex g_hc_mu;
 HdrCacheEntry g_hc[kHdrCache];
 int g_nhc = 0;
 unsigned long long g_hc_tick = 0;
-thread_local uint8_t* tl_hdr_pinned = nullptr;  // read-back buffer of this thread
 }  // namespace
 
 static bool hdr_cache_get(int dev, const void* ptr, size_t bytes, Hdr* H, uint8_t* raw,
@@ -834,9 +888,10 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     cached = !o.no_cache && hdr_cache_get(dev, comp_dev, comp_bytes, &H, raw, &nraw_cached);
     if (!cached) {
       if (!comp_dev || comp_bytes < (size_t)kHeaderBytes) return STZ_ERR_CORRUPT;
-      if (cudaMemcpyAsync(raw, comp_dev, nraw, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess)
-        return STZ_ERR_CUDA;
+      const uint8_t* h = nullptr;
+      if ((rc = readback(comp_dev, (int)nraw, 0, st, &h)) != STZ_OK) return rc;
+      if (cudaStreamSynchronize(st) != cudaSuccess) return STZ_ERR_CUDA;
+      memcpy(raw, h, nraw);
       rc = parse_hdr(raw, nraw, comp_bytes, &H);
       if (rc == STZ_OK) hdr_cache_put(dev, comp_dev, comp_bytes, H, raw, nraw);
     }
@@ -949,7 +1004,8 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     rc = (x);                    \
     if (rc != STZ_OK) return rc; \
   } while (0)
-  STZ_TRY(cuda_ok(cudaMemsetAsync(dp, 0, sizeof(DevParams), st)));
+  static_assert(sizeof(DevParams) % 4 == 0, "DevParams is cleared in words");
+  STZ_TRY(zero_words(dp, (int64_t)(sizeof(DevParams) / 4), st));
   STZ_TRY(launch_lut(tb, lut, status, st));
   STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
   const uint8_t* sec0 = comp + H.d[0].sect_off;
@@ -1028,25 +1084,24 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     STZ_TRY(launch_level(a, true, st));
   }
   if (o.status_out) {
-    STZ_TRY(cuda_ok(cudaMemcpyAsync(o.status_out, status, 4, cudaMemcpyDeviceToDevice, st)));
+    ProfScope ps_("k_readback", st);
+    k_readback<<<1, 32, 0, st>>>((const uint8_t*)status, (uint8_t*)o.status_out, 4);
+    STZ_TRY(cuda_ok(cudaGetLastError()));
     return STZ_OK;
   }
-  uint32_t hstat = 0;
-  if (cached) {  // read the header bytes back beside the status (pinned: no wait)
-    if (!tl_hdr_pinned &&
-        cudaMallocHost((void**)&tl_hdr_pinned, STZ_HEADER_MAX_BYTES) != cudaSuccess) {
-      tl_hdr_pinned = nullptr;
-      return STZ_ERR_NOMEM;
-    }
-    STZ_TRY(cuda_ok(cudaMemcpyAsync(tl_hdr_pinned, comp_dev, nraw, cudaMemcpyDeviceToHost, st)));
-  }
-  STZ_TRY(cuda_ok(cudaMemcpyAsync(&hstat, status, 4, cudaMemcpyDeviceToHost, st)));
+  // the status word, and for a cached header the header bytes beside it
+  const uint8_t* hst = nullptr;
+  const uint8_t* hhdr = nullptr;
+  STZ_TRY(readback(status, 4, 0, st, &hst));
+  if (cached) STZ_TRY(readback(comp_dev, (int)nraw, 64, st, &hhdr));
   STZ_TRY(cuda_ok(cudaStreamSynchronize(st)));
 #undef STZ_TRY
-  if (cached && (nraw != nraw_cached || memcmp(tl_hdr_pinned, raw, nraw) != 0)) {
+  uint32_t hstat = 0;
+  memcpy(&hstat, hst, 4);
+  if (cached && (nraw != nraw_cached || memcmp(hhdr, raw, nraw) != 0)) {
     // another container at this address: decode again from its own header
     Hdr F;
-    memcpy(raw, tl_hdr_pinned, nraw);
+    memcpy(raw, hhdr, nraw);
     rc = parse_hdr(raw, nraw, comp_bytes, &F);
     if (rc != STZ_OK) return rc;
     hdr_cache_put(dev, comp_dev, comp_bytes, F, raw, nraw);
