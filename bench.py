@@ -289,9 +289,10 @@ def run_ours(args, rank, world, local_rank):
     lat = np.array(lat)
 
     # end to end through the same calls, host buffers, copies timed.  The
-    # copies run on a copy stream beside the compute: step i's outputs go to
-    # the host while its later decodes run, and step i+1's field is uploaded
-    # while step i decodes (the device buffers alternate between two sets).
+    # copies run on two copy streams (one per direction) beside the compute:
+    # step i's outputs go to the host while its later decodes run, and step
+    # i+2's field is uploaded while step i decodes (three field buffers, two
+    # sets of outputs).
     # Every copy of every timed step lies inside the timed region.
     e2e = None
     if not args.no_e2e:
@@ -301,69 +302,80 @@ def run_ours(args, rank, world, local_rank):
         h_p = {k: torch.empty(p_out[k].numel(), dtype=torch.float32).pin_memory() for k in (1, 2)}
         h_box = torch.empty(box_out.numel(), dtype=torch.float32).pin_memory()
         h_slab = torch.empty(slab_out.numel(), dtype=torch.float32).pin_memory()
-        d_field = [torch.empty_like(field) for _ in range(2)]
+        nf = 3  # field buffers: step i+2's field is uploaded while step i decodes
+        d_field = [torch.empty_like(field) for _ in range(nf)]
         d_comp = torch.empty(comp_bytes, dtype=torch.uint8, device=dev)
         fulls = [full, torch.empty_like(full)]
         pouts = [p_out, {k: torch.empty_like(v) for k, v in p_out.items()}]
         boxes = [box_out, torch.empty_like(box_out)]
         slabs = [slab_out, torch.empty_like(slab_out)]
-        copy = torch.cuda.Stream(device=dev)
-        up_ev = [torch.cuda.Event() for _ in range(2)]
-        out_free = [torch.cuda.Event() for _ in range(2)]  # set set b's host copies done
+        # one stream per copy direction, and the compute on a stream of its
+        # own: uploads, downloads and compute all overlap
+        up = torch.cuda.Stream(device=dev)
+        down = torch.cuda.Stream(device=dev)
+        cstream = torch.cuda.Stream(device=dev)
+        up_ev = [torch.cuda.Event() for _ in range(nf)]
+        out_free = [torch.cuda.Event() for _ in range(2)]  # set b's host copies done
         for e in out_free:
-            e.record(stream)
+            e.record(cstream)
 
-        def upload(b):
-            with torch.cuda.stream(copy):
-                d_field[b].copy_(h_field, non_blocking=True)
-                up_ev[b].record(copy)
+        def upload(f):
+            with torch.cuda.stream(up):
+                d_field[f % nf].copy_(h_field, non_blocking=True)
+                up_ev[f % nf].record(up)
 
         def to_host(dst, src):
             ev = torch.cuda.Event()
-            ev.record(stream)
-            copy.wait_event(ev)
-            with torch.cuda.stream(copy):
+            ev.record(cstream)
+            down.wait_event(ev)
+            with torch.cuda.stream(down):
                 dst.copy_(src, non_blocking=True)
 
-        def e2e_step(i, last):
+        def e2e_step(i, n):
             b = i & 1
-            stream.wait_event(up_ev[b])
-            c = stz.compress(d_field[b], args.eb, "rel", out=out, workspace=ws)
-            if not last:
-                upload(b ^ 1)
-            h_comp.copy_(c, non_blocking=True)
-            d_comp.copy_(h_comp, non_blocking=True)
-            stream.wait_event(out_free[b])
-            y = stz.decompress_full(d_comp, out=fulls[b], workspace=ws, meta=meta)
+            cstream.wait_event(up_ev[i % nf])
+            c = stz.compress(d_field[i % nf], args.eb, "rel", out=out, workspace=ws,
+                             stream=cstream)
+            with torch.cuda.stream(cstream):
+                h_comp.copy_(c, non_blocking=True)
+                d_comp.copy_(h_comp, non_blocking=True)
+            cstream.wait_event(out_free[b])
+            y = stz.decompress_full(d_comp, out=fulls[b], workspace=ws, meta=meta, stream=cstream)
+            # the field two steps ahead: issued once this step's small upload
+            # has gone (copies of one direction queue on one engine)
+            if i + 2 < n:
+                upload(i + 2)
             to_host(h_full, y)
             for k in (1, 2):
                 pk = stz.decompress_progressive(d_comp, k, out=pouts[b][k], workspace=ws,
-                                                meta=meta)
+                                                meta=meta, stream=cstream)
                 to_host(h_p[k][: pk.numel()], pk.reshape(-1))
             bx = stz.decompress_region(d_comp, blo, bhi, 3, out=boxes[b], workspace=ws,
-                                       meta=meta)
+                                       meta=meta, stream=cstream)
             to_host(h_box[: bx.numel()], bx.reshape(-1))
             sl = stz.decompress_region(d_comp, slo, shi, 3, out=slabs[b], workspace=ws,
-                                       meta=meta)
+                                       meta=meta, stream=cstream)
             to_host(h_slab[: sl.numel()], sl.reshape(-1))
-            out_free[b].record(copy)
+            out_free[b].record(down)
 
         def run(n):
-            upload(0)
+            for f in range(min(2, n)):
+                upload(f)
             for i in range(n):
-                e2e_step(i, i == n - 1)
-            done = torch.cuda.Event()
-            done.record(copy)
-            stream.wait_event(done)
+                e2e_step(i, n)
+            for cs in (up, down):
+                done = torch.cuda.Event()
+                done.record(cs)
+                cstream.wait_event(done)
 
         run(max(args.warmup, 1))
         torch.cuda.synchronize()
         barrier()
         a = torch.cuda.Event(enable_timing=True)
         b_ = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        a.record(cstream)
         run(args.steps)
-        b_.record(stream)
+        b_.record(cstream)
         torch.cuda.synchronize()
         e2e_ms = a.elapsed_time(b_) / args.steps
         e2e_ms = reduce_max(e2e_ms, dev)
