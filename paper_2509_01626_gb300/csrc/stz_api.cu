@@ -1,6 +1,7 @@
 // stz_api.cu -- the C ABI (include/stz.h): argument checks, workspace
 // planning, container header parsing and launch sequencing.  Every step of
 // the method runs in the kernels of the other translation units.
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -855,6 +856,124 @@ static void hdr_cache_put(int dev, const void* ptr, size_t bytes, const Hdr& H, 
   e.last = ++g_hc_tick;
 }
 
+// Captured decodes.  A plain decode seen twice with the same arguments and
+// header bytes is captured as a graph on the second call and replayed from
+// then on (one-off calls, such as random boxes, never pay for a capture).
+namespace {
+struct DecKey {
+  int dev, level, whole;
+  const void* comp;
+  size_t comp_bytes;
+  int64_t lo[3], hi[3];
+  void* out;
+  size_t out_cap;
+  void* ws;
+  size_t ws_bytes;
+  size_t nraw;
+  uint64_t rawhash;  // of the header bytes (compared first)
+  uint8_t raw[STZ_HEADER_MAX_BYTES];
+};
+// equal keys: the small fields and the hash, then the header bytes
+bool same_key(const DecKey& a, const DecKey& b) {
+  return memcmp(&a, &b, offsetof(DecKey, raw)) == 0 && memcmp(a.raw, b.raw, a.nraw) == 0;
+}
+uint64_t hash_bytes(const uint8_t* p, size_t n) {  // FNV-1a over 8-byte words
+  uint64_t h = 1469598103934665603ull;
+  size_t i = 0;
+  for (; i + 8 <= n; i += 8) {
+    uint64_t w;
+    memcpy(&w, p + i, 8);
+    h = (h ^ w) * 1099511628211ull;
+  }
+  for (; i < n; i++) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
+}
+struct DecGraph {
+  DecKey key;
+  cudaGraphExec_t exec;
+  unsigned long long kernels, last;
+};
+struct DecSeen {
+  DecKey key;
+  unsigned long long last;
+};
+constexpr int kDecGraphs = 16, kDecSeen = 32;
+std::mutex g_dg_mu;
+DecGraph g_dg[kDecGraphs];  // captured decodes
+DecSeen g_ds[kDecSeen];     // decodes seen once (keys only)
+int g_ndg = 0, g_nds = 0;
+unsigned long long g_dg_tick = 0;
+}  // namespace
+
+extern "C++" {
+template <typename F>
+static int decode_graph_run(const DecKey& key, F& launch_all, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_dg_mu);
+  const unsigned long long now = ++g_dg_tick;
+  DecGraph* e = nullptr;
+  for (int i = 0; i < g_ndg; i++)
+    if (same_key(g_dg[i].key, key)) e = &g_dg[i];
+  if (!e) {
+    int seen = -1;
+    for (int i = 0; i < g_nds; i++)
+      if (same_key(g_ds[i].key, key)) seen = i;
+    if (seen < 0) {  // first sight: remember the key, launch plainly
+      int slot = 0;
+      if (g_nds < kDecSeen) {
+        slot = g_nds++;
+      } else {
+        for (int i = 1; i < kDecSeen; i++)
+          if (g_ds[i].last < g_ds[slot].last) slot = i;
+      }
+      g_ds[slot].key = key;
+      g_ds[slot].last = now;
+      return launch_all(st, false);
+    }
+    // second sight: capture into the graph table
+    g_ds[seen] = g_ds[--g_nds];
+    int slot = 0;
+    if (g_ndg < kDecGraphs) {
+      slot = g_ndg++;
+    } else {
+      for (int i = 1; i < kDecGraphs; i++)
+        if (g_dg[i].last < g_dg[slot].last) slot = i;
+      if (g_dg[slot].exec) cudaGraphExecDestroy(g_dg[slot].exec);
+    }
+    e = &g_dg[slot];
+    e->key = key;
+    e->exec = nullptr;
+    cudaStream_t& cap = g_cap_stream[key.dev];
+    if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+      cap = nullptr;
+      return STZ_ERR_CUDA;
+    }
+    cudaGraph_t graph = nullptr;
+    int rc = cuda_ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    if (rc != STZ_OK) return rc;
+    rc = launch_all(cap, true);
+    const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    if (rc == STZ_OK && ce != cudaSuccess) rc = STZ_ERR_CUDA;
+    if (rc == STZ_OK) {
+      e->kernels = graph_kernels(graph);
+      if (cudaGraphInstantiate(&e->exec, graph, 0) != cudaSuccess) {
+        e->exec = nullptr;
+        rc = STZ_ERR_CUDA;
+      }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != STZ_OK) {
+      cudaGetLastError();
+      memset(&e->key, 0, sizeof(DecKey));  // never matches (null container)
+      return launch_all(st, false);        // capture failed: this call plainly
+    }
+  }
+  e->last = now;
+  if (cudaGraphLaunch(e->exec, st) != cudaSuccess) return STZ_ERR_CUDA;
+  prof_count_launches(e->kernels);
+  return STZ_OK;
+}
+}  // extern "C++"
+
 // Options of a decode beyond the plain calls: a header parsed beforehand (no
 // read-back from the device), a decoded level-1 grid to start from, and a
 // device word that receives the status instead of a wait at the end.
@@ -1004,84 +1123,113 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     rc = (x);                    \
     if (rc != STZ_OK) return rc; \
   } while (0)
-  static_assert(sizeof(DevParams) % 4 == 0, "DevParams is cleared in words");
-  STZ_TRY(zero_words(dp, (int64_t)(sizeof(DevParams) / 4), st));
-  STZ_TRY(launch_lut(tb, lut, status, st));
-  STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
-  const uint8_t* sec0 = comp + H.d[0].sect_off;
-  SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps, H.nsub);
-  uint8_t* g1buf = have_l1 ? (uint8_t*)o.l1 : ws + P.grid[1];
-  if (!have_l1) {
-    BaseArgs a;
-    memset(&a, 0, sizeof(a));
-    a.geo = g;
-    a.dp = dp;
-    a.g1 = g1buf;
-    a.codes = codes;
-    a.sm = P.sm[0];
-    a.opos = (const uint32_t*)(sec0 + sh0.off_opos);
-    a.oval = sec0 + sh0.off_oval;
-    a.nout = (int64_t)H.d[0].nout;
-    a.two_eb = H.two_eb[1];
-    a.status = status;
-    // the part of level 1 the output depends on: the output box itself, or
-    // the coarse cells the level-2 box is predicted from
-    int64_t m1[3];
-    grid_extent(g.n, g.L, 1, m1);
-    bool whole = true;
-    for (int d = 0; d < 3; d++) {
-      a.rlo[d] = level == 1 ? P.OA[d] : imax(0, P.A[2][d] / 2 - 1);
-      a.rhi[d] = level == 1 ? P.OB[d] : imin(m1[d], P.B[2][d] / 2 + 2);
-      whole = whole && a.rlo[d] == 0 && a.rhi[d] == m1[d];
+  // every launch of this decode, on stream st (no_coop: level 1 without the
+  // cooperative launch, as inside a captured graph)
+  auto launch_all = [&](cudaStream_t st, bool no_coop) -> int {
+    static_assert(sizeof(DevParams) % 4 == 0, "DevParams is cleared in words");
+    STZ_TRY(zero_words(dp, (int64_t)(sizeof(DevParams) / 4), st));
+    STZ_TRY(launch_lut(tb, lut, status, st));
+    STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
+    const uint8_t* sec0 = comp + H.d[0].sect_off;
+    SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps, H.nsub);
+    uint8_t* g1buf = have_l1 ? (uint8_t*)o.l1 : ws + P.grid[1];
+    if (!have_l1) {
+      BaseArgs a;
+      memset(&a, 0, sizeof(a));
+      a.geo = g;
+      a.dp = dp;
+      a.g1 = g1buf;
+      a.codes = codes;
+      a.sm = P.sm[0];
+      a.opos = (const uint32_t*)(sec0 + sh0.off_opos);
+      a.oval = sec0 + sh0.off_oval;
+      a.nout = (int64_t)H.d[0].nout;
+      a.two_eb = H.two_eb[1];
+      a.status = status;
+      // the part of level 1 the output depends on: the output box itself, or
+      // the coarse cells the level-2 box is predicted from
+      int64_t m1[3];
+      grid_extent(g.n, g.L, 1, m1);
+      bool whole = true;
+      for (int d = 0; d < 3; d++) {
+        a.rlo[d] = level == 1 ? P.OA[d] : imax(0, P.A[2][d] / 2 - 1);
+        a.rhi[d] = level == 1 ? P.OB[d] : imin(m1[d], P.B[2][d] / 2 + 2);
+        whole = whole && a.rlo[d] == 0 && a.rhi[d] == m1[d];
+      }
+      a.region = whole ? 0 : 1;
+      STZ_TRY(no_coop ? launch_base_nocoop(a, true, st) : launch_base(a, true, st));
     }
-    a.region = whole ? 0 : 1;
-    STZ_TRY(launch_base(a, true, st));
-  }
-  if (level == 1) {
-    int64_t m1[3];
-    grid_extent(g.n, g.L, 1, m1);
-    const int blocks = (int)imin(cdiv(npts, 256), 4096);
-    ProfScope ps_("k_copy_box", st);
-    if (ps == 4)
-      k_copy_box<float><<<blocks, 256, 0, st>>>((const float*)g1buf, (float*)out_dev, P.OA[0],
-                                                P.OA[1], P.OA[2], od[0], od[1], od[2], m1[1],
-                                                m1[2]);
-    else
-      k_copy_box<double><<<blocks, 256, 0, st>>>((const double*)g1buf, (double*)out_dev, P.OA[0],
-                                                 P.OA[1], P.OA[2], od[0], od[1], od[2], m1[1],
-                                                 m1[2]);
-    STZ_TRY(cuda_ok(cudaGetLastError()));
-  }
-  for (int j = 2; j <= level; j++) {
-    LevelArgs a;
-    memset(&a, 0, sizeof(a));
-    a.geo = g;
-    a.level = j;
-    a.dp = dp;
-    a.coarse = (j == 2) ? (const void*)g1buf : (const void*)(ws + P.grid[j - 1]);
-    a.fine = (j == level) ? out_dev : (void*)(ws + P.grid[j]);
-    for (int d = 0; d < 3; d++) {
-      a.clo[d] = P.A[j - 1][d];
-      a.chi[d] = P.B[j - 1][d];
-      a.flo[d] = P.A[j][d];
-      a.fhi[d] = P.B[j][d];
-      a.tlo[d] = P.tlo[j][d];
-      a.tcnt[d] = P.tcnt[j][d];
+    if (level == 1) {
+      int64_t m1[3];
+      grid_extent(g.n, g.L, 1, m1);
+      const int blocks = (int)imin(cdiv(npts, 256), 4096);
+      ProfScope ps_("k_copy_box", st);
+      if (ps == 4)
+        k_copy_box<float><<<blocks, 256, 0, st>>>((const float*)g1buf, (float*)out_dev, P.OA[0],
+                                                  P.OA[1], P.OA[2], od[0], od[1], od[2], m1[1],
+                                                  m1[2]);
+      else
+        k_copy_box<double><<<blocks, 256, 0, st>>>((const double*)g1buf, (double*)out_dev, P.OA[0],
+                                                   P.OA[1], P.OA[2], od[0], od[1], od[2], m1[1],
+                                                   m1[2]);
+      STZ_TRY(cuda_ok(cudaGetLastError()));
     }
-    a.codes = codes;
-    for (int K = 1; K <= 7; K++) {
-      const int sid = 1 + 7 * (j - 2) + K - 1;
-      a.sm[K] = P.sm[sid];
-      const uint8_t* sec = comp + H.d[sid].sect_off;
-      SectHost sh = sect_host(H.d[sid].nlive, H.d[sid].nch, H.d[sid].pw, H.d[sid].nout, ps,
-                              H.nsub);
-      a.opos[K] = (const uint32_t*)(sec + sh.off_opos);
-      a.oval[K] = sec + sh.off_oval;
-      a.nout[K] = (int64_t)H.d[sid].nout;
+    for (int j = 2; j <= level; j++) {
+      LevelArgs a;
+      memset(&a, 0, sizeof(a));
+      a.geo = g;
+      a.level = j;
+      a.dp = dp;
+      a.coarse = (j == 2) ? (const void*)g1buf : (const void*)(ws + P.grid[j - 1]);
+      a.fine = (j == level) ? out_dev : (void*)(ws + P.grid[j]);
+      for (int d = 0; d < 3; d++) {
+        a.clo[d] = P.A[j - 1][d];
+        a.chi[d] = P.B[j - 1][d];
+        a.flo[d] = P.A[j][d];
+        a.fhi[d] = P.B[j][d];
+        a.tlo[d] = P.tlo[j][d];
+        a.tcnt[d] = P.tcnt[j][d];
+      }
+      a.codes = codes;
+      for (int K = 1; K <= 7; K++) {
+        const int sid = 1 + 7 * (j - 2) + K - 1;
+        a.sm[K] = P.sm[sid];
+        const uint8_t* sec = comp + H.d[sid].sect_off;
+        SectHost sh = sect_host(H.d[sid].nlive, H.d[sid].nch, H.d[sid].pw, H.d[sid].nout, ps,
+                                H.nsub);
+        a.opos[K] = (const uint32_t*)(sec + sh.off_opos);
+        a.oval[K] = sec + sh.off_oval;
+        a.nout[K] = (int64_t)H.d[sid].nout;
+      }
+      a.two_eb = H.two_eb[j];
+      a.status = status;
+      STZ_TRY(launch_level(a, true, st));
     }
-    a.two_eb = H.two_eb[j];
-    a.status = status;
-    STZ_TRY(launch_level(a, true, st));
+    return STZ_OK;
+  };
+  // plain calls repeated with the same arguments and header replay a graph
+  if (!o.status_out && !o.hdr && !prof_enabled()) {
+    DecKey key;
+    memset(&key, 0, sizeof(key));
+    key.dev = dev;
+    key.comp = comp_dev;
+    key.comp_bytes = comp_bytes;
+    key.level = level;
+    key.whole = whole;
+    for (int a = 0; a < 3; a++) {
+      key.lo[a] = lo[a];
+      key.hi[a] = hi[a];
+    }
+    key.out = out_dev;
+    key.out_cap = out_cap;
+    key.ws = ws_dev;
+    key.ws_bytes = ws_bytes;
+    key.nraw = nraw;
+    key.rawhash = hash_bytes(raw, nraw);
+    memcpy(key.raw, raw, nraw);
+    STZ_TRY(decode_graph_run(key, launch_all, st));
+  } else {
+    STZ_TRY(launch_all(st, false));
   }
   if (o.status_out) {
     ProfScope ps_("k_readback", st);
