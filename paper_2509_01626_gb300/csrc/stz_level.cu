@@ -430,37 +430,51 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
     T p[7];
     cell_predict(w0, w1, w2, w3, p);
     if (interior && fp && fz0 && fy0 && fx0) fp[0] = w1[1];  // the coarse point itself
+    // in phases over the cell's 7 points: the arithmetic of all 7 first (7
+    // independent chains to interleave), then the stores, then the counts
+    bool on[7];
 #pragma unroll
-    for (int K = 1; K <= 7; K++) {
-      const int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
-      const bool on = cell_on(lz, K);
-      const int fo = oz * fdz + oy * fe2 + ox;
-      if (!DEC) {
-        int sym = -1;
-        if (on) {
-          T xq;
-          sym = quantize_sel(xv[K - 1], p[K - 1], q, kRadius, xq);
-          *cp[K - 1] = (uint16_t)sym;
-          if (fp) fp[fo] = xq;
-          if (sym == 0) atomicAdd(&a.chunk_outliers[ti.chunk[K]], 1u);
+    for (int K = 1; K <= 7; K++) on[K - 1] = cell_on(lz, K);
+    if (!DEC) {
+      int sym[7];
+      T xq[7];
+#pragma unroll
+      for (int K = 0; K < 7; K++) sym[K] = quantize_sel(xv[K], p[K], q, kRadius, xq[K]);
+#pragma unroll
+      for (int K = 1; K <= 7; K++) {
+        const int fo = ((K >> 2) & 1) * fdz + ((K >> 1) & 1) * fe2 + (K & 1);
+        if (!on[K - 1]) {
+          sym[K - 1] = -1;
+          continue;
         }
-        const unsigned bm = __ballot_sync(0xffffffffu, sym == kRadius);
+        *cp[K - 1] = (uint16_t)sym[K - 1];
+        if (fp) fp[fo] = xq[K - 1];
+        if (sym[K - 1] == 0) atomicAdd(&a.chunk_outliers[ti.chunk[K]], 1u);
+      }
+#pragma unroll
+      for (int K = 1; K <= 7; K++) {
+        const unsigned bm = __ballot_sync(0xffffffffu, sym[K - 1] == kRadius);
         uint32_t* h = hist + (K - 1) * kHistWords;
         if (lane == 0 && bm) atomicAdd(&h[kRadius >> 1], (uint32_t)__popc(bm));
-        if (sym >= 0 && sym != kRadius) atomicAdd(&h[sym >> 1], 1u << ((sym & 1) * 16));
-      } else if (on) {
-        const int sym = cv[K - 1];
-        T val;
-        if (sym != 0) {
-          val = dequantize(sym, p[K - 1], two_eb, kRadius);
-        } else {
+        const int sk = sym[K - 1];
+        if (sk >= 0 && sk != kRadius) atomicAdd(&h[sk >> 1], 1u << ((sk & 1) * 16));
+      }
+    } else {
+      T val[7];
+#pragma unroll
+      for (int K = 0; K < 7; K++) val[K] = dequantize(cv[K], p[K], two_eb, kRadius);
+#pragma unroll
+      for (int K = 1; K <= 7; K++) {
+        if (!on[K - 1]) continue;
+        if (cv[K - 1] == 0) {  // outlier: its value from the list
           const int64_t local = cp[K - 1] - (a.codes + ti.slot[K]);
-          if (!find_outlier(a.opos[K], (const T*)a.oval[K], a.nout[K], ti.pos[K] + local, val)) {
-            val = T(0);
+          if (!find_outlier(a.opos[K], (const T*)a.oval[K], a.nout[K], ti.pos[K] + local,
+                            val[K - 1])) {
+            val[K - 1] = T(0);
             atomicOr(a.status, kStatCorrupt);
           }
         }
-        fp[fo] = val;
+        fp[((K >> 2) & 1) * fdz + ((K >> 1) & 1) * fe2 + (K & 1)] = val[K - 1];
       }
     }
     if (!DEC) xp += 2 * xdz;

@@ -43,33 +43,42 @@ __global__ void __launch_bounds__(256) k_range(const void* __restrict__ field, i
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   if (DT == STZ_F32) {
+    // 32-bit keys (a float's key fits 32 bits; 0 and 0xFFFFFFFF are no key of
+    // a finite value, so they serve as the empty bounds)
+    uint32_t lo32 = 0xFFFFFFFFu, hi32 = 0u;
+    auto upd32 = [&](uint32_t u) {
+      if ((u & 0x7F800000u) != 0x7F800000u) {
+        const uint32_t k = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+        lo32 = min(lo32, k);
+        hi32 = max(hi32, k);
+      }
+    };
     const uint32_t* f = (const uint32_t*)field;
     const int64_t n4 = n >> 2;
     const uint4* f4 = (const uint4*)field;
     int64_t i = tid;
-    for (; i + 3 * nth < n4; i += 4 * nth) {  // four 16-byte loads in flight per thread
-      uint4 v[4];
+    for (; i + 7 * nth < n4; i += 8 * nth) {  // eight 16-byte loads in flight per thread
+      uint4 v[8];
 #pragma unroll
-      for (int k = 0; k < 4; k++) v[k] = __ldcs(f4 + i + k * nth);
+      for (int k = 0; k < 8; k++) v[k] = __ldcs(f4 + i + k * nth);
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
-        if ((v[k].x & 0x7F800000u) != 0x7F800000u) upd(key_f32(v[k].x), lo, hi);
-        if ((v[k].y & 0x7F800000u) != 0x7F800000u) upd(key_f32(v[k].y), lo, hi);
-        if ((v[k].z & 0x7F800000u) != 0x7F800000u) upd(key_f32(v[k].z), lo, hi);
-        if ((v[k].w & 0x7F800000u) != 0x7F800000u) upd(key_f32(v[k].w), lo, hi);
+      for (int k = 0; k < 8; k++) {
+        upd32(v[k].x);
+        upd32(v[k].y);
+        upd32(v[k].z);
+        upd32(v[k].w);
       }
     }
     for (; i < n4; i += nth) {
-      uint4 v = __ldg(f4 + i);
-      if ((v.x & 0x7F800000u) != 0x7F800000u) upd(key_f32(v.x), lo, hi);
-      if ((v.y & 0x7F800000u) != 0x7F800000u) upd(key_f32(v.y), lo, hi);
-      if ((v.z & 0x7F800000u) != 0x7F800000u) upd(key_f32(v.z), lo, hi);
-      if ((v.w & 0x7F800000u) != 0x7F800000u) upd(key_f32(v.w), lo, hi);
+      const uint4 v = __ldg(f4 + i);
+      upd32(v.x);
+      upd32(v.y);
+      upd32(v.z);
+      upd32(v.w);
     }
-    for (int64_t i = (n4 << 2) + tid; i < n; i += nth) {
-      uint32_t u = f[i];
-      if ((u & 0x7F800000u) != 0x7F800000u) upd(key_f32(u), lo, hi);
-    }
+    for (int64_t j = (n4 << 2) + tid; j < n; j += nth) upd32(f[j]);
+    lo = lo32 == 0xFFFFFFFFu ? ~0ull : (unsigned long long)lo32;
+    hi = (unsigned long long)hi32;
   } else {
     const unsigned long long* f = (const unsigned long long*)field;
     const int64_t n2 = n >> 1;
