@@ -110,8 +110,8 @@ static int64_t vol(const int64_t e[3]) { return e[0] * e[1] * e[2]; }
 
 // Workspace plan; offsets in bytes from the workspace base.
 struct WsPlan {
-  size_t dp, grid[kMaxLevels + 1], codes, hist, chunk_out, chunk_words, word_off, out_off, enc,
-      books, lay, lut, scan_sums, result, total;
+  size_t dp, grid[kMaxLevels + 1], codes, hist, chunk_out, chunk_words, lane_bits, word_off,
+      out_off, enc, books, lay, lut, scan_sums, result, total;
 };
 
 static WsPlan plan_compress(const Geo& g) {
@@ -135,6 +135,8 @@ static WsPlan plan_compress(const Geo& g) {
   o += al256(4 * (size_t)g.total_chunks);
   w.chunk_words = o;
   o += al256(4 * (size_t)g.total_chunks);
+  w.lane_bits = o;
+  o += al256(2 * 32 * (size_t)g.total_chunks);
   w.word_off = o;
   o += al256(8 * (size_t)(g.total_chunks + 1));
   w.out_off = o;
@@ -479,6 +481,7 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
   uint32_t* hist = (uint32_t*)(ws + w.hist);
   uint32_t* chunk_out = (uint32_t*)(ws + w.chunk_out);
   uint32_t* chunk_words = (uint32_t*)(ws + w.chunk_words);
+  uint16_t* lane_bits = (uint16_t*)(ws + w.lane_bits);
   unsigned long long* word_off = (unsigned long long*)(ws + w.word_off);
   unsigned long long* out_off = (unsigned long long*)(ws + w.out_off);
   uint16_t* enc = (uint16_t*)(ws + w.enc);
@@ -547,13 +550,13 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
     STZ_TRY(launch_level(a, false, st));
   }
   STZ_TRY(launch_codebook(g, hist, enc, books, st));
-  STZ_TRY(launch_chunk_words(g, codes, enc, chunk_words, st));
+  STZ_TRY(launch_chunk_words(g, codes, enc, chunk_words, lane_bits, st));
   STZ_TRY(launch_scan2(chunk_words, chunk_out, g.total_chunks,
                        (unsigned long long*)(ws + w.scan_sums), word_off, out_off, st));
   STZ_TRY(launch_layout(g, dp, eb_mode, word_off, out_off, books, lay, out, out_cap, st));
   STZ_TRY(launch_sections(g, lay, books, word_off, dp, out, st));
-  STZ_TRY(launch_pack(g, codes, enc, word_off, lay->s, out, dp, field_dev, chunk_out, out_off,
-                      st));
+  STZ_TRY(launch_pack(g, codes, enc, lane_bits, word_off, lay->s, out, dp, field_dev, chunk_out,
+                      out_off, st));
   unsigned long long* res = (unsigned long long*)(ws + w.result);
   {
     ProfScope ps_("k_result", st);

@@ -389,28 +389,71 @@ __device__ __forceinline__ uint32_t run_bits(const uint16_t* __restrict__ c, int
   return bits;
 }
 
-// payload words per chunk
+// Encode entries of the 8 symbols held in one 16-byte word of codes.
+__device__ __forceinline__ void ent8(const uint4& v, const uint16_t* __restrict__ e,
+                                     uint32_t (&ent)[8]) {
+  const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    ent[2 * k] = __ldg(e + (u[k] & 0xFFFFu));
+    ent[2 * k + 1] = __ldg(e + (u[k] >> 16));
+  }
+}
+
+// Payload words per chunk, and the bits of each lane's run of 64 symbols
+// (the packing pass's lane split).  A whole chunk is read with coalesced
+// 16-byte loads, eight in flight per lane: load k gives lane t the symbols
+// [8 (32 k + t), +8), which belong to lane run 4 k + t / 8; the eight lanes
+// of a run add their bits by shuffle, and lane r collects run r's sum.
 __global__ void __launch_bounds__(256) k_chunk_words(const __grid_constant__ Geo g,
                                                      const uint16_t* __restrict__ codes,
                                                      const uint16_t* __restrict__ enc,
-                                                     uint32_t* __restrict__ words) {
+                                                     uint32_t* __restrict__ words,
+                                                     uint16_t* __restrict__ lane_bits) {
   const int lane = threadIdx.x & 31;
   const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j >= g.total_chunks) return;
   int sid, cnt;
   chunk_sid_cnt(g, j, sid, cnt);
-  const int s0 = lane * kLaneSyms, s1 = min(cnt, s0 + kLaneSyms);
-  uint32_t bits = run_bits(codes + j * g.bvol, s0, s1, enc + (int64_t)sid * kAlphabet);
+  const uint16_t* c = codes + j * g.bvol;
+  const uint16_t* e = enc + (int64_t)sid * kAlphabet;
+  uint32_t mine = 0;
+  if (cnt == 32 * kLaneSyms) {
+    const uint4* c4 = (const uint4*)c;
+    uint4 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = __ldg(c4 + 32 * k + lane);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      uint32_t ent[8];
+      ent8(v[k], e, ent);
+      uint32_t b = 0;
+#pragma unroll
+      for (int m = 0; m < 8; m++) b += ent[m] & 15u;
+      b += __shfl_xor_sync(0xffffffffu, b, 1);
+      b += __shfl_xor_sync(0xffffffffu, b, 2);
+      b += __shfl_xor_sync(0xffffffffu, b, 4);
+      const uint32_t t = __shfl_sync(0xffffffffu, b, 8 * (lane & 3));
+      if ((lane >> 2) == k) mine = t;
+    }
+  } else {
+    const int s0 = lane * kLaneSyms, s1 = min(cnt, s0 + kLaneSyms);
+    mine = run_bits(c, s0, s1, e);
+  }
+  lane_bits[j * 32 + lane] = (uint16_t)mine;
+  uint32_t bits = mine;
   for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
   if (lane == 0) words[j] = (bits + 31) >> 5;
 }
 
 int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc, uint32_t* words,
-                       cudaStream_t s) {
+                       uint16_t* lane_bits, cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
-  if (g.bvol > 32 * kLaneSyms) return STZ_ERR_ARG;
+  // a warp covers a chunk; 16-byte code loads need chunks on 16-byte bounds
+  if (g.bvol > 32 * kLaneSyms || g.bvol % 8 != 0) return STZ_ERR_ARG;
   ProfScope ps_("k_chunk_words", s, 2.0 * (double)total_symbols(g));  // one read of the codes
-  k_chunk_words<<<(unsigned)cdiv(g.total_chunks, 8), 256, 0, s>>>(g, codes, enc, words);
+  k_chunk_words<<<(unsigned)cdiv(g.total_chunks, 8), 256, 0, s>>>(g, codes, enc, words,
+                                                                   lane_bits);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -544,24 +587,22 @@ int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long 
 }
 
 // ---------------------------------------------------------------- bit packing
-// Blocks loop over chunks: each thread takes 8 consecutive symbols, a block
-// scan of their code lengths gives bit positions, the thread assembles its
-// (at most 96) bits in registers and ORs them into at most 4 words of the
-// chunk held in shared memory; the words are stored with coalesced writes.
-// The sub-chunk offsets are the bit positions of symbols u * ceil(n / 4).
-// Payload of every chunk.  One warp per chunk: each lane counts its
-// symbols' bits, a warp scan gives each lane its first bit, then each lane
-// appends its codes, two at a time, to a 64-bit accumulator and stores the
-// 32-bit words that fill.  A word that straddles two lanes' runs (only the
-// first word of a lane whose run does not start on a word) is stored by the
-// lane before, which ORs in the part the later lane hands it by shuffle.
-// Every lane but the chunk's last holds 64 symbols, so at least 64 bits: only
-// neighbouring lanes ever share a word.  The lanes holding a sub-chunk start
-// sum the lengths before it for the sub-chunk's bit offset.
+// Payload of every chunk.  One warp per chunk: each lane takes the bit count
+// of its run of 64 symbols from the counting pass, a warp scan gives each
+// lane its first bit, then each lane appends its codes, two at a time, to a
+// 64-bit accumulator and stores the 32-bit words that fill.  A word that
+// straddles two lanes' runs (only the first word of a lane whose run does not
+// start on a word) is stored by the lane before, which ORs in the part the
+// later lane hands it by shuffle.  Every lane but the chunk's last holds 64
+// symbols, so at least 64 bits: only neighbouring lanes ever share a word.
+// The lanes holding a sub-chunk start sum the lengths before it for the
+// sub-chunk's bit offset.  A lane with a whole run loads its 128 bytes of
+// codes at once and works from registers, the outlier listing included.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
                                               const uint16_t* __restrict__ codes,
                                               const uint16_t* __restrict__ enc,
+                                              const uint16_t* __restrict__ lane_bits,
                                               const unsigned long long* __restrict__ word_off,
                                               const SectDev* __restrict__ sect,
                                               uint8_t* __restrict__ out,
@@ -578,7 +619,14 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
   const uint16_t* e = enc + (int64_t)sid * kAlphabet;
   const uint16_t* c = codes + j * g.bvol;
   const int s0 = lane * kLaneSyms, s1 = min(cnt, s0 + kLaneSyms);
-  const uint32_t bits = run_bits(c, s0, s1, e);
+  const bool whole = s1 - s0 == kLaneSyms;
+  uint4 v[8];
+  if (whole) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = __ldg((const uint4*)(c + s0) + k);
+  }
+  const bool has_out = chunk_outliers[j] != 0;
+  const uint32_t bits = lane_bits[j * 32 + lane];
   uint32_t incl = bits;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -603,9 +651,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
   uint32_t widx = p >> 5, nacc = p & 31u, first_part = 0;
   bool first_pending = nacc != 0;
   unsigned long long acc = 0;
-  for (int i = s0; i < s1; i += 8) {
-    uint32_t ent[8];
-    enc8(c, i, s1, e, ent);
+  auto push8 = [&](const uint32_t (&ent)[8]) {
 #pragma unroll
     for (int k = 0; k < 8; k += 2) {
       // two codes joined (at most 24 bits); past the end both are empty
@@ -626,6 +672,29 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
         widx++;
       }
     }
+  };
+  unsigned long long zmask = 0;  // symbols 0 (outliers) of a whole run
+  if (whole) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      uint32_t ent[8];
+      ent8(v[k], e, ent);
+      push8(ent);
+      if (has_out) {
+        const uint32_t u[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+          if ((u[h] & 0xFFFFu) == 0u) zmask |= 1ull << (8 * k + 2 * h);
+          if ((u[h] >> 16) == 0u) zmask |= 1ull << (8 * k + 2 * h + 1);
+        }
+      }
+    }
+  } else {
+    for (int i = s0; i < s1; i += 8) {
+      uint32_t ent[8];
+      enc8(c, i, s1, e, ent);
+      push8(ent);
+    }
   }
   bool has_last = nacc > 0 && s1 > s0;
   const uint32_t last = has_last ? (uint32_t)(acc << (32u - nacc)) : 0u;
@@ -638,9 +707,13 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
   if (has_last) dst[widx] = last | from_next;
   // the chunk's outliers (symbol 0): stream position and raw value, in stream
   // order from the chunk's offset in the stream's outlier list
-  if (chunk_outliers[j] == 0) return;
+  if (!has_out) return;
   uint32_t nz = 0;
-  for (int i = s0; i < s1; i++) nz += __ldg(c + i) == 0;
+  if (whole) {
+    nz = (uint32_t)__popcll(zmask);
+  } else {
+    for (int i = s0; i < s1; i++) nz += __ldg(c + i) == 0;
+  }
   uint32_t zincl = nz;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -655,8 +728,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
   uint32_t* opos = (uint32_t*)(out + sd.sect_off + sd.off_opos);
   T* oval = (T*)(out + sd.sect_off + sd.off_oval);
   unsigned long long k = out_off[j] - sd.out0 + (zincl - nz);
-  for (int i = s0; i < s1; i++) {
-    if (__ldg(c + i) != 0) continue;
+  auto list = [&](int i) {
     const int64_t lz = i / (l[1] * l[2]), ly = (i / l[2]) % l[1], lx = i % l[2];
     int64_t pt[3] = {B[0] * g.b[0] + lz, B[1] * g.b[1] + ly, B[2] * g.b[2] + lx};
     if (sg.level > 1)
@@ -664,23 +736,33 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
     opos[k] = (uint32_t)(start + i);
     oval[k] = field[((pt[0] * st) * g.n[1] + pt[1] * st) * g.n[2] + pt[2] * st];
     k++;
+  };
+  if (whole) {
+    while (zmask) {
+      list(s0 + __ffsll((long long)zmask) - 1);
+      zmask &= zmask - 1;
+    }
+  } else {
+    for (int i = s0; i < s1; i++)
+      if (__ldg(c + i) == 0) list(i);
   }
 }
 
 int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
-                const unsigned long long* word_off, const SectDev* sect, uint8_t* out,
-                const DevParams* dp, const void* field, const uint32_t* chunk_outliers,
-                const unsigned long long* out_off, cudaStream_t s) {
+                const uint16_t* lane_bits, const unsigned long long* word_off,
+                const SectDev* sect, uint8_t* out, const DevParams* dp, const void* field,
+                const uint32_t* chunk_outliers, const unsigned long long* out_off,
+                cudaStream_t s) {
   if (g.total_chunks == 0) return STZ_OK;
-  if (g.bvol > 32 * kLaneSyms) return STZ_ERR_ARG;
+  if (g.bvol > 32 * kLaneSyms || g.bvol % 8 != 0) return STZ_ERR_ARG;
   const unsigned grid = (unsigned)cdiv(g.total_chunks, 8);
   // reads the codes; the payload it writes is added once its size is known
   ProfScope ps_("k_pack", s, 2.0 * (double)total_symbols(g));
   if (g.dtype == STZ_F32)
-    k_pack<float><<<grid, 256, 0, s>>>(g, codes, enc, word_off, sect, out, dp,
+    k_pack<float><<<grid, 256, 0, s>>>(g, codes, enc, lane_bits, word_off, sect, out, dp,
                                        (const float*)field, chunk_outliers, out_off);
   else
-    k_pack<double><<<grid, 256, 0, s>>>(g, codes, enc, word_off, sect, out, dp,
+    k_pack<double><<<grid, 256, 0, s>>>(g, codes, enc, lane_bits, word_off, sect, out, dp,
                                         (const double*)field, chunk_outliers, out_off);
   return cuda_ok(cudaGetLastError());
 }

@@ -70,9 +70,10 @@ struct BookDev {
 };
 int launch_codebook(const Geo& g, const uint32_t* hist, uint16_t* enc, BookDev* books,
                     cudaStream_t s);
-// bits per chunk -> words per chunk
+// payload words per chunk, and the bits of each 64-symbol lane run of a chunk
+// (32 u16 per chunk) for the packing pass
 int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc,
-                       uint32_t* chunk_words, cudaStream_t s);
+                       uint32_t* chunk_words, uint16_t* lane_bits, cudaStream_t s);
 // exclusive scans of two n-entry u32 arrays into (n+1)-entry u64 arrays;
 // sums: 2 * ceil(n / 4096) scratch entries
 int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long long* sums,
@@ -80,7 +81,8 @@ int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long 
 // pack every chunk's codes into the container payload and list its outliers
 struct SectDev;  // stz_container.cu
 int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
-                const unsigned long long* word_off, const SectDev* sect, uint8_t* out,
+                const uint16_t* lane_bits, const unsigned long long* word_off,
+                const SectDev* sect, uint8_t* out,
                 const DevParams* dp, const void* field, const uint32_t* chunk_outliers,
                 const unsigned long long* out_off, cudaStream_t s);
 
