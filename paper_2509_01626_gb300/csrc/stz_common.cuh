@@ -158,10 +158,32 @@ __device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(
 __device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float op_abs(float a) { return fabsf(a); }
 __device__ __forceinline__ double op_abs(double a) { return fabs(a); }
-__device__ __forceinline__ int to_int_rn(float v) { return __float2int_rn(v); }
-__device__ __forceinline__ int to_int_rn(double v) { return __double2int_rn(v); }
-__device__ __forceinline__ float from_int(int v, float) { return __int2float_rn(v); }
-__device__ __forceinline__ double from_int(int v, double) { return (double)v; }
+// Quantization integers (|v| < 2^22) to and from floating point with plain
+// additions instead of conversion instructions: in [2^23, 2^24) the ulp of a
+// float is 1, so adding 1.5 * 2^23 rounds v to an integer (to nearest, ties
+// to even, as rint does) that sits in the low bits of the sum's encoding, and
+// subtracting it back is exact.  The same holds for doubles with 1.5 * 2^52.
+constexpr float kMagicF = 12582912.0f;              // 1.5 * 2^23
+constexpr int kMagicFBits = 0x4B400000;             // its encoding
+constexpr double kMagicD = 6755399441055744.0;      // 1.5 * 2^52
+constexpr long long kMagicDBits = 0x4338000000000000LL;
+// rint(v) as a value, and as an integer in q
+__device__ __forceinline__ float round_q(float v, int& q) {
+  const float t = __fadd_rn(v, kMagicF);
+  q = __float_as_int(t) - kMagicFBits;
+  return __fsub_rn(t, kMagicF);
+}
+__device__ __forceinline__ double round_q(double v, int& q) {
+  const double t = __dadd_rn(v, kMagicD);
+  q = (int)(__double_as_longlong(t) - kMagicDBits);
+  return __dsub_rn(t, kMagicD);
+}
+__device__ __forceinline__ float from_int(int v, float) {
+  return __fsub_rn(__int_as_float(kMagicFBits + v), kMagicF);
+}
+__device__ __forceinline__ double from_int(int v, double) {
+  return __dsub_rn(__longlong_as_double(kMagicDBits + v), kMagicD);
+}
 
 template <typename T> struct QConst;
 template <> struct QConst<float> {
@@ -195,8 +217,9 @@ __device__ __forceinline__ int quantize(T x, T pred, const QConst<T>& q, int R, 
     xr = x;
     return 0;
   }
-  int qi = to_int_rn(qf);
-  T rec = op_add(pred, op_mul(from_int(qi, T()), q.two_eb));
+  int qi;
+  const T qr = round_q(qf, qi);
+  T rec = op_add(pred, op_mul(qr, q.two_eb));
   T e = op_sub(rec, x);
   if (!(op_abs(e) <= q.ebc)) {
     xr = x;
@@ -213,8 +236,11 @@ __device__ __forceinline__ int quantize_sel(T x, T pred, const QConst<T>& q, int
   const T d = op_sub(x, pred);
   const T qf = op_mul(d, q.inv2eb);
   const bool in_range = op_abs(qf) < q.rlim;
-  const int qi = in_range ? to_int_rn(qf) : 0;
-  const T rec = op_add(pred, op_mul(from_int(qi, T()), q.two_eb));
+  int qi;
+  T qr = round_q(qf, qi);
+  qi = in_range ? qi : 0;
+  qr = in_range ? qr : T(0);
+  const T rec = op_add(pred, op_mul(qr, q.two_eb));
   const bool ok = in_range && (op_abs(op_sub(rec, x)) <= q.ebc);
   xr = ok ? rec : x;
   return ok ? qi + R : 0;

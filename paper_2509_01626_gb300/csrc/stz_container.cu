@@ -28,22 +28,28 @@ __device__ __forceinline__ void put_f64(uint8_t* p, double v) {
   put_u64(p, (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void k_layout(const __grid_constant__ Geo g, const DevParams* __restrict__ dp,
-                         int eb_mode, const unsigned long long* __restrict__ word_off,
-                         const unsigned long long* __restrict__ out_off,
-                         const BookDev* __restrict__ books, LayoutDev* __restrict__ lay,
-                         uint8_t* __restrict__ out, unsigned long long cap) {
+// One thread per stream lays out its section; the section offsets are the
+// prefix sums of the sizes.  64 threads cover kMaxStreams.
+constexpr int kLayoutThreads = 64;
+static_assert(kMaxStreams <= kLayoutThreads, "one thread per stream");
+
+__global__ void __launch_bounds__(kLayoutThreads) k_layout(
+    const __grid_constant__ Geo g, const DevParams* __restrict__ dp, int eb_mode,
+    const unsigned long long* __restrict__ word_off,
+    const unsigned long long* __restrict__ out_off, const BookDev* __restrict__ books,
+    LayoutDev* __restrict__ lay, uint8_t* __restrict__ out, unsigned long long cap) {
+  __shared__ unsigned long long size[kLayoutThreads];
+  const int t = threadIdx.x;
   const unsigned long long ps = g.dtype == STZ_F32 ? 4 : 8;
-  unsigned long long off = kHeaderBytes + (unsigned long long)g.nstreams * kDirEntryBytes;
-  for (int s = 0; s < g.nstreams; s++) {
-    const StreamGeo& sg = g.s[s];
-    SectDev& d = lay->s[s];
+  SectDev d;
+  if (t < g.nstreams) {
+    const StreamGeo& sg = g.s[t];
     const unsigned long long nch = (unsigned long long)sg.nchunks;
     d.word0 = word_off[sg.chunk0];
     d.out0 = out_off[sg.chunk0];
     d.pw = word_off[sg.chunk0 + sg.nchunks] - d.word0;
     d.nout = out_off[sg.chunk0 + sg.nchunks] - d.out0;
-    d.nlive = books[s].nlive;
+    d.nlive = books[t].nlive;
     d.off_syms = 0;
     d.off_lens = 2 * d.nlive;
     d.off_chunks = al4(3 * d.nlive);
@@ -52,15 +58,38 @@ __global__ void k_layout(const __grid_constant__ Geo g, const DevParams* __restr
     d.off_opos = d.off_payload + 4 * d.pw;
     d.off_oval = al8(d.off_opos + 4 * d.nout);
     d.size = al8(d.off_oval + ps * d.nout);
-    d.sect_off = off;
-    off += d.size;
+    size[t] = d.size;
   }
-  lay->total = off;
-  if (off > cap) {
-    atomicOr((uint32_t*)&dp->status, kStatCapacity);
+  __syncthreads();
+  const unsigned long long dir_end =
+      kHeaderBytes + (unsigned long long)g.nstreams * kDirEntryBytes;
+  unsigned long long off = dir_end, total = dir_end;
+  for (int k = 0; k < g.nstreams; k++) {
+    off += k < t ? size[k] : 0ull;
+    total += size[k];
+  }
+  if (t < g.nstreams) {
+    d.sect_off = off;
+    lay->s[t] = d;
+  }
+  if (t == 0) lay->total = total;
+  if (total > cap) {
+    if (t == 0) atomicOr((uint32_t*)&dp->status, kStatCapacity);
     return;
   }
-  for (int i = 0; i < kHeaderBytes; i++) out[i] = 0;
+  if (t < g.nstreams) {
+    uint8_t* e = out + kHeaderBytes + (size_t)t * kDirEntryBytes;
+    put_u64(e + 0, d.sect_off);
+    put_u64(e + 8, (unsigned long long)g.s[t].nsym);
+    put_u32(e + 16, (uint32_t)g.s[t].nchunks);
+    put_u32(e + 20, (uint32_t)d.nlive);
+    put_u64(e + 24, d.pw);
+    put_u64(e + 32, d.nout);
+    put_u64(e + 40, 0);
+  }
+  for (int i = t; i < kHeaderBytes; i += kLayoutThreads) out[i] = 0;
+  __syncthreads();
+  if (t != 0) return;
   out[0] = 'S';
   out[1] = 'T';
   out[2] = 'Z';
@@ -80,23 +109,12 @@ __global__ void k_layout(const __grid_constant__ Geo g, const DevParams* __restr
   put_f64(out + 64, dp->eb_abs);
   put_f64(out + 72, dp->vmin);
   put_f64(out + 80, dp->vmax);
-  put_u64(out + 88, off);
+  put_u64(out + 88, total);
   for (int l = 1; l <= g.L; l++) {
     put_f64(out + 96 + 8 * (l - 1), dp->eb_level[l]);
     put_f64(out + 144 + 8 * (l - 1), dp->two_eb_d[l]);
   }
   put_f64(out + 192, 2.5);
-  for (int s = 0; s < g.nstreams; s++) {
-    uint8_t* d = out + kHeaderBytes + (size_t)s * kDirEntryBytes;
-    const SectDev& sd = lay->s[s];
-    put_u64(d + 0, sd.sect_off);
-    put_u64(d + 8, (unsigned long long)g.s[s].nsym);
-    put_u32(d + 16, (uint32_t)g.s[s].nchunks);
-    put_u32(d + 20, (uint32_t)sd.nlive);
-    put_u64(d + 24, sd.pw);
-    put_u64(d + 32, sd.nout);
-    put_u64(d + 40, 0);
-  }
 }
 
 int launch_layout(const Geo& g, const DevParams* dp, int eb_mode,
@@ -104,8 +122,8 @@ int launch_layout(const Geo& g, const DevParams* dp, int eb_mode,
                   const BookDev* books, LayoutDev* lay, uint8_t* out, size_t cap,
                   cudaStream_t s) {
   ProfScope ps_("k_layout", s);
-  k_layout<<<1, 1, 0, s>>>(g, dp, eb_mode, word_off, out_off, books, lay, out,
-                           (unsigned long long)cap);
+  k_layout<<<1, kLayoutThreads, 0, s>>>(g, dp, eb_mode, word_off, out_off, books, lay, out,
+                                        (unsigned long long)cap);
   return cuda_ok(cudaGetLastError());
 }
 
