@@ -110,8 +110,8 @@ static int64_t vol(const int64_t e[3]) { return e[0] * e[1] * e[2]; }
 
 // Workspace plan; offsets in bytes from the workspace base.
 struct WsPlan {
-  size_t dp, grid[kMaxLevels + 1], codes, hist, chunk_out, chunk_words, lane_bits, word_off,
-      out_off, enc, books, lay, lut, scan_sums, result, total;
+  size_t dp, range_part, grid[kMaxLevels + 1], codes, hist, chunk_out, chunk_words, lane_bits,
+      word_off, out_off, enc, books, lay, lut, scan_sums, result, total;
 };
 
 static WsPlan plan_compress(const Geo& g) {
@@ -121,6 +121,8 @@ static WsPlan plan_compress(const Geo& g) {
   size_t o = 0;
   w.dp = o;
   o += al256(sizeof(DevParams));
+  w.range_part = o;
+  o += al256(16 * (size_t)kRangeMaxBlocks);
   for (int l = 1; l < g.L; l++) {
     int64_t m[3];
     grid_extent(g.n, g.L, l, m);
@@ -494,11 +496,15 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
     rc = (x);               \
     if (rc != STZ_OK) return rc; \
   } while (0)
-  STZ_TRY(zero_words(hist, (int64_t)g.nstreams * kAlphabet, st));
-  STZ_TRY(zero_words(chunk_out, g.total_chunks, st));
-  STZ_TRY(launch_params_init(dp, st));
-  if (eb_mode == STZ_EB_REL) STZ_TRY(launch_range(field_dev, dtype, vol(n), dp, st));
-  STZ_TRY(launch_params(dp, dtype, eb_mode, eb, g.L, kRadius, st));
+  {
+    // the range pass (none in absolute mode) also clears the histograms and
+    // the per-chunk outlier counts
+    unsigned long long* part = (unsigned long long*)(ws + w.range_part);
+    int nparts = 0;
+    STZ_TRY(launch_range(field_dev, dtype, eb_mode == STZ_EB_REL ? vol(n) : 0, part, &nparts,
+                         hist, (int64_t)g.nstreams * kAlphabet, chunk_out, g.total_chunks, st));
+    STZ_TRY(launch_params(dp, part, nparts, dtype, eb_mode, eb, g.L, kRadius, st));
+  }
   {
     BaseArgs a;
     memset(&a, 0, sizeof(a));

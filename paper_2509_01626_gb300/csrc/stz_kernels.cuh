@@ -6,11 +6,16 @@
 namespace stz {
 
 // ---- stz_range.cu: value range and error-bound constants ----
-int launch_params_init(DevParams* dp, cudaStream_t s);
-// min / max over the finite values of the field into dp->range_lo/hi
-int launch_range(const void* field, int dtype, int64_t n, DevParams* dp, cudaStream_t s);
-// eb_abs, per-level bounds and quantizer constants (one thread)
-int launch_params(DevParams* dp, int dtype, int eb_mode, double eb, int L, int R, cudaStream_t s);
+// Per-block min / max keys over the finite values of the field (n = 0: none)
+// into part[2 b], part[2 b + 1], b < *nparts (at most kRangeMaxBlocks); the
+// same launch zero-fills the word ranges (z0, nz0) and (z1, nz1).
+constexpr int kRangeMaxBlocks = 2048;
+int launch_range(const void* field, int dtype, int64_t n, unsigned long long* part, int* nparts,
+                 uint32_t* z0, int64_t nz0, uint32_t* z1, int64_t nz1, cudaStream_t s);
+// Reduces the range partials (relative mode) and writes the whole of *dp:
+// range, eb_abs, per-level bounds, quantizer constants, status 0.
+int launch_params(DevParams* dp, const unsigned long long* part, int nparts, int dtype,
+                  int eb_mode, double eb, int L, int R, cudaStream_t s);
 
 // ---- stz_base.cu: level 1 (SZ3-style axis passes) ----
 struct BaseArgs {

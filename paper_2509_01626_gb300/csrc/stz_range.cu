@@ -24,12 +24,6 @@ __device__ __forceinline__ double val_f64(unsigned long long k) {
   return __longlong_as_double((long long)u);
 }
 
-__global__ void k_params_init(DevParams* dp) {
-  dp->range_lo = ~0ull;
-  dp->range_hi = 0ull;
-  dp->status = 0;
-}
-
 __device__ __forceinline__ void upd(unsigned long long k, unsigned long long& lo,
                                     unsigned long long& hi) {
   lo = k < lo ? k : lo;
@@ -38,10 +32,14 @@ __device__ __forceinline__ void upd(unsigned long long k, unsigned long long& lo
 
 template <int DT>
 __global__ void __launch_bounds__(256) k_range(const void* __restrict__ field, int64_t n,
-                                               DevParams* dp) {
+                                               unsigned long long* __restrict__ part,
+                                               uint32_t* __restrict__ z0, int64_t nz0,
+                                               uint32_t* __restrict__ z1, int64_t nz1) {
   unsigned long long lo = ~0ull, hi = 0ull;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < nz0; i += nth) z0[i] = 0u;
+  for (int64_t i = tid; i < nz1; i += nth) z1[i] = 0u;
   if (DT == STZ_F32) {
     // 32-bit keys (a float's key fits 32 bits; 0 and 0xFFFFFFFF are no key of
     // a finite value, so they serve as the empty bounds)
@@ -112,15 +110,47 @@ __global__ void __launch_bounds__(256) k_range(const void* __restrict__ field, i
       lo = slo[i] < lo ? slo[i] : lo;
       hi = shi[i] > hi ? shi[i] : hi;
     }
-    if (lo != ~0ull) atomicMin(&dp->range_lo, lo);
-    if (hi != 0ull) atomicMax(&dp->range_hi, hi);
+    part[2 * blockIdx.x] = lo;
+    part[2 * blockIdx.x + 1] = hi;
   }
 }
 
 // largest float <= v (v > 0)
 __device__ __forceinline__ float rz_float(double v) { return __double2float_rz(v); }
 
-__global__ void k_params(DevParams* dp, int dtype, int eb_mode, double eb, int L, int R) {
+__global__ void __launch_bounds__(256) k_params(DevParams* dp,
+                                                const unsigned long long* __restrict__ part,
+                                                int nparts, int dtype, int eb_mode, double eb,
+                                                int L, int R) {
+  unsigned long long lo = ~0ull, hi = 0ull;
+  if (eb_mode == STZ_EB_REL) {
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+      const unsigned long long l = part[2 * b], h = part[2 * b + 1];
+      lo = l < lo ? l : lo;
+      hi = h > hi ? h : hi;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+    const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  __shared__ unsigned long long slo[8], shi[8];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    slo[w] = lo;
+    shi[w] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
+    lo = slo[i] < lo ? slo[i] : lo;
+    hi = shi[i] > hi ? shi[i] : hi;
+  }
+  dp->range_lo = lo;
+  dp->range_hi = hi;
+  dp->status = 0;
   double vmin = 0.0, vmax = 0.0;
   bool any = false;
   if (eb_mode == STZ_EB_REL && dp->range_lo != ~0ull) {
@@ -165,26 +195,23 @@ __global__ void k_params(DevParams* dp, int dtype, int eb_mode, double eb, int L
   (void)R;
 }
 
-int launch_params_init(DevParams* dp, cudaStream_t s) {
-  ProfScope ps_("k_params_init", s);
-  k_params_init<<<1, 1, 0, s>>>(dp);
-  return cuda_ok(cudaGetLastError());
-}
-
-int launch_range(const void* field, int dtype, int64_t n, DevParams* dp, cudaStream_t s) {
+int launch_range(const void* field, int dtype, int64_t n, unsigned long long* part, int* nparts,
+                 uint32_t* z0, int64_t nz0, uint32_t* z1, int64_t nz1, cudaStream_t s) {
   const int sms = launch_sms();
-  int64_t per = dtype == STZ_F32 ? 4 : 2;
-  int64_t want = cdiv(cdiv(n, per), 256);
-  int blocks = (int)imin(imax(want, 1), (int64_t)sms * 8);
+  const int64_t per = dtype == STZ_F32 ? 4 : 2;
+  const int64_t want = imax(cdiv(cdiv(n, per), 256), cdiv(imax(nz0, nz1), 256));
+  const int blocks = (int)imin(imax(want, 1), imin((int64_t)sms * 8, kRangeMaxBlocks));
+  *nparts = blocks;
   ProfScope ps_("k_range", s, (double)n * (dtype == STZ_F32 ? 4 : 8));  // one read of the field
-  if (dtype == STZ_F32) k_range<STZ_F32><<<blocks, 256, 0, s>>>(field, n, dp);
-  else k_range<STZ_F64><<<blocks, 256, 0, s>>>(field, n, dp);
+  if (dtype == STZ_F32) k_range<STZ_F32><<<blocks, 256, 0, s>>>(field, n, part, z0, nz0, z1, nz1);
+  else k_range<STZ_F64><<<blocks, 256, 0, s>>>(field, n, part, z0, nz0, z1, nz1);
   return cuda_ok(cudaGetLastError());
 }
 
-int launch_params(DevParams* dp, int dtype, int eb_mode, double eb, int L, int R, cudaStream_t s) {
+int launch_params(DevParams* dp, const unsigned long long* part, int nparts, int dtype,
+                  int eb_mode, double eb, int L, int R, cudaStream_t s) {
   ProfScope ps_("k_params", s);
-  k_params<<<1, 1, 0, s>>>(dp, dtype, eb_mode, eb, L, R);
+  k_params<<<1, 256, 0, s>>>(dp, part, nparts, dtype, eb_mode, eb, L, R);
   return cuda_ok(cudaGetLastError());
 }
 
