@@ -569,6 +569,86 @@ struct ShellGeo {
   int64_t nA, nB, nC;
 };
 
+// Prediction of the sub-block-K point of a boundary cell, the rules of
+// level_predict with the taps read through per-axis offsets: tap(dz, dy, dx)
+// is the coarse value at cell + (dz, dy, dx), d in -1..2, clamped into the
+// coarse box (a clamped tap is never one a chosen rule uses).  cub[a]: the
+// cubic stencil fits along axis a at the odd point; rule[a]: the one-axis
+// rule there otherwise.  Unused slots of the low-order rules are computed and
+// discarded, so every used value has the operation order of level_predict.
+template <typename T>
+struct ShellTaps {
+  const T* __restrict__ cb;  // coarse value of the cell
+  int oz[4], oy[4], ox[4];   // element offsets of d = -1, 0, 1, 2 per axis
+  __device__ __forceinline__ T operator()(int dz, int dy, int dx) const {
+    return __ldg(cb + (oz[dz + 1] + oy[dy + 1] + ox[dx + 1]));
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T rule_sel(int r, T w0, T w1, T w2) {
+  const T mid = op_mul(op_add(w0, w1), T(0.5));
+  const T ext = op_add(w0, op_mul(op_sub(w0, w2), T(0.5)));
+  return r == kMid ? mid : (r == kExt ? ext : w0);
+}
+
+// coarse offset of slot q of a one-axis rule: 0 -> 0, 1 -> +1, 2 -> -1
+__device__ __forceinline__ constexpr int sd(int q) { return q == 0 ? 0 : (q == 1 ? 1 : -1); }
+
+template <int K, typename T>
+__device__ __forceinline__ T shell_predict(const ShellTaps<T>& t, const bool cub[3],
+                                           const int rule[3]) {
+  constexpr int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
+  constexpr int nodd = oz + oy + ox;
+  constexpr int a0 = oz ? 0 : (oy ? 1 : 2);
+  constexpr int a1 = nodd >= 2 ? (oz ? (oy ? 1 : 2) : 2) : 2;
+  // tap at offsets (u along a0, v along a1, w along a2) -> (dz, dy, dx)
+  auto at = [&](int u, int v, int w) -> T {
+    int d[3] = {0, 0, 0};
+    d[a0] += u;
+    if (nodd >= 2) d[a1] += v;
+    if (nodd == 3) d[2] += w;
+    return t(d[0], d[1], d[2]);
+  };
+  bool cubic = cub[a0];
+  if (nodd >= 2) cubic = cubic && cub[a1];
+  if (nodd == 3) cubic = cubic && cub[2];
+  if (cubic) {
+    if (nodd == 1) return cubic_1d(at(-1, 0, 0), at(0, 0, 0), at(1, 0, 0), at(2, 0, 0));
+    if (nodd == 2) {
+      const T si = op_add(op_add(at(0, 0, 0), at(0, 1, 0)), op_add(at(1, 0, 0), at(1, 1, 0)));
+      const T so = op_add(op_add(at(-1, -1, 0), at(-1, 2, 0)), op_add(at(2, -1, 0), at(2, 2, 0)));
+      return op_add(op_mul(si, T(0.25)), op_mul(op_sub(si, so), T(0.03125)));
+    }
+    const T si = op_add(op_add(op_add(at(0, 0, 0), at(0, 0, 1)), op_add(at(0, 1, 0), at(0, 1, 1))),
+                        op_add(op_add(at(1, 0, 0), at(1, 0, 1)), op_add(at(1, 1, 0), at(1, 1, 1))));
+    const T so =
+        op_add(op_add(op_add(at(-1, -1, -1), at(-1, -1, 2)), op_add(at(-1, 2, -1), at(-1, 2, 2))),
+               op_add(op_add(at(2, -1, -1), at(2, -1, 2)), op_add(at(2, 2, -1), at(2, 2, 2))));
+    return op_add(op_mul(si, T(0.125)), op_mul(op_sub(si, so), T(0.015625)));
+  }
+  const int r0 = rule[a0], r1 = rule[a1], r2 = rule[2];
+  if (nodd == 1) return rule_sel(r0, at(sd(0), 0, 0), at(sd(1), 0, 0), at(sd(2), 0, 0));
+  if (nodd == 2) {
+    T w1[3];
+#pragma unroll
+    for (int q1 = 0; q1 < 3; q1++)
+      w1[q1] = rule_sel(r0, at(sd(0), sd(q1), 0), at(sd(1), sd(q1), 0), at(sd(2), sd(q1), 0));
+    return rule_sel(r1, w1[0], w1[1], w1[2]);
+  }
+  T w2[3];
+#pragma unroll
+  for (int q2 = 0; q2 < 3; q2++) {
+    T w1[3];
+#pragma unroll
+    for (int q1 = 0; q1 < 3; q1++)
+      w1[q1] = rule_sel(r0, at(sd(0), sd(q1), sd(q2)), at(sd(1), sd(q1), sd(q2)),
+                        at(sd(2), sd(q1), sd(q2)));
+    w2[q2] = rule_sel(r1, w1[0], w1[1], w1[2]);
+  }
+  return rule_sel(r2, w2[0], w2[1], w2[2]);
+}
+
 template <typename T, bool DEC>
 __global__ void __launch_bounds__(256) k_level_shell(const __grid_constant__ LevelArgs a,
                                                      const __grid_constant__ ShellGeo sh) {
@@ -583,86 +663,128 @@ __global__ void __launch_bounds__(256) k_level_shell(const __grid_constant__ Lev
     for (int w = threadIdx.x; w < 7 * kHistWords; w += blockDim.x) hist[w] = 0;
     __syncthreads();
   }
-  int64_t m[3];
-  grid_extent(geo.n, geo.L, l, m);
+  int64_t m64[3];
+  grid_extent(geo.n, geo.L, l, m64);
+  const int m[3] = {(int)m64[0], (int)m64[1], (int)m64[2]};
   const T two_eb = (T)a.two_eb;
-  const T* coarse = (const T*)a.coarse;
-  const int64_t ce1 = a.chi[1] - a.clo[1], ce2 = a.chi[2] - a.clo[2];
-  const int64_t st[3] = {ce1 * ce2, ce2, 1};
+  const int ce[3] = {(int)(a.chi[0] - a.clo[0]), (int)(a.chi[1] - a.clo[1]),
+                     (int)(a.chi[2] - a.clo[2])};
+  const int cst[3] = {ce[1] * ce[2], ce[2], 1};  // coarse box strides (elements)
   const int64_t fe1 = a.fhi[1] - a.flo[1], fe2 = a.fhi[2] - a.flo[2];
   const int64_t s = level_stride(geo.L, l);
+  const int64_t xst[3] = {s * geo.n[1] * geo.n[2], s * geo.n[2], s};  // field strides
+  const int64_t fst[3] = {fe1 * fe2, fe2, 1};                        // fine box strides
   const int64_t total = sh.nA + sh.nB + sh.nC;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   const int64_t iters = cdiv(total, nth);
   for (int64_t it = 0; it < iters; it++) {
     const int64_t i = it * nth + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool cv = i < total;
-    int64_t c[3] = {0, 0, 0};
+    int c[3] = {0, 0, 0};
     if (cv) {
       const int64_t nx = sh.hi[2] - sh.lo[2], ny = sh.hi[1] - sh.lo[1];
       if (i < sh.nA) {
         const int64_t r = i / (ny * nx);
-        c[0] = sh.bv[0][r];
-        c[1] = sh.lo[1] + (i / nx) % ny;
-        c[2] = sh.lo[2] + i % nx;
+        c[0] = (int)sh.bv[0][r];
+        c[1] = (int)(sh.lo[1] + (i / nx) % ny);
+        c[2] = (int)(sh.lo[2] + i % nx);
       } else if (i < sh.nA + sh.nB) {
         const int64_t k = i - sh.nA, nbyx = sh.nb[1] * nx;
-        c[0] = sh.ilo[0] + k / nbyx;
-        c[1] = sh.bv[1][(k / nx) % sh.nb[1]];
-        c[2] = sh.lo[2] + k % nx;
+        c[0] = (int)(sh.ilo[0] + k / nbyx);
+        c[1] = (int)sh.bv[1][(k / nx) % sh.nb[1]];
+        c[2] = (int)(sh.lo[2] + k % nx);
       } else {
         const int64_t k = i - sh.nA - sh.nB, iyn = sh.ihi[1] - sh.ilo[1];
-        c[0] = sh.ilo[0] + k / (iyn * sh.nb[2]);
-        c[1] = sh.ilo[1] + (k / sh.nb[2]) % iyn;
-        c[2] = sh.bv[2][k % sh.nb[2]];
+        c[0] = (int)(sh.ilo[0] + k / (iyn * sh.nb[2]));
+        c[1] = (int)(sh.ilo[1] + (k / sh.nb[2]) % iyn);
+        c[2] = (int)sh.bv[2][k % sh.nb[2]];
       }
     }
-    const int64_t base = ((c[0] - a.clo[0]) * ce1 + (c[1] - a.clo[1])) * ce2 + (c[2] - a.clo[2]);
-    if (cv && a.fine) {
-      const int64_t g0 = 2 * c[0], g1 = 2 * c[1], g2 = 2 * c[2];
-      if (g0 >= a.flo[0] && g0 < a.fhi[0] && g1 >= a.flo[1] && g1 < a.fhi[1] && g2 >= a.flo[2] &&
-          g2 < a.fhi[2])
-        ((T*)a.fine)[((g0 - a.flo[0]) * fe1 + (g1 - a.flo[1])) * fe2 + (g2 - a.flo[2])] =
-            coarse[base];
+    // per axis: the odd point's existence, stencil and rule; clamped taps
+    ShellTaps<T> tp;
+    bool odd_in[3], cub[3];
+    int rule[3];
+    int64_t cbase = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+      const int lc = c[ax] - (int)a.clo[ax];
+      cbase += (int64_t)lc * cst[ax];
+      int* o = ax == 0 ? tp.oz : (ax == 1 ? tp.oy : tp.ox);
+#pragma unroll
+      for (int d = -1; d <= 2; d++) o[d + 1] = (min(max(lc + d, 0), ce[ax] - 1) - lc) * cst[ax];
+      const int go = 2 * c[ax] + 1;
+      odd_in[ax] = go < m[ax];
+      cub[ax] = go >= 3 && go + 3 < m[ax];
+      rule[ax] = go + 1 < m[ax] ? kMid : (go >= 3 ? kExt : kCopy);
     }
+    tp.cb = (const T*)a.coarse + cbase;
+    const int64_t g0[3] = {2 * (int64_t)c[0], 2 * (int64_t)c[1], 2 * (int64_t)c[2]};
+    bool ev_box = true;  // the even point (copied coarse value) inside the fine box
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) ev_box = ev_box && g0[ax] >= a.flo[ax] && g0[ax] < a.fhi[ax];
+    const int64_t fidx0 = ((g0[0] - a.flo[0]) * fe1 + (g0[1] - a.flo[1])) * fe2 + (g0[2] - a.flo[2]);
+    if (cv && a.fine && ev_box) ((T*)a.fine)[fidx0] = tp(0, 0, 0);
+    // the cell's brick and place in it (the same for the 7 sub-blocks)
+    const int Bc[3] = {c[0] / geo.b[0], c[1] / geo.b[1], c[2] / geo.b[2]};
+    const int rc[3] = {c[0] - Bc[0] * geo.b[0], c[1] - Bc[1] * geo.b[1], c[2] - Bc[2] * geo.b[2]};
+    const int64_t xbase = DEC ? 0 : g0[0] * xst[0] + g0[1] * xst[1] + g0[2] * xst[2];
 #pragma unroll
     for (int K = 1; K <= 7; K++) {
       const int o[3] = {(K >> 2) & 1, (K >> 1) & 1, K & 1};
-      const int64_t g[3] = {2 * c[0] + o[0], 2 * c[1] + o[1], 2 * c[2] + o[2]};
-      bool v = cv && g[0] < m[0] && g[1] < m[1] && g[2] < m[2];
-      const bool inbox = g[0] >= a.flo[0] && g[0] < a.fhi[0] && g[1] >= a.flo[1] &&
-                         g[1] < a.fhi[1] && g[2] >= a.flo[2] && g[2] < a.fhi[2];
-      if (DEC) v = v && inbox;
+      bool v = cv;
+#pragma unroll
+      for (int ax = 0; ax < 3; ax++) {
+        if (o[ax]) v = v && odd_in[ax];
+        if (DEC) {
+          const int64_t g = g0[ax] + o[ax];
+          v = v && g >= a.flo[ax] && g < a.fhi[ax];
+        }
+      }
       const int sid = 1 + 7 * (l - 2) + (K - 1);
       int sym = -1;
       if (v) {
-        const CellAddr ad = cell_addr(geo.s[sid], geo.b, geo.bvol, a.sm[K], c[0], c[1], c[2]);
-        const int64_t fidx = ((g[0] - a.flo[0]) * fe1 + (g[1] - a.flo[1])) * fe2 + (g[2] - a.flo[2]);
+        const StreamGeo& sg = geo.s[sid];
+        const SlotMap& sm = a.sm[K];
+        const int l0 = min(geo.b[0], (int)sg.e[0] - Bc[0] * geo.b[0]);
+        const int l1 = min(geo.b[1], (int)sg.e[1] - Bc[1] * geo.b[1]);
+        const int l2 = min(geo.b[2], (int)sg.e[2] - Bc[2] * geo.b[2]);
+        const int local = (rc[0] * l1 + rc[1]) * l2 + rc[2];
+        const int64_t ord = ((Bc[0] - sm.lo[0]) * sm.cnt[1] + (Bc[1] - sm.lo[1])) * sm.cnt[2] +
+                            (Bc[2] - sm.lo[2]);
+        const int64_t slot = (sm.base + ord) * geo.bvol + local;
+        const int64_t fidx = fidx0 + o[0] * fst[0] + o[1] * fst[1] + o[2] * fst[2];
         T pred;
         switch (K) {
-          case 1: pred = level_predict<1>(coarse, base, st, g, m); break;
-          case 2: pred = level_predict<2>(coarse, base, st, g, m); break;
-          case 3: pred = level_predict<3>(coarse, base, st, g, m); break;
-          case 4: pred = level_predict<4>(coarse, base, st, g, m); break;
-          case 5: pred = level_predict<5>(coarse, base, st, g, m); break;
-          case 6: pred = level_predict<6>(coarse, base, st, g, m); break;
-          default: pred = level_predict<7>(coarse, base, st, g, m); break;
+          case 1: pred = shell_predict<1>(tp, cub, rule); break;
+          case 2: pred = shell_predict<2>(tp, cub, rule); break;
+          case 3: pred = shell_predict<3>(tp, cub, rule); break;
+          case 4: pred = shell_predict<4>(tp, cub, rule); break;
+          case 5: pred = shell_predict<5>(tp, cub, rule); break;
+          case 6: pred = shell_predict<6>(tp, cub, rule); break;
+          default: pred = shell_predict<7>(tp, cub, rule); break;
         }
         if (!DEC) {
-          const T x = ((const T*)a.field)[((g[0] * s) * geo.n[1] + g[1] * s) * geo.n[2] + g[2] * s];
+          const T x = __ldg((const T*)a.field + xbase + o[0] * xst[0] + o[1] * xst[1] +
+                            o[2] * xst[2]);
           T xq;
-          sym = quantize(x, pred, q, kRadius, xq);
-          a.codes[ad.slot] = (uint16_t)sym;
+          sym = quantize_sel(x, pred, q, kRadius, xq);
+          a.codes[slot] = (uint16_t)sym;
           if (a.fine) ((T*)a.fine)[fidx] = xq;
-          if (sym == 0) atomicAdd(&a.chunk_outliers[geo.s[sid].chunk0 + ad.chunk], 1u);
+          if (sym == 0) {
+            const int64_t chunk = ((int64_t)Bc[0] * sg.nb[1] + Bc[1]) * sg.nb[2] + Bc[2];
+            atomicAdd(&a.chunk_outliers[sg.chunk0 + chunk], 1u);
+          }
         } else {
-          const int sy = a.codes[ad.slot];
-          T val;
-          if (sy != 0) {
-            val = dequantize(sy, pred, two_eb, kRadius);
-          } else if (!find_outlier(a.opos[K], (const T*)a.oval[K], a.nout[K], ad.pos, val)) {
-            val = T(0);
-            atomicOr(a.status, kStatCorrupt);
+          const int sy = a.codes[slot];
+          T val = dequantize(sy, pred, two_eb, kRadius);
+          if (sy == 0) {
+            const int64_t pos = (int64_t)Bc[0] * geo.b[0] * sg.e[1] * sg.e[2] +
+                                (int64_t)Bc[1] * geo.b[1] * l0 * sg.e[2] +
+                                (int64_t)Bc[2] * geo.b[2] * l0 * l1 + local;
+            if (!find_outlier(a.opos[K], (const T*)a.oval[K], a.nout[K], pos, val)) {
+              val = T(0);
+              atomicOr(a.status, kStatCorrupt);
+            }
           }
           ((T*)a.fine)[fidx] = val;
         }
