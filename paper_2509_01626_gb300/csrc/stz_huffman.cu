@@ -18,6 +18,12 @@
 namespace stz {
 
 // ---------------------------------------------------------------- histograms
+// Histogram of one stream from its chunk slots: a block takes kHistChunks
+// chunks at once, one 16-byte word (8 codes) of each per thread, so that all
+// its loads are in flight before the shared-memory counts; the most frequent
+// symbol (the zero-error code) is counted by ballot.
+constexpr int kHistChunks = 4;
+
 __global__ void __launch_bounds__(256) k_stream_hist(const __grid_constant__ Geo g, int sid,
                                                      const uint16_t* __restrict__ codes,
                                                      uint32_t* __restrict__ hist) {
@@ -25,12 +31,37 @@ __global__ void __launch_bounds__(256) k_stream_hist(const __grid_constant__ Geo
   for (int i = threadIdx.x; i < kAlphabet; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const StreamGeo& sg = g.s[sid];
-  for (int64_t j = blockIdx.x; j < sg.nchunks; j += gridDim.x) {
-    int64_t B[3], l[3], start;
-    chunk_brick(sg, g.b, j, B, l, &start);
-    const int64_t cnt = l[0] * l[1] * l[2];
-    const uint16_t* c = codes + (sg.chunk0 + j) * g.bvol;
-    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) atomicAdd(&h[c[i]], 1u);
+  const int lane = threadIdx.x & 31;
+  const int words = (int)(g.bvol / 8);  // 16-byte words per chunk slot
+  for (int64_t j0 = (int64_t)blockIdx.x * kHistChunks; j0 < sg.nchunks;
+       j0 += (int64_t)gridDim.x * kHistChunks) {
+    uint4 v[kHistChunks];
+    int cnt[kHistChunks];
+#pragma unroll
+    for (int u = 0; u < kHistChunks; u++) {
+      const int64_t j = j0 + u;
+      cnt[u] = 0;
+      v[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (j < sg.nchunks) {
+        int64_t B[3], l[3], start;
+        chunk_brick(sg, g.b, j, B, l, &start);
+        cnt[u] = (int)(l[0] * l[1] * l[2]);
+        if ((int)threadIdx.x < words && 8 * (int)threadIdx.x < cnt[u])
+          v[u] = __ldg((const uint4*)(codes + (sg.chunk0 + j) * g.bvol) + threadIdx.x);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kHistChunks; u++) {
+      const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+      for (int e = 0; e < 8; e++) {
+        const int sym = (int)((w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
+        const bool in = 8 * (int)threadIdx.x + e < cnt[u];
+        const unsigned bm = __ballot_sync(0xffffffffu, in && sym == kRadius);
+        if (lane == 0 && bm) atomicAdd(&h[kRadius], (uint32_t)__popc(bm));
+        if (in && sym != kRadius) atomicAdd(&h[sym], 1u);
+      }
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kAlphabet; i += blockDim.x)
@@ -40,7 +71,9 @@ __global__ void __launch_bounds__(256) k_stream_hist(const __grid_constant__ Geo
 int launch_stream_hist(const Geo& g, int sid, const uint16_t* codes, uint32_t* hist,
                        cudaStream_t s) {
   if (g.s[sid].nchunks == 0) return STZ_OK;
-  int blocks = (int)imin(g.s[sid].nchunks, 304);
+  // one thread per 16-byte word of a chunk slot
+  if (g.bvol % 8 != 0 || g.bvol > 8 * 256) return STZ_ERR_ARG;
+  const int blocks = (int)imin(cdiv(g.s[sid].nchunks, kHistChunks), 304);
   ProfScope ps_("k_stream_hist", s);
   k_stream_hist<<<blocks, 256, 0, s>>>(g, sid, codes, hist);
   return cuda_ok(cudaGetLastError());
