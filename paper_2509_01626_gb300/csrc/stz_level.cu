@@ -225,7 +225,11 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const __grid_constant__
 // cells with 1 <= c <= M-3 on every axis are handled here (all stencils cubic,
 // all points present); the others belong to the shell kernel below.
 constexpr int kFBZ = 8, kFBY = 16, kFBX = 16;
-constexpr int kFEY = kFBY + 3, kFEX = kFBX + 3, kFEZY = kFEY * kFEX;
+// A tile row holds coarse x = c0x - 4 .. c0x + 19 (kFEX = 24 elements; the
+// stencils read c0x - 1 .. c0x + 17), so that rows start on 16-byte
+// boundaries when the coarse box does and copy as 16-byte chunks.
+constexpr int kFEY = kFBY + 3, kFEX = kFBX + 8, kFEZY = kFEY * kFEX;
+constexpr int kFX0 = 3;  // tile x index of coarse x = c0x - 1
 
 template <typename T>
 __device__ __forceinline__ void load_plane(T (&w)[12], const T* __restrict__ t, int b) {
@@ -330,25 +334,46 @@ __device__ __forceinline__ void tile_info(const LevelArgs& a, int64_t tt, TileIn
   }
 }
 
-// Issue the copies of tile tt's coarse grid (with halo) into `tile`.
-template <typename T>
-__device__ __forceinline__ void tile_prefetch(const LevelArgs& a, int64_t tt, T* tile) {
+// Issue the copies of tile tt's coarse grid (with halo) into `tile`.  VEC:
+// the coarse box's base, row pitch and x origin are 16-byte aligned, so every
+// 16-byte chunk of a tile row lies wholly inside or wholly outside the box
+// (zero-filled); otherwise element by element.
+template <typename T, bool VEC>
+__device__ __noinline__ void tile_prefetch(const LevelArgs& a, int64_t tt, T* tile) {
   // tile counts and brick coordinates fit in 32 bits (cells per axis < 2^30)
   const int t32 = (int)tt, n2 = (int)a.tcnt[2], n12 = (int)a.tcnt[1] * n2;
   const int64_t Tb[3] = {a.tlo[0] + t32 / n12, a.tlo[1] + (t32 % n12) / n2, a.tlo[2] + t32 % n2};
-  const int c0[3] = {(int)Tb[0] * kFBZ - 1, (int)Tb[1] * kFBY - 1, (int)Tb[2] * kFBX - 1};
   const T* coarse = (const T*)a.coarse;
   const int clo0 = (int)a.clo[0], clo1 = (int)a.clo[1], clo2 = (int)a.clo[2];
-  const int chi0 = (int)a.chi[0], chi1 = (int)a.chi[1], chi2 = (int)a.chi[2];
-  const int64_t ce1 = a.chi[1] - a.clo[1], ce2 = a.chi[2] - a.clo[2];
-  constexpr int tvol = (kFBZ + 3) * kFEZY;
-  for (int i = threadIdx.x; i < tvol; i += blockDim.x) {
-    const int iz = i / kFEZY, iy = (i / kFEX) % kFEY, ix = i % kFEX;
-    const int cz = c0[0] + iz, cy = c0[1] + iy, cx = c0[2] + ix;
-    const bool in = cz >= clo0 && cz < chi0 && cy >= clo1 && cy < chi1 && cx >= clo2 && cx < chi2;
-    const T* src = in ? coarse + ((int64_t)(cz - clo0) * ce1 + (cy - clo1)) * ce2 + (cx - clo2)
-                      : coarse;
-    cp_async<sizeof(T)>(tile + i, src, in);
+  const int ce0 = (int)(a.chi[0] - a.clo[0]), ce1 = (int)(a.chi[1] - a.clo[1]),
+            ce2 = (int)(a.chi[2] - a.clo[2]);
+  // local coarse coordinates of tile element (0, 0, 0)
+  const int z0 = (int)Tb[0] * kFBZ - 1 - clo0, y0 = (int)Tb[1] * kFBY - 1 - clo1,
+            x0 = (int)Tb[2] * kFBX - 1 - kFX0 - clo2;
+  if (VEC) {
+    constexpr int epc = 16 / sizeof(T);  // elements per chunk
+    constexpr int cpr = kFEX / epc;      // chunks per row
+    constexpr int nchunk = (kFBZ + 3) * kFEY * cpr;
+    for (int q = threadIdx.x; q < nchunk; q += blockDim.x) {
+      const int row = q / cpr, j = q - row * cpr;
+      const int iz = row / kFEY, iy = row - iz * kFEY;
+      const int cz = z0 + iz, cy = y0 + iy, cx = x0 + j * epc;
+      const bool in = (unsigned)cz < (unsigned)ce0 && (unsigned)cy < (unsigned)ce1 &&
+                      (unsigned)cx < (unsigned)ce2;
+      const T* src = in ? coarse + ((int64_t)cz * ce1 + cy) * ce2 + cx : coarse;
+      cp_async<16>(tile + row * kFEX + j * epc, src, in);
+    }
+  } else {
+    constexpr int tvol = (kFBZ + 3) * kFEY * (kFBX + 3);
+    for (int i = threadIdx.x; i < tvol; i += blockDim.x) {
+      const int row = i / (kFBX + 3), ix = i - row * (kFBX + 3);
+      const int iz = row / kFEY, iy = row - iz * kFEY;
+      const int cz = z0 + iz, cy = y0 + iy, cx = x0 + kFX0 + ix;
+      const bool in = (unsigned)cz < (unsigned)ce0 && (unsigned)cy < (unsigned)ce1 &&
+                      (unsigned)cx < (unsigned)ce2;
+      const T* src = in ? coarse + ((int64_t)cz * ce1 + cy) * ce2 + cx : coarse;
+      cp_async<sizeof(T)>(tile + row * kFEX + kFX0 + ix, src, in);
+    }
   }
   cp_async_commit();
 }
@@ -371,7 +396,7 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
   const int fhi0 = (int)a.fhi[0], fhi1 = (int)a.fhi[1], fhi2 = (int)a.fhi[2];
   const bool fy0 = 2 * cy >= flo1 && 2 * cy < fhi1, fy1 = 2 * cy + 1 >= flo1 && 2 * cy + 1 < fhi1;
   const bool fx0 = 2 * cx >= flo2 && 2 * cx < fhi2, fx1 = 2 * cx + 1 >= flo2 && 2 * cx + 1 < fhi2;
-  const int tb = (kFEY + ly + 1) * kFEX + (lx + 1);
+  const int tb = (kFEY + ly + 1) * kFEX + (lx + 1 + kFX0);
   uint16_t* cp[7];
   int cstep[7];
 #pragma unroll
@@ -519,12 +544,19 @@ __global__ void __launch_bounds__(kLevelThreads, 2) k_level_fast(const __grid_co
   const int xdz = (int)(s * geo.n[1] * geo.n[2]), xdy = (int)(s * geo.n[2]), xdx = (int)s;
   const int fe2 = (int)(a.fhi[2] - a.flo[2]);
   const int fdz = (int)((a.fhi[1] - a.flo[1]) * fe2);
+  constexpr int epc = 16 / sizeof(T);
+  const bool vec = ((uintptr_t)a.coarse & 15) == 0 && (a.chi[2] - a.clo[2]) % epc == 0 &&
+                   a.clo[2] % epc == 0;
+  auto prefetch = [&](int64_t t, T* tile) {
+    if (vec) tile_prefetch<T, true>(a, t, tile);
+    else tile_prefetch<T, false>(a, t, tile);
+  };
   int since_flush = 0;
   int64_t tt = blockIdx.x;
   int b = 0;
   if (tt < ntiles) {
     tile_info(a, tt, s_ti[0]);
-    tile_prefetch(a, tt, tiles[0]);
+    prefetch(tt, tiles[0]);
   }
   for (; tt < ntiles; tt += gridDim.x, b ^= 1) {
     cp_async_wait_all();
@@ -532,7 +564,7 @@ __global__ void __launch_bounds__(kLevelThreads, 2) k_level_fast(const __grid_co
     const int64_t nt = tt + gridDim.x;
     if (nt < ntiles) {
       tile_info(a, nt, s_ti[b ^ 1]);
-      tile_prefetch(a, nt, tiles[b ^ 1]);
+      prefetch(nt, tiles[b ^ 1]);
     }
     const TileInfo& ti = s_ti[b];
     bool full = true;
