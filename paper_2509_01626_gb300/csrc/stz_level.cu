@@ -378,11 +378,18 @@ __device__ __noinline__ void tile_prefetch(const LevelArgs& a, int64_t tt, T* ti
   cp_async_commit();
 }
 
+// Two consecutive values as one 8- or 16-byte access.
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
 // One tile of the fast path.  FULL: all 7 sub-block bricks of the tile are
 // whole, so a cell has the same local code index lz*256 + tid in every stream.
 // The 7 global loads of a cell (x when compressing, codes when decoding) are
-// issued one cell ahead of their use.
-template <typename T, bool DEC, bool FULL>
+// issued one cell ahead of their use.  PAIR: the fine box and (at stride 1)
+// the field have even, aligned rows, so the x-neighbour points of a cell
+// (ox = 0, 1) are read and written as pairs.
+template <typename T, bool DEC, bool FULL, bool PAIR>
 __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restrict__ tile,
                                           const TileInfo& ti, const int M[3], const QConst<T>& q,
                                           T two_eb, uint32_t* hist, int xdz, int xdy, int xdx,
@@ -421,15 +428,56 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
     const int gz = 2 * cz + oz;
     return interior && gz >= flo0 && gz < fhi0 && (oy ? fy1 : fy0) && (ox ? fx1 : fx0);
   };
+  using P2 = typename Pair2<T>::type;
+  const bool xpair = PAIR && !DEC && xdx == 1;
+  // the 7 field values of cell lz at x pointer p (compress; one "on" for all)
+  auto load_x = [&](const T* p, bool on, T (&dst)[7]) {
+    if (xpair) {
+      dst[0] = on ? p[1] : T(0);  // K = 1; the even point is the coarse copy
+      const P2 zero = {T(0), T(0)};
+      const P2 v2 = on ? *(const P2*)(p + xdy) : zero;
+      const P2 v4 = on ? *(const P2*)(p + xdz) : zero;
+      const P2 v6 = on ? *(const P2*)(p + xdz + xdy) : zero;
+      dst[1] = v2.x;
+      dst[2] = v2.y;
+      dst[3] = v4.x;
+      dst[4] = v4.y;
+      dst[5] = v6.x;
+      dst[6] = v6.y;
+    } else {
+#pragma unroll
+      for (int K = 1; K <= 7; K++) {
+        const int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
+        dst[K - 1] = on ? p[oz * xdz + oy * xdy + ox * xdx] : T(0);
+      }
+    }
+  };
+  // the copied coarse value (index 0) and the 7 points of a cell, stored to
+  // the fine box where on; x-neighbour pairs as one access when PAIR
+  auto store8 = [&](const T (&v)[8], const bool (&o)[8]) {
+#pragma unroll
+    for (int pr = 0; pr < 4; pr++) {
+      T* dst = fp + (pr >> 1) * fdz + (pr & 1) * fe2;
+      const bool a0 = o[2 * pr], a1 = o[2 * pr + 1];
+      if (PAIR && a0 && a1) {
+        P2 w;
+        w.x = v[2 * pr];
+        w.y = v[2 * pr + 1];
+        *(P2*)dst = w;
+      } else {
+        if (a0) dst[0] = v[2 * pr];
+        if (a1) dst[1] = v[2 * pr + 1];
+      }
+    }
+  };
   // loads of cell 0
   T xv[7];
   int cv[7];
+  if (!DEC) load_x(xp, cell_on(0, 1), xv);
 #pragma unroll
   for (int K = 1; K <= 7; K++) {
-    const int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
     const bool on = cell_on(0, K);
-    if (!DEC) xv[K - 1] = on ? xp[oz * xdz + oy * xdy + ox * xdx] : T(0);
-    else cv[K - 1] = on ? (int)*cp[K - 1] : 1;
+    if (DEC) cv[K - 1] = on ? (int)*cp[K - 1] : 1;
   }
   T w0[12], w1[12], w2[12], w3[12];
   load_plane(w0, tile, tb - kFEZY);
@@ -445,16 +493,15 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
     T xn[7];
     int cn[7];
     const bool more = lz + 1 < kFBZ;
+    if (!DEC) load_x(xp + 2 * xdz, more && cell_on(lz + 1, 1), xn);
 #pragma unroll
     for (int K = 1; K <= 7; K++) {
-      const int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
       const bool on = more && cell_on(lz + 1, K);
-      if (!DEC) xn[K - 1] = on ? xp[2 * xdz + oz * xdz + oy * xdy + ox * xdx] : T(0);
-      else cn[K - 1] = on ? (int)*(cp[K - 1] + cstep[K - 1]) : 1;
+      if (DEC) cn[K - 1] = on ? (int)*(cp[K - 1] + cstep[K - 1]) : 1;
     }
     T p[7];
     cell_predict(w0, w1, w2, w3, p);
-    if (interior && fp && fz0 && fy0 && fx0) fp[0] = w1[1];  // the coarse point itself
+    const bool copy_on = interior && fz0 && fy0 && fx0;  // the coarse point itself
     // in phases over the cell's 7 points: the arithmetic of all 7 first (7
     // independent chains to interleave), then the stores, then the counts
     bool on[7];
@@ -467,14 +514,17 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
       for (int K = 0; K < 7; K++) sym[K] = quantize_sel(xv[K], p[K], q, kRadius, xq[K]);
 #pragma unroll
       for (int K = 1; K <= 7; K++) {
-        const int fo = ((K >> 2) & 1) * fdz + ((K >> 1) & 1) * fe2 + (K & 1);
         if (!on[K - 1]) {
           sym[K - 1] = -1;
           continue;
         }
         *cp[K - 1] = (uint16_t)sym[K - 1];
-        if (fp) fp[fo] = xq[K - 1];
         if (sym[K - 1] == 0) atomicAdd(&a.chunk_outliers[ti.chunk[K]], 1u);
+      }
+      if (fp) {
+        const T v8[8] = {w1[1], xq[0], xq[1], xq[2], xq[3], xq[4], xq[5], xq[6]};
+        const bool o8[8] = {copy_on, on[0], on[1], on[2], on[3], on[4], on[5], on[6]};
+        store8(v8, o8);
       }
 #pragma unroll
       for (int K = 1; K <= 7; K++) {
@@ -490,8 +540,7 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
       for (int K = 0; K < 7; K++) val[K] = dequantize(cv[K], p[K], two_eb, kRadius);
 #pragma unroll
       for (int K = 1; K <= 7; K++) {
-        if (!on[K - 1]) continue;
-        if (cv[K - 1] == 0) {  // outlier: its value from the list
+        if (on[K - 1] && cv[K - 1] == 0) {  // outlier: its value from the list
           const int64_t local = cp[K - 1] - (a.codes + ti.slot[K]);
           if (!find_outlier(a.opos[K], (const T*)a.oval[K], a.nout[K], ti.pos[K] + local,
                             val[K - 1])) {
@@ -499,8 +548,10 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
             atomicOr(a.status, kStatCorrupt);
           }
         }
-        fp[((K >> 2) & 1) * fdz + ((K >> 1) & 1) * fe2 + (K & 1)] = val[K - 1];
       }
+      const T v8[8] = {w1[1], val[0], val[1], val[2], val[3], val[4], val[5], val[6]};
+      const bool o8[8] = {copy_on, on[0], on[1], on[2], on[3], on[4], on[5], on[6]};
+      store8(v8, o8);
     }
     if (!DEC) xp += 2 * xdz;
     if (fp) fp += 2 * fdz;
@@ -519,7 +570,7 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
   }
 }
 
-template <typename T, bool DEC>
+template <typename T, bool DEC, bool PAIR>
 __global__ void __launch_bounds__(kLevelThreads, 2) k_level_fast(const __grid_constant__ LevelArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileInfo s_ti[2];
@@ -572,9 +623,10 @@ __global__ void __launch_bounds__(kLevelThreads, 2) k_level_fast(const __grid_co
     for (int K = 1; K <= 7; K++)
       full = full && ti.l[K][0] == kFBZ && ti.l[K][1] == kFBY && ti.l[K][2] == kFBX;
     if (full)
-      fast_tile<T, DEC, true>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2, fdz);
+      fast_tile<T, DEC, true, PAIR>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2, fdz);
     else
-      fast_tile<T, DEC, false>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2, fdz);
+      fast_tile<T, DEC, false, PAIR>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2,
+                                     fdz);
     if (!DEC && ++since_flush == kFlushTiles) {
       __syncthreads();
       flush_hist<T>(hist, a.hist, l);
@@ -870,7 +922,16 @@ static int run_level_fast(const LevelArgs& a, const int64_t M[3], double bytes, 
   if (M[0] < 4 || M[1] < 4 || M[2] < 4) return STZ_OK;
   size_t smem = 2 * (((size_t)(kFBZ + 3) * kFEZY * sizeof(T) + 15) & ~(size_t)15);
   if (!DEC) smem += sizeof(uint32_t) * 7 * kHistWords;
-  auto kern = k_level_fast<T, DEC>;
+  // x-neighbour pairs as one access: the fine box's rows (and, reading the
+  // field at stride 1, the field's rows) even and 2-element aligned
+  const uintptr_t a2 = 2 * sizeof(T);
+  bool pair = true;
+  if (a.fine)
+    pair = pair && (uintptr_t)a.fine % a2 == 0 && (a.fhi[2] - a.flo[2]) % 2 == 0 &&
+           a.flo[2] % 2 == 0;
+  if (!DEC && level_stride(a.geo.L, a.level) == 1)
+    pair = pair && (uintptr_t)a.field % a2 == 0 && a.geo.n[2] % 2 == 0;
+  auto kern = pair ? k_level_fast<T, DEC, true> : k_level_fast<T, DEC, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return STZ_ERR_CUDA;
