@@ -291,9 +291,11 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the same calls, host buffers, copies timed.  The
     # copies run on two copy streams (one per direction) beside the compute:
-    # step i's outputs go to the host while its later decodes run, and step
-    # i+2's field is uploaded while step i decodes (three field buffers, two
-    # sets of outputs).
+    # step i's outputs go to the host while step i+1 computes, and step i+2's
+    # field is uploaded while step i decodes (three field buffers, two sets of
+    # outputs).  Copies of one direction queue on one copy engine, so step
+    # i's output copies are issued after step i+1's container round trip,
+    # which the compute waits for.
     # Every copy of every timed step lies inside the timed region.
     e2e = None
     if not args.no_e2e:
@@ -325,12 +327,23 @@ def run_ours(args, rank, world, local_rank):
                 d_field[f % nf].copy_(h_field, non_blocking=True)
                 up_ev[f % nf].record(up)
 
-        def to_host(dst, src):
+        pending = []  # the previous step's output copies: (ready event, dst, src), set
+
+        def done_on(st):
             ev = torch.cuda.Event()
-            ev.record(cstream)
-            down.wait_event(ev)
-            with torch.cuda.stream(down):
-                dst.copy_(src, non_blocking=True)
+            ev.record(st)
+            return ev
+
+        def flush():
+            # issue the previous step's output copies on the download stream
+            if not pending:
+                return
+            items, ob = pending.pop()
+            for ev, dst, src in items:
+                down.wait_event(ev)
+                with torch.cuda.stream(down):
+                    dst.copy_(src, non_blocking=True)
+            out_free[ob].record(down)
 
         def e2e_step(i, n):
             b = i & 1
@@ -340,30 +353,33 @@ def run_ours(args, rank, world, local_rank):
             with torch.cuda.stream(cstream):
                 h_comp.copy_(c, non_blocking=True)
                 d_comp.copy_(h_comp, non_blocking=True)
+            flush()
             cstream.wait_event(out_free[b])
+            items = []
             y = stz.decompress_full(d_comp, out=fulls[b], workspace=ws, meta=meta, stream=cstream)
+            items.append((done_on(cstream), h_full, y))
             # the field two steps ahead: issued once this step's small upload
             # has gone (copies of one direction queue on one engine)
             if i + 2 < n:
                 upload(i + 2)
-            to_host(h_full, y)
             for k in (1, 2):
                 pk = stz.decompress_progressive(d_comp, k, out=pouts[b][k], workspace=ws,
                                                 meta=meta, stream=cstream)
-                to_host(h_p[k][: pk.numel()], pk.reshape(-1))
+                items.append((done_on(cstream), h_p[k][: pk.numel()], pk.reshape(-1)))
             bx = stz.decompress_region(d_comp, blo, bhi, 3, out=boxes[b], workspace=ws,
                                        meta=meta, stream=cstream)
-            to_host(h_box[: bx.numel()], bx.reshape(-1))
+            items.append((done_on(cstream), h_box[: bx.numel()], bx.reshape(-1)))
             sl = stz.decompress_region(d_comp, slo, shi, 3, out=slabs[b], workspace=ws,
                                        meta=meta, stream=cstream)
-            to_host(h_slab[: sl.numel()], sl.reshape(-1))
-            out_free[b].record(down)
+            items.append((done_on(cstream), h_slab[: sl.numel()], sl.reshape(-1)))
+            pending.append((items, b))
 
         def run(n):
             for f in range(min(2, n)):
                 upload(f)
             for i in range(n):
                 e2e_step(i, n)
+            flush()
             for cs in (up, down):
                 done = torch.cuda.Event()
                 done.record(cs)
