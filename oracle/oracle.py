@@ -120,7 +120,7 @@ def _dims3(shape):
 
 
 def make_params(shape, dtype, eb, mode="rel", levels=3, radius=1024, max_code_len=12,
-                brick=None, nsub=4) -> _Params:
+                brick=None, nsub=8) -> _Params:
     ndim, d3 = _dims3(shape)
     if brick is None:
         brick = BRICK_3D if ndim == 3 else BRICK_2D

@@ -27,7 +27,7 @@ constexpr int kLevels = 3;              // L used by stz_compress
 constexpr int kRadius = 1024;           // quantization radius R
 constexpr int kAlphabet = 2 * kRadius;  // symbols 0 (outlier) .. 2R-1
 constexpr int kMaxCodeLen = 12;         // Huffman length limit = decode table index bits
-constexpr int kNSub = 4;                // sub-chunks per chunk (independent decode chains)
+constexpr int kNSub = 8;                // sub-chunks per chunk (independent decode chains)
 constexpr int kDecThreads = 256;        // threads per block of the chunk decoder
 constexpr int kLutSize = 1 << kMaxCodeLen;
 constexpr int kHeaderBytes = 256;

@@ -892,27 +892,29 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-constexpr int kStageWords = 10240;                              // 40 KiB per block
+// 24 KiB of payload per block: with 8 runs per chunk (32 chunks per block)
+// 768 bytes per chunk, 3 bits per symbol, at once; 6 blocks share an SM
+constexpr int kStageWords = 6144;
 constexpr int kMaxChunkWords = (4096 * kMaxCodeLen + 31) / 32;  // bricks hold <= 4096 cells
 static_assert(kMaxChunkWords + 2 <= kStageWords, "a chunk must fit the stage");
 constexpr size_t kDecSmem = sizeof(uint32_t) * kStageWords + sizeof(uint16_t) * kLutSize +
-                            sizeof(unsigned long long) * kDecThreads +
+                            sizeof(uint32_t) * kDecThreads +
                             sizeof(uint32_t) * (kDecThreads + 1) + sizeof(uint32_t) * kDecThreads +
                             sizeof(int) * kDecThreads;
 static_assert((sizeof(uint32_t) * kStageWords) % 16 == 0 &&
                   (sizeof(uint32_t) * kStageWords + sizeof(uint16_t) * kLutSize) % 8 == 0,
               "shared arrays of the chunk decoder must stay aligned");
 
-__global__ void __launch_bounds__(kDecThreads) k_decode_chunks(
+__global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
     const __grid_constant__ Geo g, const __grid_constant__ DecTables tb,
     const uint16_t* __restrict__ lut, uint16_t* __restrict__ codes,
     uint32_t* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  // arrays in order of alignment: 16-byte-loaded table, then 8-, then 4-byte
+  // arrays in order of alignment: the 16-byte-loaded table first, then 4-byte
   uint32_t* stage = (uint32_t*)dsm;
   uint16_t* t = (uint16_t*)(stage + kStageWords);
-  unsigned long long* cw0 = (unsigned long long*)(t + kLutSize);  // chunk's first word
-  uint32_t* S = (uint32_t*)(cw0 + kDecThreads);                   // padded-size prefix sums
+  uint32_t* cw0 = (uint32_t*)(t + kLutSize);     // chunk's first word in the stream payload
+  uint32_t* S = cw0 + kDecThreads;               // padded-size prefix sums
   uint32_t* cjl = S + kDecThreads + 1;                            // chunk index in stream
   int* ccnt = (int*)(cjl + kDecThreads);                          // symbols; -1: bad chunk
   __shared__ uint32_t wsum[8];

@@ -96,7 +96,7 @@ def test_header_layout(ora):
     dims = struct.unpack_from("<3q", b, 32)
     eb, eb_abs, vmin, vmax = struct.unpack_from("<4d", b, 56)
     (total,) = struct.unpack_from("<Q", b, 88)
-    assert (version, dtype, ndim, levels, mode, maxlen, nsub) == (1, 0, 3, 3, 1, 12, 4)
+    assert (version, dtype, ndim, levels, mode, maxlen, nsub) == (1, 0, 3, 3, 1, 12, 8)
     assert radius == 1024 and bricks == (8, 16, 16) and ns == 15 and dims == (9, 10, 11)
     assert total == len(b)
     assert vmin == float(x.min()) and vmax == float(x.max())
