@@ -479,6 +479,11 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
     const bool on = cell_on(0, K);
     if (DEC) cv[K - 1] = on ? (int)*cp[K - 1] : 1;
   }
+  // counts of the zero-error symbol R per stream, kept in registers over the
+  // tile and added to the shared histogram once per warp at its end
+  uint32_t nR[7];
+#pragma unroll
+  for (int K = 0; K < 7; K++) nR[K] = 0;
   T w0[12], w1[12], w2[12], w3[12];
   load_plane(w0, tile, tb - kFEZY);
   load_plane(w1, tile, tb);
@@ -528,11 +533,10 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
       }
 #pragma unroll
       for (int K = 1; K <= 7; K++) {
-        const unsigned bm = __ballot_sync(0xffffffffu, sym[K - 1] == kRadius);
-        uint32_t* h = hist + (K - 1) * kHistWords;
-        if (lane == 0 && bm) atomicAdd(&h[kRadius >> 1], (uint32_t)__popc(bm));
         const int sk = sym[K - 1];
-        if (sk >= 0 && sk != kRadius) atomicAdd(&h[sk >> 1], 1u << ((sk & 1) * 16));
+        nR[K - 1] += sk == kRadius;
+        if (sk >= 0 && sk != kRadius)
+          atomicAdd(&hist[(K - 1) * kHistWords + (sk >> 1)], 1u << ((sk & 1) * 16));
       }
     } else {
       T val[7];
@@ -566,6 +570,14 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
       w0[j] = w1[j];
       w1[j] = w2[j];
       w2[j] = w3[j];
+    }
+  }
+  if (!DEC) {
+    static_assert((kRadius & 1) == 0, "R counts in the low half of its packed word");
+#pragma unroll
+    for (int K = 0; K < 7; K++) {
+      const uint32_t n = __reduce_add_sync(0xffffffffu, nR[K]);
+      if (lane == 0 && n) atomicAdd(&hist[K * kHistWords + (kRadius >> 1)], n);
     }
   }
 }
