@@ -724,25 +724,27 @@ __device__ __forceinline__ T shell_predict(const ShellTaps<T>& t, const bool cub
     return op_add(op_mul(si, T(0.125)), op_mul(op_sub(si, so), T(0.015625)));
   }
   const int r0 = rule[a0], r1 = rule[a1], r2 = rule[2];
-  if (nodd == 1) return rule_sel(r0, at(sd(0), 0, 0), at(sd(1), 0, 0), at(sd(2), 0, 0));
-  if (nodd == 2) {
+  if constexpr (nodd == 1) {
+    return rule_sel(r0, at(sd(0), 0, 0), at(sd(1), 0, 0), at(sd(2), 0, 0));
+  } else if constexpr (nodd == 2) {
     T w1[3];
 #pragma unroll
     for (int q1 = 0; q1 < 3; q1++)
       w1[q1] = rule_sel(r0, at(sd(0), sd(q1), 0), at(sd(1), sd(q1), 0), at(sd(2), sd(q1), 0));
     return rule_sel(r1, w1[0], w1[1], w1[2]);
-  }
-  T w2[3];
+  } else {
+    T w2[3];
 #pragma unroll
-  for (int q2 = 0; q2 < 3; q2++) {
-    T w1[3];
+    for (int q2 = 0; q2 < 3; q2++) {
+      T w1[3];
 #pragma unroll
-    for (int q1 = 0; q1 < 3; q1++)
-      w1[q1] = rule_sel(r0, at(sd(0), sd(q1), sd(q2)), at(sd(1), sd(q1), sd(q2)),
-                        at(sd(2), sd(q1), sd(q2)));
-    w2[q2] = rule_sel(r1, w1[0], w1[1], w1[2]);
+      for (int q1 = 0; q1 < 3; q1++)
+        w1[q1] = rule_sel(r0, at(sd(0), sd(q1), sd(q2)), at(sd(1), sd(q1), sd(q2)),
+                          at(sd(2), sd(q1), sd(q2)));
+      w2[q2] = rule_sel(r1, w1[0], w1[1], w1[2]);
+    }
+    return rule_sel(r2, w2[0], w2[1], w2[2]);
   }
-  return rule_sel(r2, w2[0], w2[1], w2[2]);
 }
 
 template <typename T, bool DEC>
@@ -773,6 +775,7 @@ __global__ void __launch_bounds__(256) k_level_shell(const __grid_constant__ Lev
   const int64_t total = sh.nA + sh.nB + sh.nC;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   const int64_t iters = cdiv(total, nth);
+  uint32_t nR[7] = {0, 0, 0, 0, 0, 0, 0};  // zero-error symbols per stream, added at the end
   for (int64_t it = 0; it < iters; it++) {
     const int64_t i = it * nth + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool cv = i < total;
@@ -886,14 +889,18 @@ __global__ void __launch_bounds__(256) k_level_shell(const __grid_constant__ Lev
         }
       }
       if (!DEC) {
-        const unsigned bm = __ballot_sync(0xffffffffu, sym == kRadius);
-        uint32_t* h = hist + (K - 1) * kHistWords;
-        if (lane == 0 && bm) atomicAdd(&h[kRadius >> 1], (uint32_t)__popc(bm));
-        if (sym >= 0 && sym != kRadius) atomicAdd(&h[sym >> 1], 1u << ((sym & 1) * 16));
+        nR[K - 1] += sym == kRadius;
+        if (sym >= 0 && sym != kRadius)
+          atomicAdd(&hist[(K - 1) * kHistWords + (sym >> 1)], 1u << ((sym & 1) * 16));
       }
     }
   }
   if (!DEC) {
+#pragma unroll
+    for (int K = 0; K < 7; K++) {
+      const uint32_t n = __reduce_add_sync(0xffffffffu, nR[K]);
+      if (lane == 0 && n) atomicAdd(&hist[K * kHistWords + (kRadius >> 1)], n);
+    }
     __syncthreads();
     flush_hist<T>(hist, a.hist, l);
   }
