@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(1024) k_base_coarse(const __grid_constant__ Ba
   const int nsg = pl.sm[0] * pl.sm[1] * pl.sm[2];
   T* sg = (T*)smem_raw;
   uint16_t* sc = (uint16_t*)(smem_raw + sizeof(T) * nsg);
-  coarse_phase<T, DEC>(a, pl, sg, sc, m, s1, q);
+  if (pl.nsmall > 0) coarse_phase<T, DEC>(a, pl, sg, sc, m, s1, q);
   // small remaining passes (a region's dependencies) in this block: global
   // writes are visible to the block after the barrier
   for (int k = pl.nsmall; k < pl.nlocal; k++) {
@@ -456,7 +456,18 @@ static int run_coop(const BaseArgs& a, cudaStream_t s, bool allow_coop = true) {
     for (int k = pl.nsmall; k < pl.npass; k++) rest += pl.p[k].total;
     if (rest <= kLocalPoints) pl.nlocal = pl.npass;
   }
-  const size_t nsg = (size_t)pl.sm[0] * pl.sm[1] * pl.sm[2];
+  // a region whose passes are small altogether runs them all on the level-1
+  // grid in the single block: no subgrid is gathered and written back
+  if (a.region) {
+    int64_t all = 0;
+    for (int k = 0; k < pl.npass; k++) all += pl.p[k].total;
+    if (all <= kLocalPoints) {
+      pl.nsmall = 0;
+      pl.nlocal = pl.npass;
+    }
+  }
+  const size_t nsg =
+      pl.nsmall > 0 ? (size_t)pl.sm[0] * pl.sm[1] * pl.sm[2] : 0;  // no coarse phase: none
   const size_t smem = (sizeof(T) + sizeof(uint16_t)) * nsg;
   {
     auto ck = k_base_coarse<T, DEC>;
