@@ -419,11 +419,16 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
                                     (int64_t)fe2 +
                        (2 * cx - flo2)
                  : nullptr;
+  // the tile's fine points all inside the fine box (every tile of a full
+  // decode): its cells need no per-point box test
+  const bool tile_in = !DEC || (2 * c0z >= flo0 && 2 * (c0z + kFBZ) <= fhi0 &&
+                                2 * ti.c0[1] >= flo1 && 2 * (ti.c0[1] + kFBY) <= fhi1 &&
+                                2 * ti.c0[2] >= flo2 && 2 * (ti.c0[2] + kFBX) <= fhi2);
   // cell lz is "on" for sub-block K if interior (and its point inside the box)
   auto cell_on = [&](int lz, int K) -> bool {
     const int cz = c0z + lz;
     const bool interior = in_yx && (unsigned)(cz - 1) <= (unsigned)(M[0] - 4);
-    if (!DEC) return interior;
+    if (tile_in) return interior;
     const int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
     const int gz = 2 * cz + oz;
     return interior && gz >= flo0 && gz < fhi0 && (oy ? fy1 : fy0) && (ox ? fx1 : fx0);
@@ -506,7 +511,7 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
     }
     T p[7];
     cell_predict(w0, w1, w2, w3, p);
-    const bool copy_on = interior && fz0 && fy0 && fx0;  // the coarse point itself
+    const bool copy_on = interior && (tile_in || (fz0 && fy0 && fx0));  // the coarse point
     // in phases over the cell's 7 points: the arithmetic of all 7 first (7
     // independent chains to interleave), then the stores, then the counts
     bool on[7];

@@ -60,6 +60,10 @@ CASES = {
     "abs_64": (lambda: synth.sinusoids((64, 64, 64), 11), 5e-3, "abs"),
     "const_20": (lambda: np.full((20, 20, 20), 3.25, dtype=np.float32), 1e-3, "rel"),
     "nonfinite": (_nonfinite, 1e-3, "rel"),
+    # interior-kernel variants: even rows (paired accesses) over coarse rows that are
+    # not a multiple of 16 bytes (element-wise tile copies), and the reverse
+    "pair_rows_24x20x108": (lambda: synth.sinusoids((24, 20, 108), 12), 1e-3, "rel"),
+    "odd_rows_20x24x63": (lambda: synth.sinusoids((20, 24, 63), 13), 1e-3, "rel"),
 }
 
 _cache = {}
@@ -128,7 +132,8 @@ def test_decode_matches_oracle(stzg, ora, name):
 
 
 @pytest.mark.parametrize("name", ["sin128_rel1e-3", "ragged_37x29x41", "2d_180x360",
-                                  "f64_40x33x27", "nonfinite", "ones_axis_1x40x1"])
+                                  "f64_40x33x27", "nonfinite", "ones_axis_1x40x1",
+                                  "pair_rows_24x20x108"])
 def test_regions_match_oracle(stzg, ora, name):
     x, eb, mode, ref = case(name, ora)
     comp = torch.from_numpy(ref).cuda()
@@ -141,6 +146,22 @@ def test_regions_match_oracle(stzg, ora, name):
         s = 1 << (3 - level)
         sl = tuple(slice(-(-a // s) * s, b, s) for a, b in zip(lo, hi))
         assert np.array_equal(_bits(r), _bits(np.ascontiguousarray(full[sl]))), (lo, hi, level)
+
+
+@pytest.mark.parametrize("nsub", [1, 2, 4, 8])
+def test_sub_chunk_counts_decode(stzg, ora, nsub):
+    """Containers with every sub-chunk count the format allows decode as the
+    oracle decodes them, in full and in boxes."""
+    x = synth.grf((48, 40, 72), synth.seed_for(2, 7))
+    ref = ora.compress(x, 1e-4, nsub=nsub)
+    assert ora.info(ref)["nsub"] == nsub
+    comp = torch.from_numpy(ref).cuda()
+    full = ora.decompress(ref)
+    assert np.array_equal(_bits(stzg.decompress_full(comp).cpu().numpy()), _bits(full))
+    for lo, hi in synth.random_boxes(x.shape, 4, 99, 8, 40):
+        r = stzg.decompress_region(comp, lo, hi, 3).cpu().numpy()
+        sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+        assert np.array_equal(_bits(r), _bits(np.ascontiguousarray(full[sl]))), (lo, hi)
 
 
 @pytest.mark.parametrize("name", ["sin3d_f32_22x19x27", "sin3d_f64_9x14x10", "sin2d_f32_37x50"])
