@@ -11,7 +11,7 @@
 // points, reading x (compress) and writing G_l (next level's coarse grid, or
 // the output) with coalesced accesses along x.  Persistent grid: blocks loop
 // over tiles; compress accumulates per-stream histograms in shared memory
-// (16-bit counters packed in pairs, flushed before they can overflow).
+// (one 32-bit counter per symbol), added to the global ones at the end.
 #include "stz_kernels.cuh"
 #include "stz_prof.cuh"
 #include "stz_predict.cuh"
@@ -22,8 +22,7 @@
 namespace stz {
 
 constexpr int kLevelThreads = 256;
-constexpr int kHistWords = kAlphabet / 2;  // per stream, 2 counters per word
-constexpr int kFlushTiles = 31;            // 31 * 2048 < 65536
+constexpr int kHistWords = kAlphabet;  // shared-memory counters per stream
 
 struct TileCtx {
   int64_t m[3];   // G_l extent
@@ -69,8 +68,8 @@ __device__ __forceinline__ void do_point(const LevelArgs& a, const TileCtx& tc, 
     const bool isR = v && sym == kRadius;
     const unsigned bm = __ballot_sync(0xffffffffu, isR);
     uint32_t* h = hist + (K - 1) * kHistWords;
-    if (bm != 0u && lane == __ffs(bm) - 1) atomicAdd(&h[kRadius >> 1], (uint32_t)__popc(bm));
-    if (v && !isR) atomicAdd(&h[sym >> 1], 1u << ((sym & 1) * 16));
+    if (bm != 0u && lane == __ffs(bm) - 1) atomicAdd(&h[kRadius], (uint32_t)__popc(bm));
+    if (v && !isR) atomicAdd(&h[sym], 1u);
   } else {
     if (v) {
       int sym = a.codes[s_slot[K] + local];
@@ -92,14 +91,11 @@ __device__ __forceinline__ void do_point(const LevelArgs& a, const TileCtx& tc, 
 template <typename T>
 __device__ void flush_hist(uint32_t* hist, uint32_t* gh, int level) {
   for (int w = threadIdx.x; w < 7 * kHistWords; w += blockDim.x) {
-    uint32_t v = hist[w];
+    const uint32_t v = hist[w];
     if (v) {
-      int K = w / kHistWords + 1;
-      int sym = (w % kHistWords) * 2;
-      int sid = 1 + 7 * (level - 2) + (K - 1);
-      uint32_t* dst = gh + (int64_t)sid * kAlphabet + sym;
-      if (v & 0xFFFFu) atomicAdd(dst, v & 0xFFFFu);
-      if (v >> 16) atomicAdd(dst + 1, v >> 16);
+      const int K = w / kHistWords + 1;
+      const int sid = 1 + 7 * (level - 2) + (K - 1);
+      atomicAdd(gh + (int64_t)sid * kAlphabet + (w % kHistWords), v);
       hist[w] = 0;
     }
   }
@@ -138,7 +134,6 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const __grid_constant__
   const int64_t ntiles = a.tcnt[0] * a.tcnt[1] * a.tcnt[2];
   const int bvol = b0 * b1 * b2;
   const int iters = (bvol + nth - 1) / nth;
-  int since_flush = 0;
   for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
     const int64_t Tb[3] = {a.tlo[0] + tt / (a.tcnt[1] * a.tcnt[2]),
                            a.tlo[1] + (tt / a.tcnt[2]) % a.tcnt[1], a.tlo[2] + tt % a.tcnt[2]};
@@ -201,11 +196,6 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const __grid_constant__
       do_point<5, T, DEC>(a, tc, tile, st, q, two_eb, hist, s_slot, s_pos, s_chunk, s_l, lane);
       do_point<6, T, DEC>(a, tc, tile, st, q, two_eb, hist, s_slot, s_pos, s_chunk, s_l, lane);
       do_point<7, T, DEC>(a, tc, tile, st, q, two_eb, hist, s_slot, s_pos, s_chunk, s_l, lane);
-    }
-    if (!DEC && ++since_flush == kFlushTiles) {
-      __syncthreads();
-      flush_hist<T>(hist, a.hist, l);
-      since_flush = 0;
     }
   }
   if (!DEC) {
@@ -541,7 +531,7 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
         const int sk = sym[K - 1];
         nR[K - 1] += sk == kRadius;
         if (sk >= 0 && sk != kRadius)
-          atomicAdd(&hist[(K - 1) * kHistWords + (sk >> 1)], 1u << ((sk & 1) * 16));
+          atomicAdd(&hist[(K - 1) * kHistWords + sk], 1u);
       }
     } else {
       T val[7];
@@ -578,11 +568,10 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
     }
   }
   if (!DEC) {
-    static_assert((kRadius & 1) == 0, "R counts in the low half of its packed word");
 #pragma unroll
     for (int K = 0; K < 7; K++) {
       const uint32_t n = __reduce_add_sync(0xffffffffu, nR[K]);
-      if (lane == 0 && n) atomicAdd(&hist[K * kHistWords + (kRadius >> 1)], n);
+      if (lane == 0 && n) atomicAdd(&hist[K * kHistWords + kRadius], n);
     }
   }
 }
@@ -619,7 +608,6 @@ __global__ void __launch_bounds__(kLevelThreads, 2) k_level_fast(const __grid_co
     if (vec) tile_prefetch<T, true>(a, t, tile);
     else tile_prefetch<T, false>(a, t, tile);
   };
-  int since_flush = 0;
   int64_t tt = blockIdx.x;
   int b = 0;
   if (tt < ntiles) {
@@ -644,11 +632,6 @@ __global__ void __launch_bounds__(kLevelThreads, 2) k_level_fast(const __grid_co
     else
       fast_tile<T, DEC, false, PAIR>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2,
                                      fdz);
-    if (!DEC && ++since_flush == kFlushTiles) {
-      __syncthreads();
-      flush_hist<T>(hist, a.hist, l);
-      since_flush = 0;
-    }
   }
   cp_async_wait_all();
   if (!DEC) {
@@ -896,7 +879,7 @@ __global__ void __launch_bounds__(256) k_level_shell(const __grid_constant__ Lev
       if (!DEC) {
         nR[K - 1] += sym == kRadius;
         if (sym >= 0 && sym != kRadius)
-          atomicAdd(&hist[(K - 1) * kHistWords + (sym >> 1)], 1u << ((sym & 1) * 16));
+          atomicAdd(&hist[(K - 1) * kHistWords + sym], 1u);
       }
     }
   }
@@ -904,7 +887,7 @@ __global__ void __launch_bounds__(256) k_level_shell(const __grid_constant__ Lev
 #pragma unroll
     for (int K = 0; K < 7; K++) {
       const uint32_t n = __reduce_add_sync(0xffffffffu, nR[K]);
-      if (lane == 0 && n) atomicAdd(&hist[K * kHistWords + (kRadius >> 1)], n);
+      if (lane == 0 && n) atomicAdd(&hist[K * kHistWords + kRadius], n);
     }
     __syncthreads();
     flush_hist<T>(hist, a.hist, l);
@@ -1014,8 +997,7 @@ static int run_level_shell(const LevelArgs& a, const ShellGeo& sh, double bytes,
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess)
     return STZ_ERR_CUDA;
-  // at most 65535 cells per block keeps the 16-bit histogram counters exact
-  int64_t grid = imax(cdiv(total, 65535), imin(cdiv(total, 256), (int64_t)sm_count() * 4));
+  int64_t grid = imin(cdiv(total, 256), (int64_t)sm_count() * 4);
   char nm[48];
   snprintf(nm, sizeof(nm), "k_level%d_shell_%s_%s", a.level, DEC ? "dec" : "enc",
            sizeof(T) == 4 ? "f32" : "f64");
