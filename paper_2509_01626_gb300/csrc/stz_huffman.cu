@@ -629,8 +629,10 @@ int launch_scan2(const uint32_t* a, const uint32_t* b, int64_t n, unsigned long 
 // later lane hands it by shuffle.  Every lane but the chunk's last holds 64
 // symbols, so at least 64 bits: only neighbouring lanes ever share a word.
 // The lanes holding a sub-chunk start sum the lengths before it for the
-// sub-chunk's bit offset.  A lane with a whole run loads its 128 bytes of
-// codes at once and works from registers, the outlier listing included.
+// sub-chunk's bit offset.  A whole chunk is read with coalesced 16-byte loads
+// and handed to the lanes through shared memory (16-byte units XOR-swizzled
+// so that neither the writes nor the per-lane reads conflict); a lane with a
+// whole run then works from registers, the outlier listing included.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
                                               const uint16_t* __restrict__ codes,
@@ -654,7 +656,24 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ Geo g,
   const int s0 = lane * kLaneSyms, s1 = min(cnt, s0 + kLaneSyms);
   const bool whole = s1 - s0 == kLaneSyms;
   uint4 v[8];
-  if (whole) {
+  if (cnt == 32 * kLaneSyms) {  // every lane's run whole: coalesced, then transposed
+    __shared__ uint4 stage[8][256];  // 4 KiB per warp
+    uint4* st = stage[threadIdx.x >> 5];
+    const uint4* c4 = (const uint4*)c;
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = __ldg(c4 + 32 * k + lane);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int u = 32 * k + lane;
+      st[u ^ ((u >> 3) & 7)] = v[k];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int u = 8 * lane + k;
+      v[k] = st[u ^ ((u >> 3) & 7)];
+    }
+  } else if (whole) {
 #pragma unroll
     for (int k = 0; k < 8; k++) v[k] = __ldg((const uint4*)(c + s0) + k);
   }
