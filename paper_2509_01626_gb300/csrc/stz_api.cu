@@ -1136,8 +1136,11 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
   // cooperative launch, as inside a captured graph)
   auto launch_all = [&](cudaStream_t st, bool no_coop) -> int {
     static_assert(sizeof(DevParams) % 4 == 0, "DevParams is cleared in words");
-    STZ_TRY(zero_words(dp, (int64_t)(sizeof(DevParams) / 4), st));
-    STZ_TRY(launch_lut(tb, lut, status, st));
+    // the parameter words (status among them) are cleared by the table kernel
+    if (tb.nlut > 0)
+      STZ_TRY(launch_lut(tb, lut, (uint32_t*)dp, (int)(sizeof(DevParams) / 4), st));
+    else
+      STZ_TRY(zero_words(dp, (int64_t)(sizeof(DevParams) / 4), st));
     STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
     const uint8_t* sec0 = comp + H.d[0].sect_off;
     SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps, H.nsub);

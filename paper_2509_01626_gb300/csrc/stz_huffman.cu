@@ -820,13 +820,18 @@ int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
 }
 
 // ---------------------------------------------------------------- decode tables
+// Block 0 also clears the decode's parameter words (its status among them).
+// A table that cannot be built is left empty: every lookup then fails, so the
+// decode of any chunk of that stream reports the container corrupt.
 __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables tb,
                                              uint16_t* __restrict__ lut,
-                                             uint32_t* __restrict__ status) {
+                                             uint32_t* __restrict__ clear, int nclear) {
   __shared__ int cnt[32];
   __shared__ uint32_t fcode[32];
   __shared__ int fidx[32];
   __shared__ int bad;
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < nclear; i += blockDim.x) clear[i] = 0u;
   const int sid = tb.lut_sid[blockIdx.x];
   const DecStream& d = tb.ds[sid];
   uint16_t* t = lut + (int64_t)sid * kLutSize;
@@ -865,7 +870,6 @@ __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables t
   __syncthreads();
   if (bad) {  // an empty table: every lookup then flags the chunk as corrupt
     for (int i = tid; i < kLutSize; i += blockDim.x) t[i] = 0;
-    if (tid == 0) atomicOr(status, kStatCorrupt);
     return;
   }
   // each window i of the table: the one length L whose L-bit prefix of i
@@ -883,10 +887,11 @@ __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables t
   }
 }
 
-int launch_lut(const DecTables& tb, uint16_t* lut, uint32_t* status, cudaStream_t s) {
-  if (tb.nlut == 0) return STZ_OK;
+int launch_lut(const DecTables& tb, uint16_t* lut, uint32_t* clear, int nclear,
+               cudaStream_t s) {
+  if (tb.nlut == 0) return STZ_ERR_ARG;
   ProfScope ps_("k_lut", s);
-  k_lut<<<tb.nlut, 256, 0, s>>>(tb, lut, status);
+  k_lut<<<tb.nlut, 256, 0, s>>>(tb, lut, clear, nclear);
   return cuda_ok(cudaGetLastError());
 }
 

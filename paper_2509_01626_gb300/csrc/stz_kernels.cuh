@@ -115,7 +115,10 @@ struct DecTables {
   int njobs;
   int64_t nblocks;            // thread blocks of the chunk decoder
 };
-int launch_lut(const DecTables& tb, uint16_t* lut, uint32_t* status, cudaStream_t s);
+// decode tables of the streams tb.lut_sid[0 .. nlut) (nlut > 0); block 0 also
+// zero-fills the nclear words at clear
+int launch_lut(const DecTables& tb, uint16_t* lut, uint32_t* clear, int nclear,
+               cudaStream_t s);
 // bytes: the launch's algorithmic bytes (payload read, codes written)
 int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint16_t* lut,
                          uint16_t* codes, uint32_t* status, double bytes, cudaStream_t s);
