@@ -735,9 +735,12 @@ __device__ __forceinline__ T shell_predict(const ShellTaps<T>& t, const bool cub
   }
 }
 
+// 4 blocks per SM when decoding: the loads of a cell's taps and codes are its
+// latency.  Compressing, the shared histograms leave room for 3 at most, and
+// the registers that 3 would cost spill more than the extra warps hide.
 template <typename T, bool DEC>
-__global__ void __launch_bounds__(256) k_level_shell(const __grid_constant__ LevelArgs a,
-                                                     const __grid_constant__ ShellGeo sh) {
+__global__ void __launch_bounds__(256, DEC ? 4 : 2)
+    k_level_shell(const __grid_constant__ LevelArgs a, const __grid_constant__ ShellGeo sh) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* hist = (uint32_t*)smem;
   const Geo& geo = a.geo;
