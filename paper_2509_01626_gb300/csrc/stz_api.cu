@@ -57,6 +57,12 @@ void make_geo(const int64_t n[3], int ndim, int dtype, int L, const int b[3], Ge
 __global__ void k_readback(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
+// the same for two pieces at once
+__global__ void k_readback2(const uint8_t* __restrict__ s0, uint8_t* __restrict__ d0, int n0,
+                            const uint8_t* __restrict__ s1, uint8_t* __restrict__ d1, int n1) {
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) d0[i] = s0[i];
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) d1[i] = s1[i];
+}
 
 // Zero fill of device words by a kernel (not cudaMemsetAsync, which may be
 // carried out by a copy engine and then wait behind the caller's copies).
@@ -80,21 +86,27 @@ thread_local uint8_t* tl_rb_host = nullptr;  // mapped, pinned, portable
 thread_local uint8_t* tl_rb_dev = nullptr;   // its device address
 }  // namespace
 
+// This thread's read-back buffer, allocated on first use.
+static int rb_ready() {
+  if (tl_rb_host) return STZ_OK;
+  if (cudaHostAlloc((void**)&tl_rb_host, kReadbackBytes,
+                    cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    tl_rb_host = nullptr;
+    return STZ_ERR_NOMEM;
+  }
+  if (cudaHostGetDevicePointer((void**)&tl_rb_dev, tl_rb_host, 0) != cudaSuccess) {
+    cudaFreeHost(tl_rb_host);
+    tl_rb_host = nullptr;
+    return STZ_ERR_CUDA;
+  }
+  return STZ_OK;
+}
+
 // Queues a copy of n (<= 4096 - off) device bytes to offset off of this
 // thread's read-back buffer; *host receives where they will be on the host.
 static int readback(const void* src, int n, int off, cudaStream_t st, const uint8_t** host) {
-  if (!tl_rb_host) {
-    if (cudaHostAlloc((void**)&tl_rb_host, kReadbackBytes,
-                      cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
-      tl_rb_host = nullptr;
-      return STZ_ERR_NOMEM;
-    }
-    if (cudaHostGetDevicePointer((void**)&tl_rb_dev, tl_rb_host, 0) != cudaSuccess) {
-      cudaFreeHost(tl_rb_host);
-      tl_rb_host = nullptr;
-      return STZ_ERR_CUDA;
-    }
-  }
+  const int rr = rb_ready();
+  if (rr != STZ_OK) return rr;
   if (n <= 0 || off < 0 || off + n > kReadbackBytes) return STZ_ERR_ARG;
   {
     ProfScope ps_("k_readback", st);
@@ -102,6 +114,26 @@ static int readback(const void* src, int n, int off, cudaStream_t st, const uint
   }
   if (cudaGetLastError() != cudaSuccess) return STZ_ERR_CUDA;
   *host = tl_rb_host + off;
+  return STZ_OK;
+}
+
+// Two read-backs in one launch: n0 bytes to offset off0, n1 bytes to off1
+// (the ranges must not overlap).
+static int readback2(const void* s0, int n0, int off0, const void* s1, int n1, int off1,
+                     cudaStream_t st, const uint8_t** h0, const uint8_t** h1) {
+  const int rr = rb_ready();
+  if (rr != STZ_OK) return rr;
+  if (n0 <= 0 || off0 < 0 || off0 + n0 > kReadbackBytes || n1 <= 0 || off1 < 0 ||
+      off1 + n1 > kReadbackBytes || (off0 < off1 + n1 && off1 < off0 + n0))
+    return STZ_ERR_ARG;
+  {
+    ProfScope ps_("k_readback", st);
+    k_readback2<<<1, 256, 0, st>>>((const uint8_t*)s0, tl_rb_dev + off0, n0,
+                                   (const uint8_t*)s1, tl_rb_dev + off1, n1);
+  }
+  if (cudaGetLastError() != cudaSuccess) return STZ_ERR_CUDA;
+  *h0 = tl_rb_host + off0;
+  *h1 = tl_rb_host + off1;
   return STZ_OK;
 }
 
@@ -1252,8 +1284,10 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
   // the status word, and for a cached header the header bytes beside it
   const uint8_t* hst = nullptr;
   const uint8_t* hhdr = nullptr;
-  STZ_TRY(readback(status, 4, 0, st, &hst));
-  if (cached) STZ_TRY(readback(comp_dev, (int)nraw, 64, st, &hhdr));
+  if (cached)
+    STZ_TRY(readback2(status, 4, 0, comp_dev, (int)nraw, 64, st, &hst, &hhdr));
+  else
+    STZ_TRY(readback(status, 4, 0, st, &hst));
   STZ_TRY(cuda_ok(cudaStreamSynchronize(st)));
 #undef STZ_TRY
   uint32_t hstat = 0;
