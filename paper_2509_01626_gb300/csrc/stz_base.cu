@@ -325,8 +325,6 @@ __global__ void __launch_bounds__(256) k_base_coop(const __grid_constant__ BaseA
   }
 }
 
-template <typename T, bool DEC>
-static int run_passes(const BaseArgs& a, cudaStream_t s);
 
 template <typename T, bool DEC>
 static int run_coop(const BaseArgs& a, cudaStream_t s, bool allow_coop = true) {
@@ -507,59 +505,6 @@ static int run_coop(const BaseArgs& a, cudaStream_t s, bool allow_coop = true) {
   return cuda_ok(e);
 }
 
-template <typename T, bool DEC>
-static int run_passes(const BaseArgs& a, cudaStream_t s) {
-  int64_t m[3];
-  grid_extent(a.geo.n, a.geo.L, 1, m);
-  int64_t mx = imax(m[0], imax(m[1], m[2]));
-  int64_t T_ = 1;
-  while (T_ < mx) T_ <<= 1;
-  PassGeo p;
-  for (int b = 0; b < 3; b++) {
-    p.start[b] = 0;
-    p.step[b] = 1;
-    p.cnt[b] = 1;
-  }
-  p.total = 1;
-  p.axis = 0;
-  p.t = 1;
-  p.origin = 1;
-  const char* nm = DEC ? "k_base_pass_dec" : "k_base_pass_enc";
-  {
-    ProfScope ps_(nm, s);
-    k_base_pass<T, DEC><<<1, 32, 0, s>>>(a, p);
-  }
-  p.origin = 0;
-  for (int64_t t = T_ >> 1; t >= 1; t >>= 1) {
-    for (int ax = 0; ax < 3; ax++) {
-      p.axis = ax;
-      p.t = t;
-      p.total = 1;
-      for (int b = 0; b < 3; b++) {
-        if (b == ax) {
-          p.start[b] = t;
-          p.step[b] = 2 * t;
-          p.cnt[b] = m[b] > t ? (m[b] - t - 1) / (2 * t) + 1 : 0;
-        } else if (b < ax) {
-          p.start[b] = 0;
-          p.step[b] = t;
-          p.cnt[b] = cdiv(m[b], t);
-        } else {
-          p.start[b] = 0;
-          p.step[b] = 2 * t;
-          p.cnt[b] = cdiv(m[b], 2 * t);
-        }
-        p.total *= p.cnt[b];
-      }
-      if (p.total == 0) continue;
-      int64_t blocks = cdiv(p.total, 256);
-      ProfScope ps_(nm, s);
-      k_base_pass<T, DEC><<<(unsigned)blocks, 256, 0, s>>>(a, p);
-    }
-  }
-  return cuda_ok(cudaGetLastError());
-}
-
 int launch_base(const BaseArgs& a, bool decode, cudaStream_t s) {
   if (a.geo.dtype == STZ_F32)
     return decode ? run_coop<float, true>(a, s) : run_coop<float, false>(a, s);
@@ -570,14 +515,6 @@ int launch_base_nocoop(const BaseArgs& a, bool decode, cudaStream_t s) {
   if (a.geo.dtype == STZ_F32)
     return decode ? run_coop<float, true>(a, s, false) : run_coop<float, false>(a, s, false);
   return decode ? run_coop<double, true>(a, s, false) : run_coop<double, false>(a, s, false);
-}
-
-// One launch per pass (kept for comparison and for devices without
-// cooperative launch).
-int launch_base_passes(const BaseArgs& a, bool decode, cudaStream_t s) {
-  if (a.geo.dtype == STZ_F32)
-    return decode ? run_passes<float, true>(a, s) : run_passes<float, false>(a, s);
-  return decode ? run_passes<double, true>(a, s) : run_passes<double, false>(a, s);
 }
 
 }  // namespace stz

@@ -35,7 +35,6 @@ struct BaseArgs {
   int64_t rlo[3], rhi[3];
 };
 int launch_base(const BaseArgs& a, bool decode, cudaStream_t s);
-int launch_base_passes(const BaseArgs& a, bool decode, cudaStream_t s);
 // the coarse single-block phase, then one plain launch per remaining pass (no
 // cooperative launch: for graphs whose branches run concurrently)
 int launch_base_nocoop(const BaseArgs& a, bool decode, cudaStream_t s);
