@@ -128,10 +128,14 @@ int stz_decompress_progressive(const void* comp_dev, size_t comp_bytes, int leve
 
 /*
  * Random-access decompression of the box [lo, hi) at level `level`
- * (Sec. 3.3, Fig. 5): level 1 is decoded whole; at each finer level only the
- * chunks and predictions the box needs (its points plus the interpolation
- * support) are decoded.  The output is the box's points whose coordinates are
- * multiples of 2^(L-level), C order; out_dims receives its shape.  The values
+ * (Sec. 3.3, Fig. 5): every level-1 chunk is entropy-decoded, but only the
+ * level-1 interpolation passes the box depends on are run; at each finer
+ * level only the chunks and predictions the box needs (its points plus the
+ * interpolation support) are decoded, and of a level's 7 sub-block streams
+ * only those with points in that support (an axis-aligned slice skips the
+ * others: the 2D-slice decoding saving of Sec. 3.3).  The output is the
+ * box's points whose coordinates are multiples of 2^(L-level), C order;
+ * out_dims receives its shape.  The values
  * are bitwise those of the full decode.  The box must be non-empty and inside
  * the field (STZ_ERR_ARG otherwise); it may contain no lattice point, then
  * out_dims has a zero.
@@ -205,6 +209,22 @@ size_t stz_region_workspace_size(const void* hdr_host, size_t hdr_bytes, size_t 
                                  int level1_given);
 
 /*
+ * Plan of a region decode, on the host only (no device work): for each
+ * stream of the container (0 = level 1, 1 + 7(l-2) + (k-1) = level l
+ * sub-block k), the number of its chunks that stz_decompress_region (or the
+ * _async form, with level1_given as there) entropy-decodes for the box
+ * [lo, hi) at `level`.  Sec. 3.3: a level-l point depends only on nearby
+ * points of level l-1, so a box needs few chunks, and an axis-aligned slice
+ * needs none of the sub-blocks whose points it does not hold (3 of the 7
+ * finest-level streams for a z-slice at an even z).  hdr_host as for
+ * stz_region_workspace_size; chunks has room for max_streams entries.
+ * Returns the container's stream count, or STZ_ERR_ARG / STZ_ERR_CORRUPT.
+ */
+int stz_region_chunks(const void* hdr_host, size_t hdr_bytes, size_t comp_bytes,
+                      const int64_t* lo, const int64_t* hi, int level, int level1_given,
+                      int64_t* chunks, int max_streams);
+
+/*
  * Region decode (as stz_decompress_region: Sec. 3.3 random access, values
  * bitwise those of the full decode) that never waits on the host:
  *   hdr_host, hdr_bytes  host copy of the container's first bytes (see above)
@@ -224,29 +244,39 @@ int stz_decompress_region_async(const void* comp_dev, size_t comp_bytes, const v
                                 uint32_t* status_dev, void* stream);
 
 /*
- * Region decompression without any device allocation, for callers that
- * cannot obtain device memory at the point of the call: a plug-in (an I/O
- * library filter, a visualisation reader) that its host application hands
- * only the compressed input and the output buffer, or a latency-critical
- * path that must not pay cudaMalloc's implicit device synchronisation.
- * The paper has no counterpart; it is an addition of this library.
+ * Region decompression without any allocation, for callers that cannot
+ * obtain memory at the point of the call: a plug-in (an I/O library filter,
+ * a visualisation reader) that its host application hands only the
+ * compressed input and the output buffer, or a latency-critical path that
+ * must not pay cudaMalloc's implicit device synchronisation.  The paper has
+ * no counterpart; it is an addition of this library.
  *
  * Same arguments, output and errors as stz_decompress_region, minus the
  * workspace: the scratch comes from one array of STZ_NOALLOC_SCRATCH_BYTES
  * in the library's device memory, which every GPU that loads the library
- * holds until the process exits.  A call whose decode needs more scratch
- * than that returns STZ_ERR_CAPACITY before any work is queued (the level-1
- * grid of the field is always decoded whole, so this covers fields up to
- * about 512^3 f32 with boxes up to about 128^3).
+ * holds until the process exits (with CUDA's lazy module loading it is
+ * reserved on a device when the library's kernels are first loaded there,
+ * at the latest by this call's first use on that device).  A call whose
+ * decode needs more scratch than that returns STZ_ERR_CAPACITY before any
+ * work is queued (all level-1 chunks are decoded into it, so this covers
+ * fields up to about 512^3 f32 with boxes up to about 128^3).
+ *
+ * Allocates nothing, on the host or the device: no cudaMalloc, cudaFree,
+ * cudaHostAlloc or graph instantiation.  The header and the final status
+ * word come back by plain copies into the call's own stack, and the kernels
+ * are launched one by one (other decode calls cache parsed headers, use a
+ * pinned per-thread read-back buffer and replay repeated calls as graphs;
+ * this one does none of that).  Only with kernel timing switched on
+ * (stz_profile_enable) does the library's timer create CUDA events.
  *
  * The first call on a device looks up that array's device address (with
  * the device current); make that first call before any stream capture on
  * the device.  The calling thread must have the stream's device current.
+ * The call waits on the host for the header and for the final status.
  * All calls share the one array and it keeps the last call's contents
  * (each call clears what must start at zero): calls whose work overlaps on
  * the GPU -- on different streams, or from different host threads -- race
  * and give wrong results.  Issue them on one stream, one after another.
- * Allocates nothing: no cudaMalloc, no cudaFree.
  */
 #define STZ_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 int stz_decompress_region_noalloc(const void* comp_dev, size_t comp_bytes, const int64_t* lo,

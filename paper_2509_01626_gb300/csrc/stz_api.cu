@@ -362,15 +362,40 @@ static int read_hdr(const void* comp, size_t comp_bytes, int on_device, cudaStre
 struct DecPlan {
   int k;
   int64_t OA[3], OB[3];                                // output box on G_k
-  int64_t A[kMaxLevels + 1][3], B[kMaxLevels + 1][3];  // boxes on G_j (G_1 whole)
+  int64_t A[kMaxLevels + 1][3], B[kMaxLevels + 1][3];  // grid boxes on G_j (G_1 whole)
+  int64_t N1A[3], N1B[3];                              // the part of G_1 the output needs
   int64_t tlo[kMaxLevels + 1][3], tcnt[kMaxLevels + 1][3];
   SlotMap sm[kMaxStreams];
   int64_t nslots;
   size_t dp, grid[kMaxLevels + 1], codes, lut, total;
 };
 
+// Coarse support of the G_j coordinates [a, b) along one axis, on G_{j-1}
+// (extent M): a coordinate 2c + 1 is predicted from coarse c - 1 .. c + 2
+// (the cubic reach, Eqs. 6-8; the boundary rules use a subset), a
+// coordinate 2c is the copy of coarse c.  A range holding one even
+// coordinate -- an axis-aligned slice on the lattice of the coarser level --
+// therefore needs one coarse plane; any other range needs its widened hull.
+static void coarse_support(int64_t a, int64_t b, int64_t M, int64_t* ca, int64_t* cb) {
+  if (b - a == 1 && a % 2 == 0) {
+    *ca = a / 2;
+    *cb = a / 2 + 1;
+  } else {
+    *ca = imax(0, a / 2 - 1);
+    *cb = imin(M, b / 2 + 2);
+  }
+}
+
 // skip_l1: the caller supplies the decoded level-1 grid (no level-1 buffer,
 // no level-1 code slots).
+//
+// Random access (Sec. 3.3): at each level j >= 2 only the points of the box
+// [A[j], B[j]) are predicted, and of the level's 7 sub-block streams each
+// decodes only the bricks holding its own points of that box.  A sub-block
+// whose offset parity along some axis never occurs in the box (an
+// axis-aligned slice at an even coordinate has no odd-z points) decodes no
+// chunk at all: a z-slice at the finest level reads 3 of the 7 level-L
+// streams, the 2D-slice decoding saving of Sec. 3.3.
 static void plan_decode(const Geo& g, int k, const int64_t lo[3], const int64_t hi[3], DecPlan* P,
                         bool skip_l1 = false) {
   memset(P, 0, sizeof(*P));
@@ -383,20 +408,21 @@ static void plan_decode(const Geo& g, int k, const int64_t lo[3], const int64_t 
   for (int j = k; j >= 2; j--) {
     int64_t M[3];
     grid_extent(g.n, g.L, j - 1, M);
-    for (int a = 0; a < 3; a++) {
-      P->A[j - 1][a] = imax(0, P->A[j][a] / 2 - 1);
-      P->B[j - 1][a] = imin(M[a], P->B[j][a] / 2 + 2);
-    }
+    for (int a = 0; a < 3; a++)
+      coarse_support(P->A[j][a], P->B[j][a], M[a], &P->A[j - 1][a], &P->B[j - 1][a]);
   }
   {
     int64_t m1[3];
     grid_extent(g.n, g.L, 1, m1);
     for (int a = 0; a < 3; a++) {
-      P->A[1][a] = 0;
+      P->N1A[a] = P->A[1][a];
+      P->N1B[a] = P->B[1][a];
+      P->A[1][a] = 0;  // the level-1 grid buffer is always laid out whole
       P->B[1][a] = m1[a];
     }
   }
-  // slots: level 1 whole, then for each level the bricks over the needed cells
+  // slots: level 1 whole, then for each level and sub-block the bricks over
+  // that sub-block's points in the box
   int64_t nslots = 0;
   const StreamGeo& s0 = g.s[0];
   for (int a = 0; a < 3; a++) {
@@ -417,10 +443,20 @@ static void plan_decode(const Geo& g, int k, const int64_t lo[3], const int64_t 
       SlotMap& sm = P->sm[sid];
       int64_t c = 1;
       for (int a = 0; a < 3; a++) {
-        sm.lo[a] = P->tlo[j][a];
-        sm.cnt[a] = imax(0, imin(P->tlo[j][a] + P->tcnt[j][a], sg.nb[a]) - P->tlo[j][a]);
+        // cells c of the sub-block with 2c + o in [A, B)
+        const int64_t o = sg.o[a];
+        const int64_t c0 = imax(0, (P->A[j][a] - o + 1) >> 1);
+        const int64_t c1 = imin(sg.e[a], (P->B[j][a] - o + 1) >> 1);
+        if (c1 <= c0) {
+          c = 0;
+          break;
+        }
+        sm.lo[a] = c0 / g.b[a];
+        sm.cnt[a] = cdiv(c1, g.b[a]) - sm.lo[a];
         c *= sm.cnt[a];
       }
+      if (c == 0)
+        for (int a = 0; a < 3; a++) sm.lo[a] = sm.cnt[a] = 0;
       sm.base = nslots;
       nslots += c;
     }
@@ -1023,6 +1059,10 @@ struct DecOpts {
   const void* l1;
   uint32_t* status_out;
   bool no_cache;  // read the header back even when it is cached
+  // allocate nothing on the host or the device: the header and the status
+  // word come back by plain copies into this call's stack, the header cache
+  // is not used, and the launches are never captured into a graph
+  bool no_alloc;
 };
 
 static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* lo_in,
@@ -1043,6 +1083,12 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
   bool cached = false;
   if (o.hdr) {
     H = *o.hdr;
+  } else if (o.no_alloc) {
+    if (comp_bytes < (size_t)kHeaderBytes) return STZ_ERR_CORRUPT;
+    if (cudaMemcpyAsync(raw, comp_dev, nraw, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return STZ_ERR_CUDA;
+    rc = parse_hdr(raw, nraw, comp_bytes, &H);
   } else {
     if (cudaGetDevice(&dev) != cudaSuccess) return STZ_ERR_CUDA;
     cached = !o.no_cache && hdr_cache_get(dev, comp_dev, comp_bytes, &H, raw, &nraw_cached);
@@ -1139,10 +1185,10 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
   double dec_bytes = 0.0;
   for (int s = have_l1 ? 1 : 0; s < ns_needed; s++) {
     if (g.s[s].nsym == 0) continue;
-    tb.lut_sid[tb.nlut++] = s;
     const SlotMap& sm = P.sm[s];
     const int64_t c = sm.cnt[0] * sm.cnt[1] * sm.cnt[2];
-    if (c == 0) continue;
+    if (c == 0) continue;  // no point of this stream is needed: no table, no chunk
+    tb.lut_sid[tb.nlut++] = s;
     DecChunkJob& jb = tb.jobs[tb.njobs++];
     jb.sid = s;
     for (int a = 0; a < 3; a++) {
@@ -1196,8 +1242,8 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
       grid_extent(g.n, g.L, 1, m1);
       bool whole = true;
       for (int d = 0; d < 3; d++) {
-        a.rlo[d] = level == 1 ? P.OA[d] : imax(0, P.A[2][d] / 2 - 1);
-        a.rhi[d] = level == 1 ? P.OB[d] : imin(m1[d], P.B[2][d] / 2 + 2);
+        a.rlo[d] = level == 1 ? P.OA[d] : P.N1A[d];
+        a.rhi[d] = level == 1 ? P.OB[d] : P.N1B[d];
         whole = whole && a.rlo[d] == 0 && a.rhi[d] == m1[d];
       }
       a.region = whole ? 0 : 1;
@@ -1252,7 +1298,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     return STZ_OK;
   };
   // plain calls repeated with the same arguments and header replay a graph
-  if (!o.status_out && !o.hdr && !prof_enabled()) {
+  if (!o.status_out && !o.hdr && !o.no_alloc && !prof_enabled()) {
     DecKey key;
     memset(&key, 0, sizeof(key));
     key.dev = dev;
@@ -1280,6 +1326,12 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     k_readback<<<1, 32, 0, st>>>((const uint8_t*)status, (uint8_t*)o.status_out, 4);
     STZ_TRY(cuda_ok(cudaGetLastError()));
     return STZ_OK;
+  }
+  if (o.no_alloc) {
+    uint32_t hs = 0;
+    STZ_TRY(cuda_ok(cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st)));
+    STZ_TRY(cuda_ok(cudaStreamSynchronize(st)));
+    return (hs & kStatCorrupt) ? STZ_ERR_CORRUPT : STZ_OK;
   }
   // the status word, and for a cached header the header bytes beside it
   const uint8_t* hst = nullptr;
@@ -1351,6 +1403,30 @@ size_t stz_region_workspace_size(const void* hdr_host, size_t hdr_bytes, size_t 
   DecPlan P;
   plan_decode(g, level, lo, hi, &P, level1_given != 0);
   return P.total;
+}
+
+int stz_region_chunks(const void* hdr_host, size_t hdr_bytes, size_t comp_bytes,
+                      const int64_t* lo_in, const int64_t* hi_in, int level, int level1_given,
+                      int64_t* chunks, int max_streams) {
+  if (!hdr_host || !lo_in || !hi_in || !chunks) return STZ_ERR_ARG;
+  Hdr H;
+  const int rc = parse_hdr((const uint8_t*)hdr_host, hdr_bytes, comp_bytes, &H);
+  if (rc != STZ_OK) return rc;
+  if (level < 1 || level > H.L || max_streams < H.ns) return STZ_ERR_ARG;
+  int64_t lo[3], hi[3];
+  box3(H, lo_in, hi_in, lo, hi);
+  Geo g;
+  make_geo(H.n, H.ndim, H.dtype, H.L, H.b, &g);
+  for (int a = 0; a < 3; a++)
+    if (lo[a] < 0 || hi[a] > g.n[a] || lo[a] >= hi[a]) return STZ_ERR_ARG;
+  DecPlan P;
+  plan_decode(g, level, lo, hi, &P, level1_given != 0);
+  const int ns_needed = 1 + 7 * (level - 1);
+  for (int s = 0; s < H.ns; s++) {
+    const SlotMap& sm = P.sm[s];
+    chunks[s] = (s < ns_needed && g.s[s].nsym > 0) ? sm.cnt[0] * sm.cnt[1] * sm.cnt[2] : 0;
+  }
+  return H.ns;
 }
 
 int stz_decompress_region_async(const void* comp_dev, size_t comp_bytes, const void* hdr_host,
@@ -1426,10 +1502,13 @@ int stz_decompress_region_noalloc(const void* comp_dev, size_t comp_bytes, const
   void* ws = nullptr;
   const int rc = noalloc_scratch(&ws);
   if (rc != STZ_OK) return rc;
-  // decode_impl rejects a plan larger than the array before it queues work
+  // decode_core rejects a plan larger than the array before it queues work
   // and clears the device parameters (status word) at its start
-  return decode_impl(comp_dev, comp_bytes, lo, hi, level, 0, out_dev, out_cap, out_dims, ws,
-                     STZ_NOALLOC_SCRATCH_BYTES, (cudaStream_t)stream);
+  DecOpts o;
+  memset(&o, 0, sizeof(o));
+  o.no_alloc = true;
+  return decode_core(comp_dev, comp_bytes, lo, hi, level, 0, out_dev, out_cap, out_dims, ws,
+                     STZ_NOALLOC_SCRATCH_BYTES, (cudaStream_t)stream, o);
 }
 
 }  // extern "C"

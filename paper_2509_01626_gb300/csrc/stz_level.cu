@@ -143,7 +143,10 @@ __global__ void __launch_bounds__(kLevelThreads) k_level(const __grid_constant__
       const int K = tid + 1;
       const StreamGeo& sg = geo.s[1 + 7 * (l - 2) + (K - 1)];
       const SlotMap& sm = a.sm[K];
-      bool ok = Tb[0] < sg.nb[0] && Tb[1] < sg.nb[1] && Tb[2] < sg.nb[2];
+      // the brick holds points of this stream that the call needs (a region
+      // decode gives each stream its own brick range)
+      bool ok = Tb[0] >= sm.lo[0] && Tb[0] < sm.lo[0] + sm.cnt[0] && Tb[1] >= sm.lo[1] &&
+                Tb[1] < sm.lo[1] + sm.cnt[1] && Tb[2] >= sm.lo[2] && Tb[2] < sm.lo[2] + sm.cnt[2];
       if (ok) {
         int64_t l0 = imin(b0, sg.e[0] - c0[0]), l1 = imin(b1, sg.e[1] - c0[1]),
                 l2 = imin(b2, sg.e[2] - c0[2]);
@@ -306,7 +309,10 @@ __device__ __forceinline__ void tile_info(const LevelArgs& a, int64_t tt, TileIn
     const int K = tid + 1;
     const StreamGeo& sg = geo.s[1 + 7 * (l - 2) + (K - 1)];
     const SlotMap& sm = a.sm[K];
-    if (Tb[0] < sg.nb[0] && Tb[1] < sg.nb[1] && Tb[2] < sg.nb[2]) {
+    // the brick holds points of this stream that the call needs (a region
+    // decode gives each stream its own brick range, within the stream's own)
+    if (Tb[0] >= sm.lo[0] && Tb[0] < sm.lo[0] + sm.cnt[0] && Tb[1] >= sm.lo[1] &&
+        Tb[1] < sm.lo[1] + sm.cnt[1] && Tb[2] >= sm.lo[2] && Tb[2] < sm.lo[2] + sm.cnt[2]) {
       const int64_t l0 = imin(kFBZ, sg.e[0] - c0[0]), l1 = imin(kFBY, sg.e[1] - c0[1]),
                     l2 = imin(kFBX, sg.e[2] - c0[2]);
       ti.l[K][0] = (int)l0;

@@ -105,18 +105,17 @@ class Server:
                    for _ in range(self.nslots)]
         self.outs = [torch.empty(slot_out, dtype=torch.uint8, device=self.device)
                      for _ in range(self.nslots)]
-        self.status = torch.zeros(self.nslots, dtype=torch.int32, device=self.device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.nslots)]
         self.events = [torch.cuda.Event() for _ in range(self.nslots)]
 
-    def _launch(self, slot: int, r: Request):
+    def _launch(self, slot: int, r: Request, status: torch.Tensor):
         f = self.fields[r.field]
         if any(b - a > self.max_edge for a, b in zip(r.lo, r.hi)):
             raise ValueError(f"box edge above the server's maximum {self.max_edge}: {r}")
         dt = f.meta["dtype"]
         out = self.outs[slot].view(dt)
         shape = stz.decompress_region_async(f.comp, f.hdr, r.lo, r.hi, r.level, out,
-                                            self.ws[slot], self.status[slot:slot + 1],
+                                            self.ws[slot], status,
                                             level1=f.level1, stream=self.streams[slot])
         self.events[slot].record(self.streams[slot])
         return shape
@@ -124,36 +123,48 @@ class Server:
     def run(self, requests, keep_outputs: bool = False, realtime: bool = True):
         """Serve the requests (sorted by arrival); returns the results in
         completion order and the wall time of the run."""
-        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        order = sorted(range(len(requests)), key=lambda i: requests[i].arrival)
+        pending = collections.deque((i, requests[i]) for i in order)
+        # one status word per request: each decode writes its own, and the
+        # words are read once, after the run
+        status = torch.zeros(max(1, len(requests)), dtype=torch.int32, device=self.device)
         waiting = collections.deque()
         free = list(range(self.nslots - 1, -1, -1))
         inflight = {}
-        results = []
+        results, index = [], []
         t0 = time.perf_counter()
         while pending or waiting or inflight:
             now = time.perf_counter() - t0
-            while pending and (not realtime or pending[0].arrival <= now):
+            while pending and (not realtime or pending[0][1].arrival <= now):
                 waiting.append(pending.popleft())
             # admit every waiting request a slot is free for, and launch them
             while waiting and free:
-                r = waiting.popleft()
+                i, r = waiting.popleft()
                 slot = free.pop()
-                inflight[slot] = (r, self._launch(slot, r))
+                inflight[slot] = (i, r, self._launch(slot, r, status[i:i + 1]))
             # completions
             done = [s for s in inflight if self.events[s].query()]
             if done:
                 now = time.perf_counter() - t0
                 for s in done:
-                    r, shape = inflight.pop(s)
+                    i, r, shape = inflight.pop(s)
                     out = None
                     if keep_outputs:
                         n = int(np.prod(shape)) if len(shape) else 0
-                        out = self.outs[s].view(self.fields[r.field].meta["dtype"])[:n] \
-                            .reshape(shape).clone()
-                    st = int(self.status[s].item()) if keep_outputs else 0
-                    results.append(Result(r, now - r.arrival, shape, st, out))
+                        with torch.cuda.stream(self.streams[s]):
+                            out = self.outs[s].view(self.fields[r.field].meta["dtype"])[:n] \
+                                .reshape(shape).clone()
+                    results.append(Result(r, now - r.arrival, shape, 0, out))
+                    index.append(i)
                     free.append(s)
         wall = time.perf_counter() - t0
+        torch.cuda.synchronize(self.device)
+        st = status.cpu().numpy()
+        for res, i in zip(results, index):
+            res.status = int(st[i])
+        if st.any():
+            raise RuntimeError(f"{int((st != 0).sum())} request decodes reported a corrupt "
+                               "container")
         return results, wall
 
 

@@ -102,6 +102,8 @@ def lib() -> ctypes.CDLL:
         L.stz_region_workspace_size.restype = sz
         L.stz_region_workspace_size.argtypes = [vp, sz, sz, i64p, i64p, ctypes.c_int,
                                                 ctypes.c_int]
+        L.stz_region_chunks.argtypes = [vp, sz, sz, i64p, i64p, ctypes.c_int, ctypes.c_int,
+                                         i64p, ctypes.c_int]
         L.stz_decompress_region_async.argtypes = [vp, sz, vp, sz, vp, i64p, i64p, ctypes.c_int,
                                                   vp, sz, i64p, vp, sz, vp, vp]
         L.stz_launch_count.restype = ctypes.c_ulonglong
@@ -262,6 +264,9 @@ def decompress_region(comp: torch.Tensor, lo, hi, level: int | None = None,
     inf = meta or info(comp)
     if level is None:
         level = inf["levels"]
+    if out is not None and (out.dtype != inf["dtype"] or out.device != comp.device
+                            or not out.is_contiguous()):
+        raise ValueError("out must be a contiguous tensor of the container's dtype on its device")
     if out is None:
         n = 1
         for a, b in zip(lo, hi):
@@ -295,12 +300,16 @@ def decompress_region_noalloc(comp: torch.Tensor, lo, hi, level: int, out: torch
     memory when they decode; `out` must be given.  Calls share that array,
     so issue them on one stream."""
     inf = meta or info(comp)
+    if out.dtype != inf["dtype"] or out.device != comp.device or not out.is_contiguous():
+        raise ValueError("out must be a contiguous tensor of the container's dtype on its device")
     od = (ctypes.c_int64 * 3)()
-    rc = lib().stz_decompress_region_noalloc(ctypes.c_void_p(comp.data_ptr()), comp.numel(),
-                                             _i64(lo), _i64(hi), int(level),
-                                             ctypes.c_void_p(out.data_ptr()),
-                                             out.numel() * out.element_size(), od,
-                                             _stream(stream))
+    # the library looks up its scratch array on the current device
+    with torch.cuda.device(comp.device):
+        rc = lib().stz_decompress_region_noalloc(ctypes.c_void_p(comp.data_ptr()), comp.numel(),
+                                                 _i64(lo), _i64(hi), int(level),
+                                                 ctypes.c_void_p(out.data_ptr()),
+                                                 out.numel() * out.element_size(), od,
+                                                 _stream(stream))
     _check(rc, "stz_decompress_region_noalloc")
     oshape = _shape_out(od, inf["ndim"])
     n = 1
@@ -322,6 +331,18 @@ def region_workspace_size(hdr: bytes, comp_bytes: int, lo, hi, level: int,
                           level1_given: bool) -> int:
     return int(lib().stz_region_workspace_size(hdr, len(hdr), int(comp_bytes), _i64(lo), _i64(hi),
                                                int(level), 1 if level1_given else 0))
+
+
+def region_chunks(hdr: bytes, comp_bytes: int, lo, hi, level: int,
+                  level1_given: bool = False) -> list[int]:
+    """stz_region_chunks (host only): per stream, the chunks a region decode
+    of [lo, hi) at `level` entropy-decodes."""
+    buf = (ctypes.c_int64 * 64)()
+    n = lib().stz_region_chunks(hdr, len(hdr), int(comp_bytes), _i64(lo), _i64(hi), int(level),
+                                1 if level1_given else 0, buf, 64)
+    if n < 0:
+        _check(n, "stz_region_chunks")
+    return [int(buf[i]) for i in range(n)]
 
 
 def decompress_region_async(comp: torch.Tensor, hdr: bytes, lo, hi, level: int,

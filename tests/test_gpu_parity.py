@@ -148,6 +148,49 @@ def test_regions_match_oracle(stzg, ora, name):
         assert np.array_equal(_bits(r), _bits(np.ascontiguousarray(full[sl]))), (lo, hi, level)
 
 
+@pytest.mark.parametrize("name", ["grf128_rel1e-3", "ragged_37x29x41", "2d_180x360",
+                                  "f64_40x33x27", "ones_axis_1x40x1"])
+def test_axis_slices_match_oracle(stzg, ora, name):
+    """Axis-aligned slices, thin slabs and lines at even and odd coordinates,
+    at every level: a slice decodes only the sub-block streams that hold its
+    points (Sec. 3.3), and its values equal the oracle's region decode and
+    the slice of the oracle's full decode."""
+    x, eb, mode, ref = case(name, ora)
+    comp = torch.from_numpy(ref).cuda()
+    full = ora.decompress(ref)
+    nd = x.ndim
+    for axis in range(nd):
+        n = x.shape[axis]
+        for c in sorted({0, 1, n // 2 - n // 2 % 2, n // 2 - n // 2 % 2 + 1, n - 2, n - 1}):
+            if not 0 <= c < n:
+                continue
+            for width in (1, 2, 3):
+                if c + width > n:
+                    continue
+                lo = [0] * nd
+                hi = list(x.shape)
+                lo[axis], hi[axis] = c, c + width
+                for level in (1, 2, 3):
+                    s = 1 << (3 - level)
+                    sl = tuple(slice(-(-a // s) * s, b, s) for a, b in zip(lo, hi))
+                    want = np.ascontiguousarray(full[sl])
+                    if want.size == 0:
+                        continue
+                    r = stzg.decompress_region(comp, lo, hi, level).cpu().numpy()
+                    assert np.array_equal(_bits(r), _bits(want)), (axis, c, width, level)
+                    o = ora.decompress_region(ref, lo, hi, level)
+                    assert np.array_equal(_bits(r), _bits(o)), (axis, c, width, level)
+    # lines along each axis (two coordinates fixed)
+    if nd == 3:
+        for axis in range(3):
+            lo = [5 % x.shape[0], 6 % x.shape[1], 7 % x.shape[2]]
+            hi = [v + 1 for v in lo]
+            lo[axis], hi[axis] = 0, x.shape[axis]
+            r = stzg.decompress_region(comp, lo, hi, 3).cpu().numpy()
+            sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+            assert np.array_equal(_bits(r), _bits(np.ascontiguousarray(full[sl]))), axis
+
+
 @pytest.mark.parametrize("nsub", [1, 2, 4, 8])
 def test_sub_chunk_counts_decode(stzg, ora, nsub):
     """Containers with every sub-chunk count the format allows decode as the
@@ -222,6 +265,15 @@ def test_full_size_512_grf(stzg, ora):
         r = stzg.decompress_region(comp, lo, hi, 3).cpu().numpy()
         sl = tuple(slice(a, b) for a, b in zip(lo, hi))
         assert np.array_equal(_bits(r), _bits(np.ascontiguousarray(recon[sl])))
+    # 512^2 slices on every axis, at even and odd coordinates (3 or 4 of the 7
+    # finest streams decoded)
+    for axis in range(3):
+        for c in (256, 257, 0, 511):
+            lo, hi = [0, 0, 0], [512, 512, 512]
+            lo[axis], hi[axis] = c, c + 1
+            r = stzg.decompress_region(comp, lo, hi, 3).cpu().numpy()
+            sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+            assert np.array_equal(_bits(r), _bits(np.ascontiguousarray(recon[sl]))), (axis, c)
 
 
 def test_region_dependencies_256_grf(stzg, ora):
