@@ -60,7 +60,14 @@ class _Params(ctypes.Structure):
         ("max_code_len", ctypes.c_int),
         ("brick", ctypes.c_int * 3),
         ("nsub", ctypes.c_int),
+        ("predictor", ctypes.c_int),
+        ("eb_ratio", ctypes.c_double),
     ]
+
+
+# predictors of levels 2..L (ablation of Sec. 3.1): opt. 4 cubic (the method),
+# opt. 2 multi-linear, opt. 1 direct
+PREDICTORS = {"cubic": 0, "linear": 1, "direct": 2}
 
 
 class _Info(ctypes.Structure):
@@ -101,6 +108,9 @@ def lib():
         L.ora_predict_f32.restype = ctypes.c_float
         L.ora_predict_f32.argtypes = [vp, i64p, ctypes.c_int, ctypes.c_int, i64p, ctypes.c_int,
                                       ctypes.c_int64]
+        L.ora_predict_mode_f64.restype = ctypes.c_double
+        L.ora_predict_mode_f64.argtypes = [vp, i64p, ctypes.c_int, ctypes.c_int, i64p,
+                                           ctypes.c_int]
         L.ora_stream_pos.restype = ctypes.c_int64
         L.ora_stream_pos.argtypes = [i64p, ctypes.POINTER(ctypes.c_int), i64p]
         _lib = L
@@ -120,7 +130,7 @@ def _dims3(shape):
 
 
 def make_params(shape, dtype, eb, mode="rel", levels=3, radius=1024, max_code_len=12,
-                brick=None, nsub=8) -> _Params:
+                brick=None, nsub=8, predictor="cubic", eb_ratio=2.5) -> _Params:
     ndim, d3 = _dims3(shape)
     if brick is None:
         brick = BRICK_3D if ndim == 3 else BRICK_2D
@@ -136,6 +146,8 @@ def make_params(shape, dtype, eb, mode="rel", levels=3, radius=1024, max_code_le
     p.radius = int(radius)
     p.max_code_len = int(max_code_len)
     p.nsub = int(nsub)
+    p.predictor = PREDICTORS[predictor]
+    p.eb_ratio = float(eb_ratio)
     return p
 
 
@@ -197,6 +209,8 @@ def info(comp: np.ndarray) -> dict:
         "max_code_len": p.max_code_len,
         "brick": tuple(p.brick),
         "nsub": p.nsub,
+        "predictor": {v: k for k, v in PREDICTORS.items()}[p.predictor],
+        "eb_ratio": p.eb_ratio,
         "eb_mode": "rel" if p.eb_mode == 1 else "abs",
         "eb": p.eb,
         "eb_abs": inf.eb_abs,
@@ -281,6 +295,15 @@ def predict(grid: np.ndarray, levels: int, level: int, g, axis: int = 0, t: int 
         return lib().ora_predict_f64(grid.ctypes.data, _i64(n), levels, level, _i64(g), axis, t)
     return np.float32(lib().ora_predict_f32(grid.ctypes.data, _i64(n), levels, level, _i64(g),
                                             axis, t))
+
+
+def predict_mode(grid: np.ndarray, levels: int, level: int, g, predictor: str) -> float:
+    """Level >= 2 prediction of field point g with the chosen predictor
+    ("cubic", "linear", "direct"); float64 grids."""
+    grid = np.ascontiguousarray(grid, dtype=np.float64)
+    n = grid.shape if grid.ndim == 3 else (1,) + grid.shape
+    return lib().ora_predict_mode_f64(grid.ctypes.data, _i64(n), levels, level, _i64(g),
+                                      PREDICTORS[predictor])
 
 
 def stream_pos(e, b, c) -> int:

@@ -28,7 +28,8 @@
  *     9 u8 eb_mode | 10 u8 max_code_len | 11 u8 nsub | 12 u32 radius |
  *     16 u32 brick z,y,x | 28 u32 nstreams | 32 i64 nz,ny,nx | 56 f64 eb |
  *     64 f64 eb_abs | 72 f64 min | 80 f64 max | 88 u64 total_bytes |
- *     96 f64 eb_level[6] | 144 f64 two_eb[6] | 192 f64 ratio | rest 0
+ *     96 f64 eb_level[6] | 144 f64 two_eb[6] | 192 f64 eb_ratio |
+ *     200 u8 predictor (0 cubic, 1 multi-linear, 2 direct) | rest 0
  *   directory at 256, one 48-byte entry per stream:
  *     u64 section_offset | u64 nsym | u32 nchunks | u32 nlive |
  *     u64 payload_words | u64 noutliers | u64 0
@@ -178,11 +179,16 @@ static double eb_absolute(int eb_mode, double eb, int any_finite, double vmin, d
   return ea;
 }
 
-static double eb_of_level(double eb_abs, int L, int l) {
+/* ratio: 2.5 in the paper; ratio^k is formed by repeated multiplication in
+ * double, in this order, so that a decoder or another implementation forms
+ * the same bound (2.5^k is exact for k <= 6) */
+static double eb_of_level(double eb_abs, int L, int l, double ratio) {
   double r = 1.0;
-  for (int k = 0; k < L - l; k++) r *= 2.5; /* 2.5^k is exact in double */
+  for (int k = 0; k < L - l; k++) r *= ratio;
   return eb_abs / r;
 }
+
+static double ratio_of(const ora_params* p) { return p->eb_ratio == 0.0 ? 2.5 : p->eb_ratio; }
 
 static float rz_float(double v) { /* largest float <= v, for v > 0 */
   float f = (float)v;
@@ -457,6 +463,10 @@ static int check_params(const ora_params* p) {
     if (p->brick[a] < 1 || p->brick[a] > 4096) return ORA_ERR_ARG;
   if ((int64_t)p->brick[0] * p->brick[1] * p->brick[2] * p->max_code_len > 65535) return ORA_ERR_ARG;
   if (p->nsub != 1 && p->nsub != 2 && p->nsub != 4 && p->nsub != 8) return ORA_ERR_ARG;
+  if (p->predictor != ORA_PRED_CUBIC && p->predictor != ORA_PRED_LINEAR &&
+      p->predictor != ORA_PRED_DIRECT)
+    return ORA_ERR_ARG;
+  if (p->eb_ratio != 0.0 && !(p->eb_ratio >= 1.0 && p->eb_ratio <= 64.0)) return ORA_ERR_ARG;
   return ORA_OK;
 }
 
@@ -544,8 +554,9 @@ static int encode_all(const void* field, const ora_params* p, const geom* g,
     c.r = (float*)recon;
     c.codes = cp;
     c.R = p->radius;
+    c.predictor = p->predictor;
     for (int l = 1; l <= g->L; l++) {
-      eb_lv[l] = eb_of_level(*eb_abs, g->L, l);
+      eb_lv[l] = eb_of_level(*eb_abs, g->L, l, ratio_of(p));
       level_consts_f32(eb_lv[l], p->radius, &c.q[l]);
       two_eb_lv[l] = (double)c.q[l].two_eb;
     }
@@ -559,8 +570,9 @@ static int encode_all(const void* field, const ora_params* p, const geom* g,
     c.r = (double*)recon;
     c.codes = cp;
     c.R = p->radius;
+    c.predictor = p->predictor;
     for (int l = 1; l <= g->L; l++) {
-      eb_lv[l] = eb_of_level(*eb_abs, g->L, l);
+      eb_lv[l] = eb_of_level(*eb_abs, g->L, l, ratio_of(p));
       level_consts_f64(eb_lv[l], p->radius, &c.q[l]);
       two_eb_lv[l] = c.q[l].two_eb;
     }
@@ -672,7 +684,8 @@ int ora_compress(const void* field, const ora_params* p, uint8_t* out, size_t ca
     putf64(out + 96 + 8 * (l - 1), eb_lv[l]);
     putf64(out + 144 + 8 * (l - 1), two[l]);
   }
-  putf64(out + 192, 2.5);
+  putf64(out + 192, ratio_of(p));
+  out[200] = (uint8_t)p->predictor;
 
   /* directory and sections */
   int64_t* fidx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -782,6 +795,8 @@ static int parse(const uint8_t* c, size_t nbytes, parsed* P) {
   P->info.nstreams = (int)get32(c + 28);
   for (int a = 0; a < 3; a++) p->dims[a] = (int64_t)get64(c + 32 + 8 * a);
   p->eb = getf64(c + 56);
+  p->eb_ratio = getf64(c + 192);
+  p->predictor = c[200];
   P->info.eb_abs = getf64(c + 64);
   P->info.total_bytes = get64(c + 88);
   if (check_params(p) != ORA_OK) return ORA_ERR_CORRUPT;
@@ -974,6 +989,7 @@ static int decode_to_level(const uint8_t* comp, size_t comp_bytes, int level, pa
     c.oval = ovf;
     c.nout = nout;
     c.R = P->info.p.radius;
+    c.predictor = P->info.p.predictor;
     for (int l = 1; l <= P->g.L; l++) c.q[l].two_eb = (float)P->info.two_eb[l];
     run_base_f32(&c);
     run_levels_f32(&c, level);
@@ -989,6 +1005,7 @@ static int decode_to_level(const uint8_t* comp, size_t comp_bytes, int level, pa
     c.oval = ovd;
     c.nout = nout;
     c.R = P->info.p.radius;
+    c.predictor = P->info.p.predictor;
     for (int l = 1; l <= P->g.L; l++) c.q[l].two_eb = P->info.two_eb[l];
     run_base_f64(&c);
     run_levels_f64(&c, level);
@@ -1067,7 +1084,19 @@ double ora_predict_f64(const double* grid, const int64_t n[3], int levels, int l
   grid_ext(&gg, level, m);
   int64_t p[3] = {g[0] / s, g[1] / s, g[2] / s};
   if (level == 1) return base_pred_f64(grid, n, s, m, p, axis, t);
-  return level_pred_f64(grid, n, s, m, p);
+  return level_pred_f64(grid, n, s, m, p, ORA_PRED_CUBIC);
+}
+
+double ora_predict_mode_f64(const double* grid, const int64_t n[3], int levels, int level,
+                            const int64_t g[3], int predictor) {
+  geom gg;
+  for (int a = 0; a < 3; a++) { gg.n[a] = n[a]; gg.b[a] = 1; }
+  gg.L = levels;
+  if (level < 2 || level > levels) return 0.0;
+  int64_t m[3], s = stride_of(&gg, level);
+  grid_ext(&gg, level, m);
+  int64_t p[3] = {g[0] / s, g[1] / s, g[2] / s};
+  return level_pred_f64(grid, n, s, m, p, predictor);
 }
 
 float ora_predict_f32(const float* grid, const int64_t n[3], int levels, int level,
@@ -1079,5 +1108,5 @@ float ora_predict_f32(const float* grid, const int64_t n[3], int levels, int lev
   grid_ext(&gg, level, m);
   int64_t p[3] = {g[0] / s, g[1] / s, g[2] / s};
   if (level == 1) return base_pred_f32(grid, n, s, m, p, axis, t);
-  return level_pred_f32(grid, n, s, m, p);
+  return level_pred_f32(grid, n, s, m, p, ORA_PRED_CUBIC);
 }

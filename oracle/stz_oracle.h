@@ -78,7 +78,17 @@ typedef struct {
   int max_code_len;   /* Huffman length limit, 1..24 */
   int brick[3];       /* chunk brick (bz, by, bx) in sub-block cells */
   int nsub;           /* sub-chunks per chunk: 1, 2, 4 or 8 */
+  /* Prediction of levels 2..L (the ablation of Sec. 3.1, Fig. 2):
+   * ORA_PRED_CUBIC  = opt. 4, Eqs. 6-8 (the method; default),
+   * ORA_PRED_LINEAR = opt. 2, multi-linear Eqs. 3-5,
+   * ORA_PRED_DIRECT = opt. 1, Eq. 1 (the coarse point at the cell). */
+  int predictor;
+  /* Adaptive bound of Sec. 3.1 opt. 5: eb_l = eb_{l+1} / eb_ratio.  0 means
+   * the paper's 2.5; 1 switches the adaptive bound off. */
+  double eb_ratio;
 } ora_params;
+
+enum { ORA_PRED_CUBIC = 0, ORA_PRED_LINEAR = 1, ORA_PRED_DIRECT = 2 };
 
 /* Upper bound on the container size for the given parameters. */
 size_t ora_compress_bound(const ora_params* p);
@@ -138,6 +148,9 @@ int ora_huffman_lengths(const uint64_t* freq, int nsym, int max_len,
  * base coder's 1D rule.  g is the point in field coordinates.  For tests. */
 double ora_predict_f64(const double* grid, const int64_t n[3], int levels,
                        int level, const int64_t g[3], int axis, int64_t t);
+/* The same for levels >= 2 with a chosen predictor (ORA_PRED_*). */
+double ora_predict_mode_f64(const double* grid, const int64_t n[3], int levels,
+                            int level, const int64_t g[3], int predictor);
 float ora_predict_f32(const float* grid, const int64_t n[3], int levels,
                       int level, const int64_t g[3], int axis, int64_t t);
 
