@@ -62,6 +62,10 @@ def parse_args():
     p.add_argument("--serve-size", type=int, default=1024)
     p.add_argument("--serve-requests", type=int, default=1000, help="requests per rate")
     p.add_argument("--serve-rates", default="1000,5000,10000,50000")
+    p.add_argument("--no-bounds", action="store_true", help="skip the four-bound section")
+    p.add_argument("--no-large", action="store_true",
+                   help="skip the 1024^3 f32 / 768^3 f64 section")
+    p.add_argument("--no-ablation", action="store_true", help="skip the predictor ablation")
     return p.parse_args()
 
 
@@ -220,9 +224,11 @@ def run_ours(args, rank, world, local_rank):
         if ev:
             ev[3].record(stream)
         stz.decompress_region(comp, blo, bhi, 3, out=box_out, workspace=ws, meta=meta)
-        stz.decompress_region(comp, slo, shi, 3, out=slab_out, workspace=ws, meta=meta)
         if ev:
             ev[4].record(stream)
+        stz.decompress_region(comp, slo, shi, 3, out=slab_out, workspace=ws, meta=meta)
+        if ev:
+            ev[5].record(stream)
         return comp
 
     dist = world > 1
@@ -240,7 +246,7 @@ def run_ours(args, rank, world, local_rank):
 
     clocks = ClockSampler(_gpu_uuid(local_rank))
     clocks.start()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     launches0 = stz.launch_count()
     barrier()
     torch.cuda.synchronize()
@@ -268,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
         stz.profile_enable(False)
         kernels = stz.profile_read()
     ms_step = reduce_max(ms_step, dev)
-    ops = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in evs])
+    ops = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(5)] for e in evs])
     op_ms = ops.mean(axis=0)
 
     # region-decode latency distribution (synchronous calls, host clock)
@@ -488,27 +494,188 @@ def run_served(args, dev):
     free, _ = torch.cuda.mem_get_info(dev)
     budget = int(min(16 << 30, free // 4))
     srv = serve.Server(comps, budget_bytes=budget, max_edge=256, max_slots=32)
+    # the same loop with one slot: requests one after another, with the same
+    # cached level-1 grids and parsed headers -- isolates what the overlap of
+    # requests (continuous batching) adds beyond the caching
+    srv1 = serve.Server(comps, budget_bytes=budget, max_edge=256, max_slots=1)
     reg_out = torch.empty(256 ** 3 * 4, dtype=torch.uint8, device=dev)
     rates = [float(r) for r in args.serve_rates.split(",") if r]
     # warm both paths
     warm = serve.poisson_requests([shape] * len(comps), 20, 1e5, synth.seed_for(5, 99))
     srv.run(warm)
+    srv1.run(warm)
     serve.serial(comps, warm, ws, reg_out, realtime=False)
     per_rate = []
     for k, rate in enumerate(rates):
         reqs = serve.poisson_requests([shape] * len(comps), args.serve_requests, rate,
                                       synth.seed_for(5, 200 + k))
         res, wall = srv.run(reqs)
+        cres, cwall = srv1.run(reqs)
         sres, swall = serve.serial(comps, reqs, ws, reg_out)
         per_rate.append({"rate_rps": rate, "served": serve.latency_stats(res, wall),
+                         "serial_cached": serve.latency_stats(cres, cwall),
                          "serial": serve.latency_stats(sres, swall)})
     out = {"workload": f"{len(comps)} resident {size}^3 f32 k^-5/3 GRFs (rel eb 1e-3); "
                        "Poisson requests, box edge U[16,256] per axis, level U{1,2,3}",
            "resident_gb": round(resident / 1e9, 3), "raw_gb": round(raw / 1e9, 3),
            "slots": srv.nslots, "budget_gb": round(budget / 1e9, 2), "per_rate": per_rate}
-    del srv, comps, ws, reg_out
+    del srv, srv1, comps, ws, reg_out
     torch.cuda.empty_cache()
     return out
+
+
+# ------------------------------------------------- further timed workloads
+def _time_ms(fn, reps=5, warm=2):
+    """Median device time of fn() over `reps` calls (CUDA events on the
+    current stream, after `warm` untimed calls)."""
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def _psnr(x, y) -> float:
+    """20 log10(max - min) - 10 log10(MSE), in float64 (the paper uses PSNR
+    without defining it)."""
+    import torch
+
+    xd = x.double()
+    mse = float(((xd - y.double()) ** 2).mean())
+    rng = float(xd.max() - xd.min())
+    return float("inf") if mse == 0 else 20 * np.log10(rng) - 10 * np.log10(mse)
+
+
+def run_bounds(args, dev, field, peak):
+    """The 512^3 field at every relative bound of its workload: compress and
+    full-decode rates, compression ratio, PSNR and the largest error."""
+    import torch
+
+    from paper_2509_01626_gb300 import stz
+
+    shape = tuple(field.shape)
+    ws = stz.alloc_workspace(shape, torch.float32, dev)
+    out = torch.empty(stz.compress_bound(shape, torch.float32), dtype=torch.uint8, device=dev)
+    full = torch.empty_like(field)
+    fb = field.numel() * 4
+    meta = {"shape": shape, "dtype": torch.float32, "ndim": 3, "levels": 3}
+    rows = []
+    for eb in (1e-2, 1e-3, 1e-4, 1e-5):
+        comp = stz.compress(field, eb, "rel", out=out, workspace=ws)
+        cms = _time_ms(lambda: stz.compress(field, eb, "rel", out=out, workspace=ws))
+        dms = _time_ms(lambda: stz.decompress_full(comp, out=full, workspace=ws, meta=meta))
+        y = stz.decompress_full(comp, out=full, workspace=ws, meta=meta)
+        ea = stz.info(comp)["eb_abs"]
+        err = float((y.double() - field.double()).abs().max())
+        rows.append({"eb": eb, "compress_gbs": round(fb / cms / 1e6, 1),
+                     "decompress_gbs": round(fb / dms / 1e6, 1),
+                     "compress_frac": round(fb / cms / 1e6 / peak, 4),
+                     "decompress_frac": round(fb / dms / 1e6 / peak, 4),
+                     "cr": round(fb / comp.numel(), 3), "psnr_db": round(_psnr(field, y), 2),
+                     "max_err_over_eb": round(err / ea, 4)})
+    del ws, out, full
+    torch.cuda.empty_cache()
+    return rows
+
+
+def run_large(args, dev, peak):
+    """1024^3 f32 k^-5/3 turbulence-like field and 768^3 f64 smooth field at
+    relative bound 1e-4: compress, full decode and decode to each progressive
+    level; the f32 field also with four levels (Sec. 3.2)."""
+    import torch
+
+    from paper_2509_01626_gb300 import stz, synth
+
+    out_rows = []
+    cases = [("1024^3 f32 GRF k^-5/3", lambda: synth.grf(
+                 (1024,) * 3, synth.seed_for(4, 0), slope=-5.0 / 3.0, lognormal_sigma=None,
+                 dtype=np.float32, device=str(dev), white_source="torch", as_tensor=True), (3, 4)),
+             ("768^3 f64 smooth", lambda: synth.sinusoids_device(
+                 (768,) * 3, synth.seed_for(4, 1), n_terms=4, fmin=1.0, fmax=3.0, noise=0.0,
+                 dtype=np.float64, device=str(dev)), (3,))]
+    for name, gen, levels in cases:
+        x = gen()
+        shape = tuple(x.shape)
+        fb = x.numel() * x.element_size()
+        for L in levels:
+            ws = stz.alloc_workspace(shape, x.dtype, dev, L)
+            out = torch.empty(stz.compress_bound(shape, x.dtype, L), dtype=torch.uint8,
+                              device=dev)
+            full = torch.empty_like(x)
+            comp = stz.compress(x, 1e-4, "rel", out=out, workspace=ws, levels=L)
+            meta = {"shape": shape, "dtype": x.dtype, "ndim": 3, "levels": L}
+            cms = _time_ms(lambda: stz.compress(x, 1e-4, "rel", out=out, workspace=ws, levels=L),
+                           reps=3)
+            dms = _time_ms(lambda: stz.decompress_full(comp, out=full, workspace=ws, meta=meta),
+                           reps=3)
+            prog = {}
+            for k in range(1, L):
+                pk = torch.empty(x.numel() // (8 ** (L - k)) + 8 ** L, dtype=x.dtype, device=dev)
+                prog[str(k)] = round(_time_ms(lambda: stz.decompress_progressive(
+                    comp, k, out=pk, workspace=ws, meta=meta), reps=3), 4)
+                del pk
+            out_rows.append({"field": name, "levels": L, "eb": 1e-4,
+                             "compress_ms": round(cms, 3), "decompress_ms": round(dms, 3),
+                             "compress_gbs": round(fb / cms / 1e6, 1),
+                             "decompress_gbs": round(fb / dms / 1e6, 1),
+                             "compress_frac": round(fb / cms / 1e6 / peak, 4),
+                             "decompress_frac": round(fb / dms / 1e6 / peak, 4),
+                             "progressive_ms": prog, "cr": round(fb / comp.numel(), 3)})
+            del ws, out, full, comp
+            torch.cuda.empty_cache()
+        del x
+        torch.cuda.empty_cache()
+    return out_rows
+
+
+# the rate-distortion ablation of Sec. 3.1 (Fig. 2), in the paper's order; the
+# partition-only baseline (sub-blocks coded independently by SZ3) is not built
+ABLATION = [("direct prediction (opt. 1)", "direct", 2, 1.0),
+            ("multi-dim linear + quantize only (opts. 2-3)", "linear", 2, 1.0),
+            ("cubic multi-dim (opt. 4)", "cubic", 2, 1.0),
+            ("cubic + adaptive bound 2.5 (opt. 5)", "cubic", 2, 2.5),
+            ("3 levels + all (Sec. 3.2)", "cubic", 3, 2.5)]
+
+
+def run_ablation(args, dev, field512):
+    """Compression ratio and PSNR of each step of the Sec. 3.1 ablation on the
+    128^3 sinusoid field and the 512^3 log-normal GRF, at three bounds."""
+    import torch
+
+    from paper_2509_01626_gb300 import stz, synth
+
+    fields = [("128^3 f32 sinusoids", torch.from_numpy(
+                  synth.sinusoids((128,) * 3, synth.seed_for(1))).to(dev)),
+              ("512^3 f32 log-normal GRF", field512)]
+    rows = []
+    for fname, x in fields:
+        shape = tuple(x.shape)
+        fb = x.numel() * 4
+        for label, pred, L, ratio in ABLATION:
+            ws = stz.alloc_workspace(shape, torch.float32, dev, L)
+            out = torch.empty(stz.compress_bound(shape, torch.float32, L), dtype=torch.uint8,
+                              device=dev)
+            full = torch.empty_like(x)
+            for eb in (1e-2, 1e-3, 1e-4):
+                comp = stz.compress(x, eb, "rel", out=out, workspace=ws, levels=L,
+                                    predictor=pred, eb_ratio=ratio)
+                y = stz.decompress_full(comp, out=full, workspace=ws)
+                rows.append({"field": fname, "step": label, "predictor": pred, "levels": L,
+                             "eb_ratio": ratio, "eb": eb, "cr": round(fb / comp.numel(), 3),
+                             "psnr_db": round(_psnr(x, y), 2)})
+            del ws, out, full
+            torch.cuda.empty_cache()
+    return rows
 
 
 # --------------------------------------------------------------- oracle arm
@@ -638,7 +805,28 @@ def main():
                     "traffic": None if ratio is None else int(ratio * nbytes / cnt),
                     "algorithmic_bytes_per_launch": int(nbytes / cnt),
                     "launches_per_step": round(cnt / args.steps, 2)}
+    # the metric's own figures: each operation's input GB/s against the peak
+    op_rates = {}
+    for name, ms in (("compress", op[0]), ("decompress_full", op[1])):
+        gbs = fb / (ms * 1e-3) / 1e9
+        op_rates[name] = {"gbs": round(gbs, 2), "ms": round(float(ms), 4),
+                          "frac_of_hbm": round(gbs / peak, 4)}
+    op_rates["progressive_levels_1_2_ms"] = round(float(op[2]), 4)
+    op_rates["box_64cube_ms"] = round(float(op[3]), 4)
+    op_rates["slice_512sq_ms"] = round(float(op[4]), 4)
+    op_rates["region_p99_ms"] = round(float(np.percentile(r["lat"], 99)), 4)
+    if roofline is not None:
+        roofline["ops"] = op_rates
     dev = torch.device("cuda", local_rank)
+    bounds = large = ablation = None
+    if rank == 0 and not (args.no_bounds and args.no_ablation):
+        field = torch.from_numpy(r["x_host"]).to(dev)
+        bounds = None if args.no_bounds else run_bounds(args, dev, field, peak)
+        ablation = None if args.no_ablation else run_ablation(args, dev, field)
+        del field
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_large and args.size >= 512:
+        large = run_large(args, dev, peak)
     batched = None if args.no_batch else run_batched(args, dev)
     served = None if args.no_serve else run_served(args, dev)
     cpu = None
@@ -657,13 +845,15 @@ def main():
         "compress_frac_of_hbm": round(fb / (op[0] * 1e-3) / 1e9 / peak, 4),
         "decompress_frac_of_hbm": round(fb / (op[1] * 1e-3) / 1e9 / peak, 4),
         "progressive_ms_levels_1_2": round(float(op[2]), 4),
-        "box_and_slice_ms": round(float(op[3]), 4),
+        "box_ms": round(float(op[3]), 4),
+        "slice_ms": round(float(op[4]), 4),
         "region_latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                               "p99": round(float(np.percentile(lat, 99)), 4),
                               "n": int(lat.size), "edges": "16-256", "levels": "1-3"},
         "compression_ratio": round(fb / r["comp_bytes"], 3),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": r["e2e"],
         "gpu_launches": int(r["launches"]), "clocks": r["clk"], "kernels": breakdown[:12],
+        "bounds": bounds, "large": large, "ablation": ablation,
         "batched": batched, "served": served,
     }
     print(json.dumps(line), flush=True)

@@ -95,6 +95,44 @@ int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype
                  stz_eb_mode eb_mode, double eb, void* out_dev, size_t out_cap,
                  size_t* out_bytes, void* ws_dev, size_t ws_bytes, void* stream);
 
+/*
+ * Options of stz_compress_ex (NULL or zeroed fields: the method as the paper
+ * defines it -- three levels, cubic prediction, adaptive bound ratio 2.5).
+ *
+ *   levels     L, 1..6 (0: 3).  Sec. 3.2: three levels; more for very large
+ *              fields ("4-level (or higher)" for e.g. 4096^3), fewer for small
+ *              ones.  Level 1 is the stride-2^(L-1) grid.
+ *   predictor  prediction of levels 2..L, the ablation of Sec. 3.1 (Fig. 2):
+ *              STZ_PRED_CUBIC (opt. 4, Eqs. 6-8; the method), STZ_PRED_LINEAR
+ *              (opt. 2, multi-linear Eqs. 3-5), STZ_PRED_DIRECT (opt. 1,
+ *              Eq. 1: the coarse point of the cell).  The two ablation
+ *              predictors run in a general (slower) kernel.
+ *   eb_ratio   adaptive bound of Sec. 3.1 opt. 5: eb_l = eb_{l+1} / eb_ratio,
+ *              in [1, 64] (0: 2.5; 1: the same bound on every level).
+ *
+ * The container records all three; every decompression call reads them.
+ */
+typedef enum { STZ_PRED_CUBIC = 0, STZ_PRED_LINEAR = 1, STZ_PRED_DIRECT = 2 } stz_predictor;
+
+typedef struct {
+  int levels;
+  stz_predictor predictor;
+  double eb_ratio;
+} stz_compress_opts;
+
+/* stz_compress_bound / stz_workspace_size for a given level count L (0: 3);
+ * the workspace then suffices for every decompression of such a container. */
+size_t stz_compress_bound_ex(const int64_t* dims, int ndim, stz_dtype dtype, int levels);
+size_t stz_workspace_size_ex(const int64_t* dims, int ndim, stz_dtype dtype, int levels);
+
+/* stz_compress with options (opts may be NULL); ws_bytes >=
+ * stz_workspace_size_ex(dims, ndim, dtype, opts->levels).  Out-of-range
+ * options return STZ_ERR_ARG. */
+int stz_compress_ex(const void* field_dev, const int64_t* dims, int ndim, stz_dtype dtype,
+                    stz_eb_mode eb_mode, double eb, const stz_compress_opts* opts,
+                    void* out_dev, size_t out_cap, size_t* out_bytes, void* ws_dev,
+                    size_t ws_bytes, void* stream);
+
 /* Header of a container (host or device memory; comp_on_device selects). */
 typedef struct {
   stz_dtype dtype;

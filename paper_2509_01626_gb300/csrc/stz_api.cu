@@ -155,7 +155,9 @@ static WsPlan plan_compress(const Geo& g) {
   o += al256(sizeof(DevParams));
   w.range_part = o;
   o += al256(16 * (size_t)kRangeMaxBlocks);
-  for (int l = 1; l < g.L; l++) {
+  // reconstructed grids of levels 1..L-1 (level 1's also when L = 1: its
+  // passes predict from it)
+  for (int l = 1; l < (g.L > 1 ? g.L : 2); l++) {
     int64_t m[3];
     grid_extent(g.n, g.L, l, m);
     w.grid[l] = o;
@@ -228,7 +230,7 @@ static size_t bound_of(const Geo& g) {
 
 // ------------------------------------------------------------ header parsing
 struct Hdr {
-  int dtype, ndim, L, eb_mode, maxlen, R, ns, nsub;
+  int dtype, ndim, L, eb_mode, maxlen, R, ns, nsub, pred;
   int b[3];
   int64_t n[3];
   double eb, eb_abs, two_eb[kMaxLevels + 1];
@@ -288,7 +290,10 @@ static int parse_hdr(const uint8_t* h, size_t avail, size_t comp_bytes, Hdr* H) 
   H->eb = rdf64(h + 56);
   H->eb_abs = rdf64(h + 64);
   H->total = rd64(h + 88);
+  H->pred = h[200];
   if (H->dtype != STZ_F32 && H->dtype != STZ_F64) return STZ_ERR_CORRUPT;
+  if (H->pred != kPredCubic && H->pred != kPredLinear && H->pred != kPredDirect)
+    return STZ_ERR_CORRUPT;
   if (H->ndim != 2 && H->ndim != 3) return STZ_ERR_CORRUPT;
   if (H->L < 1 || H->L > kMaxLevels) return STZ_ERR_CORRUPT;
   if (H->eb_mode != STZ_EB_ABS && H->eb_mode != STZ_EB_REL) return STZ_ERR_CORRUPT;
@@ -328,6 +333,11 @@ static int parse_hdr(const uint8_t* h, size_t avail, size_t comp_bytes, Hdr* H) 
     if (sh.size > H->total - e.sect_off) return STZ_ERR_CORRUPT;
   }
   if (H->R != kRadius || H->maxlen > kMaxCodeLen) return STZ_ERR_ARG;
+  {
+    int64_t m1[3];  // the level-1 grid is indexed in 32 bits
+    grid_extent(H->n, H->L, 1, m1);
+    if (m1[0] * m1[1] * m1[2] >= ((int64_t)1 << 31)) return STZ_ERR_ARG;
+  }
   {
     int64_t tv = 1;
     for (int a = 0; a < 3; a++) tv *= H->b[a] + 3;
@@ -512,9 +522,19 @@ __global__ void k_result(const unsigned long long* __restrict__ total,
 // Argument checks of stz_compress; fills the job (geometry, workspace plan).
 int compress_check(const void* field_dev, const int64_t* dims, int ndim, int dtype, int eb_mode,
                    double eb, void* out_dev, size_t out_cap, void* ws_dev, size_t ws_bytes,
-                   CompressJob* j) {
+                   CompressJob* j, const stz_compress_opts* opts) {
   int64_t n[3];
   if (dims3(dims, ndim, n) != STZ_OK) return STZ_ERR_ARG;
+  int L = kLevels, pred = kPredCubic;
+  double ratio = 2.5;
+  if (opts) {
+    if (opts->levels != 0) L = opts->levels;
+    pred = (int)opts->predictor;
+    if (opts->eb_ratio != 0.0) ratio = opts->eb_ratio;
+  }
+  if (L < 1 || L > kMaxLevels) return STZ_ERR_ARG;
+  if (pred != kPredCubic && pred != kPredLinear && pred != kPredDirect) return STZ_ERR_ARG;
+  if (!(ratio >= 1.0 && ratio <= 64.0)) return STZ_ERR_ARG;
   if (dtype != STZ_F32 && dtype != STZ_F64) return STZ_ERR_ARG;
   if (eb_mode != STZ_EB_ABS && eb_mode != STZ_EB_REL) return STZ_ERR_ARG;
   if (!(eb > 0.0) || !isfinite(eb)) return STZ_ERR_ARG;
@@ -522,8 +542,16 @@ int compress_check(const void* field_dev, const int64_t* dims, int ndim, int dty
   if (((uintptr_t)field_dev % 16) || ((uintptr_t)out_dev % 8) || ((uintptr_t)ws_dev % 256))
     return STZ_ERR_ARG;
   memset(j, 0, sizeof(*j));
-  make_geo(n, ndim, dtype, kLevels, default_brick(ndim), &j->g);
+  make_geo(n, ndim, dtype, L, default_brick(ndim), &j->g);
+  {
+    // the level-1 grid (with L = 1 the whole field) is indexed in 32 bits
+    int64_t m1[3];
+    grid_extent(n, L, 1, m1);
+    if (m1[0] * m1[1] * m1[2] >= ((int64_t)1 << 31)) return STZ_ERR_ARG;
+  }
   if (ws_bytes < plan_compress(j->g).total) return STZ_ERR_CAPACITY;
+  j->pred = pred;
+  j->eb_ratio = ratio;
   j->field = field_dev;
   j->eb_mode = eb_mode;
   j->eb = eb;
@@ -571,7 +599,8 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
     int nparts = 0;
     STZ_TRY(launch_range(field_dev, dtype, eb_mode == STZ_EB_REL ? vol(n) : 0, part, &nparts,
                          hist, (int64_t)g.nstreams * kAlphabet, chunk_out, g.total_chunks, st));
-    STZ_TRY(launch_params(dp, part, nparts, dtype, eb_mode, eb, g.L, kRadius, st));
+    STZ_TRY(launch_params(dp, part, nparts, dtype, eb_mode, eb, g.L, kRadius, j.eb_ratio, j.pred,
+                          st));
   }
   {
     BaseArgs a;
@@ -595,6 +624,7 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
     memset(&a, 0, sizeof(a));
     a.geo = g;
     a.level = l;
+    a.pred = j.pred;
     a.dp = dp;
     a.field = field_dev;
     int64_t M[3], m[3];
@@ -650,10 +680,10 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
 // fixed; the field's current contents are read at each replay.
 namespace {
 struct CompKey {
-  int dev, ndim, dtype, eb_mode;
+  int dev, ndim, dtype, eb_mode, levels, pred;
   const void* field;
   int64_t dims[3];
-  double eb;
+  double eb, eb_ratio;
   void* out;
   size_t out_cap;
   void* ws;
@@ -701,6 +731,9 @@ int compress_graph_launch(const CompressJob& j, const void* field, const int64_t
   key.field = field;
   for (int a = 0; a < 3; a++) key.dims[a] = dims[a];
   key.eb = eb;
+  key.levels = j.g.L;
+  key.pred = j.pred;
+  key.eb_ratio = j.eb_ratio;
   key.out = out;
   key.out_cap = out_cap;
   key.ws = ws;
@@ -796,19 +829,29 @@ const char* stz_strerror(int code) {
 
 const char* stz_version(void) { return "stz-gb300 1.0 (sm_103a)"; }
 
-size_t stz_compress_bound(const int64_t* dims, int ndim, stz_dtype dtype) {
+size_t stz_compress_bound_ex(const int64_t* dims, int ndim, stz_dtype dtype, int levels) {
   int64_t n[3];
-  if (dims3(dims, ndim, n) != STZ_OK || (dtype != STZ_F32 && dtype != STZ_F64)) return 0;
+  if (levels == 0) levels = kLevels;
+  if (dims3(dims, ndim, n) != STZ_OK || (dtype != STZ_F32 && dtype != STZ_F64) || levels < 1 ||
+      levels > kMaxLevels)
+    return 0;
   Geo g;
-  make_geo(n, ndim, dtype, kLevels, default_brick(ndim), &g);
+  make_geo(n, ndim, dtype, levels, default_brick(ndim), &g);
   return bound_of(g);
 }
 
-size_t stz_workspace_size(const int64_t* dims, int ndim, stz_dtype dtype) {
+size_t stz_compress_bound(const int64_t* dims, int ndim, stz_dtype dtype) {
+  return stz_compress_bound_ex(dims, ndim, dtype, kLevels);
+}
+
+size_t stz_workspace_size_ex(const int64_t* dims, int ndim, stz_dtype dtype, int levels) {
   int64_t n[3];
-  if (dims3(dims, ndim, n) != STZ_OK || (dtype != STZ_F32 && dtype != STZ_F64)) return 0;
+  if (levels == 0) levels = kLevels;
+  if (dims3(dims, ndim, n) != STZ_OK || (dtype != STZ_F32 && dtype != STZ_F64) || levels < 1 ||
+      levels > kMaxLevels)
+    return 0;
   Geo g;
-  make_geo(n, ndim, dtype, kLevels, default_brick(ndim), &g);
+  make_geo(n, ndim, dtype, levels, default_brick(ndim), &g);
   WsPlan w = plan_compress(g);
   DecPlan P;
   int64_t lo[3] = {0, 0, 0};
@@ -816,14 +859,19 @@ size_t stz_workspace_size(const int64_t* dims, int ndim, stz_dtype dtype) {
   return w.total > P.total ? w.total : P.total;
 }
 
-int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype dtype,
-                 stz_eb_mode eb_mode, double eb, void* out_dev, size_t out_cap,
-                 size_t* out_bytes, void* ws_dev, size_t ws_bytes, void* stream) {
+size_t stz_workspace_size(const int64_t* dims, int ndim, stz_dtype dtype) {
+  return stz_workspace_size_ex(dims, ndim, dtype, kLevels);
+}
+
+int stz_compress_ex(const void* field_dev, const int64_t* dims, int ndim, stz_dtype dtype,
+                    stz_eb_mode eb_mode, double eb, const stz_compress_opts* opts,
+                    void* out_dev, size_t out_cap, size_t* out_bytes, void* ws_dev,
+                    size_t ws_bytes, void* stream) {
   if (!out_bytes) return STZ_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   CompressJob j;
   int rc = compress_check(field_dev, dims, ndim, dtype, eb_mode, eb, out_dev, out_cap, ws_dev,
-                          ws_bytes, &j);
+                          ws_bytes, &j, opts);
   if (rc != STZ_OK) return rc;
   CompressDev d;
   // repeated calls with the same arguments replay one captured graph (no
@@ -846,6 +894,13 @@ int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype
   prof_add_bytes("k_pack", 4.0 * (double)r[1]);
   if (r[2] & kStatCapacity) return STZ_ERR_CAPACITY;
   return STZ_OK;
+}
+
+int stz_compress(const void* field_dev, const int64_t* dims, int ndim, stz_dtype dtype,
+                 stz_eb_mode eb_mode, double eb, void* out_dev, size_t out_cap,
+                 size_t* out_bytes, void* ws_dev, size_t ws_bytes, void* stream) {
+  return stz_compress_ex(field_dev, dims, ndim, dtype, eb_mode, eb, nullptr, out_dev, out_cap,
+                         out_bytes, ws_dev, ws_bytes, stream);
 }
 
 int stz_info(const void* comp, size_t comp_bytes, int comp_on_device, stz_info_t* info) {
@@ -1269,6 +1324,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
       memset(&a, 0, sizeof(a));
       a.geo = g;
       a.level = j;
+      a.pred = H.pred;
       a.dp = dp;
       a.coarse = (j == 2) ? (const void*)g1buf : (const void*)(ws + P.grid[j - 1]);
       a.fine = (j == level) ? out_dev : (void*)(ws + P.grid[j]);

@@ -145,9 +145,14 @@ struct DevParams {
   float inv2eb_f[kMaxLevels + 1], two_eb_f[kMaxLevels + 1], ebc_f[kMaxLevels + 1];
   double inv2eb_d[kMaxLevels + 1], two_eb_dd[kMaxLevels + 1], ebc_d[kMaxLevels + 1];
   unsigned long long range_lo, range_hi;  // order-preserving keys of min / max
+  double eb_ratio;    // eb_l = eb_{l+1} / eb_ratio (Sec. 3.1 opt. 5)
   uint32_t status;
-  uint32_t pad;
+  uint32_t pred;      // predictor of levels 2..L (kPred*)
 };
+
+// Predictor of levels 2..L (the ablation of Sec. 3.1): opt. 4 cubic Eqs. 6-8
+// (the method), opt. 2 multi-linear Eqs. 3-5, opt. 1 direct Eq. 1.
+constexpr int kPredCubic = 0, kPredLinear = 1, kPredDirect = 2;
 
 // ---- correctly rounded single operations (no contraction into FMA) ----
 __device__ __forceinline__ float op_add(float a, float b) { return __fadd_rn(a, b); }

@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(kLayoutThreads) k_layout(
     put_f64(out + 96 + 8 * (l - 1), dp->eb_level[l]);
     put_f64(out + 144 + 8 * (l - 1), dp->two_eb_d[l]);
   }
-  put_f64(out + 192, 2.5);
+  put_f64(out + 192, dp->eb_ratio);
+  out[200] = (uint8_t)dp->pred;
 }
 
 int launch_layout(const Geo& g, const DevParams* dp, int eb_mode,

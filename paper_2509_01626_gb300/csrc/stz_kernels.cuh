@@ -13,9 +13,12 @@ constexpr int kRangeMaxBlocks = 2048;
 int launch_range(const void* field, int dtype, int64_t n, unsigned long long* part, int* nparts,
                  uint32_t* z0, int64_t nz0, uint32_t* z1, int64_t nz1, cudaStream_t s);
 // Reduces the range partials (relative mode) and writes the whole of *dp:
-// range, eb_abs, per-level bounds, quantizer constants, status 0.
+// range, eb_abs, per-level bounds (eb_l = eb_abs / ratio^(L-l), the power
+// formed by repeated multiplication), quantizer constants, the predictor
+// and status 0.
 int launch_params(DevParams* dp, const unsigned long long* part, int nparts, int dtype,
-                  int eb_mode, double eb, int L, int R, cudaStream_t s);
+                  int eb_mode, double eb, int L, int R, double ratio, int pred,
+                  cudaStream_t s);
 
 // ---- stz_base.cu: level 1 (SZ3-style axis passes) ----
 struct BaseArgs {
@@ -43,6 +46,7 @@ int launch_base_nocoop(const BaseArgs& a, bool decode, cudaStream_t s);
 struct LevelArgs {
   Geo geo;
   int level;                  // l >= 2
+  int pred;                   // kPredCubic / kPredLinear / kPredDirect
   const DevParams* dp;
   const void* field;          // compress: input field
   const void* coarse;         // G_{l-1} reconstruction, box [clo, chi)
@@ -146,6 +150,8 @@ struct CompressJob {
   const void* field;
   int eb_mode;
   double eb;
+  int pred;          // predictor of levels 2..L
+  double eb_ratio;   // adaptive-bound ratio
   void* out;
   size_t out_cap;
   void* ws;
@@ -159,7 +165,7 @@ struct CompressDev {
 };
 int compress_check(const void* field_dev, const int64_t* dims, int ndim, int dtype, int eb_mode,
                    double eb, void* out_dev, size_t out_cap, void* ws_dev, size_t ws_bytes,
-                   CompressJob* j);
+                   CompressJob* j, const stz_compress_opts* opts = nullptr);
 int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, CompressDev* d);
 // stz_compress's launch sequence as a graph captured once per argument tuple
 // and replayed

@@ -55,7 +55,7 @@ __device__ __forceinline__ void do_point(const LevelArgs& a, const TileCtx& tc, 
   if (!DEC) {
     int sym = 0;
     if (v) {
-      T pred = level_predict<K>(tile, tc.base, st, g, tc.m);
+      T pred = level_predict<K>(tile, tc.base, st, g, tc.m, a.pred);
       const int64_t s = level_stride(geo.L, a.level);
       const T* f = (const T*)a.field;
       T x = f[((g[0] * s) * geo.n[1] + g[1] * s) * geo.n[2] + g[2] * s];
@@ -80,7 +80,7 @@ __device__ __forceinline__ void do_point(const LevelArgs& a, const TileCtx& tc, 
           atomicOr(a.status, kStatCorrupt);
         }
       } else {
-        T pred = level_predict<K>(tile, tc.base, st, g, tc.m);
+        T pred = level_predict<K>(tile, tc.base, st, g, tc.m, a.pred);
         val = dequantize(sym, pred, two_eb, kRadius);
       }
       ((T*)a.fine)[fidx] = val;
@@ -1031,7 +1031,10 @@ static int run_level(const LevelArgs& a, cudaStream_t s) {
   grid_extent(a.geo.n, a.geo.L, a.level - 1, M);
   const int64_t sl = level_stride(a.geo.L, a.level);
   const int64_t fe = (a.fhi[1] - a.flo[1]) * (a.fhi[2] - a.flo[2]);
-  const bool fast = a.geo.b[0] == kFBZ && a.geo.b[1] == kFBY && a.geo.b[2] == kFBX &&
+  // the fast interior and boundary kernels implement the cubic predictor;
+  // the ablation predictors run in the generic kernel
+  const bool fast = a.pred == kPredCubic && a.geo.b[0] == kFBZ && a.geo.b[1] == kFBY &&
+                    a.geo.b[2] == kFBX &&
                     2 * kFBZ * sl * a.geo.n[1] * a.geo.n[2] < ((int64_t)1 << 31) &&
                     2 * kFBZ * fe < ((int64_t)1 << 31);
   ShellGeo sh;

@@ -44,16 +44,22 @@ __device__ __forceinline__ int slot_coarse(int slot) { return slot == 0 ? 0 : (s
 // extent.  Interior: Eq. 6 / Eq. 7 / Eq. 8 by number of odd axes; otherwise
 // the separable product of the one-axis rules along the odd axes in the
 // order z, y, x (multi-linear Eqs. 3-5 where every rule is the midpoint).
+//
+// pred selects the ablation of Sec. 3.1: kPredLinear never takes the cubic
+// stencils (Eqs. 3-5 everywhere, the one-sided rules at the boundary);
+// kPredDirect is Eq. 1, the coarse value of the cell itself (t[base]).
 template <int K, typename T, typename I>
 __device__ __forceinline__ T level_predict(const T* __restrict__ t, I base, const I st[3],
-                                           const int64_t g[3], const int64_t m[3]) {
+                                           const int64_t g[3], const int64_t m[3],
+                                           int pred = kPredCubic) {
   constexpr int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
   constexpr int nodd = oz + oy + ox;
   constexpr int a0 = oz ? 0 : (oy ? 1 : 2);
   constexpr int a1 = nodd >= 2 ? (oz ? (oy ? 1 : 2) : 2) : 2;
   constexpr int a2 = 2;
   const I s0 = st[a0], s1 = st[a1], s2 = st[a2];
-  bool cub = g[a0] >= 3 && g[a0] + 3 < m[a0];
+  if (pred == kPredDirect) return t[base];
+  bool cub = pred == kPredCubic && g[a0] >= 3 && g[a0] + 3 < m[a0];
   if (nodd >= 2) cub = cub && g[a1] >= 3 && g[a1] + 3 < m[a1];
   if (nodd == 3) cub = cub && g[a2] >= 3 && g[a2] + 3 < m[a2];
   if (cub) {

@@ -121,7 +121,7 @@ __device__ __forceinline__ float rz_float(double v) { return __double2float_rz(v
 __global__ void __launch_bounds__(256) k_params(DevParams* dp,
                                                 const unsigned long long* __restrict__ part,
                                                 int nparts, int dtype, int eb_mode, double eb,
-                                                int L, int R) {
+                                                int L, int R, double ratio, int pred) {
   unsigned long long lo = ~0ull, hi = 0ull;
   if (eb_mode == STZ_EB_REL) {
     for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
@@ -166,6 +166,8 @@ __global__ void __launch_bounds__(256) k_params(DevParams* dp,
   }
   dp->eb = eb;
   dp->eb_abs = ea;
+  dp->eb_ratio = ratio;
+  dp->pred = (uint32_t)pred;
   dp->vmin = vmin;
   dp->vmax = vmax;
   for (int l = 0; l <= kMaxLevels; l++) {
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(256) k_params(DevParams* dp,
   }
   for (int l = 1; l <= L; l++) {
     double r = 1.0;
-    for (int k = 0; k < L - l; k++) r = __dmul_rn(r, 2.5);
+    for (int k = 0; k < L - l; k++) r = __dmul_rn(r, ratio);
     double ebl = __ddiv_rn(ea, r);
     dp->eb_level[l] = ebl;
     double two = __dmul_rn(2.0, ebl);
@@ -210,9 +212,9 @@ int launch_range(const void* field, int dtype, int64_t n, unsigned long long* pa
 }
 
 int launch_params(DevParams* dp, const unsigned long long* part, int nparts, int dtype,
-                  int eb_mode, double eb, int L, int R, cudaStream_t s) {
+                  int eb_mode, double eb, int L, int R, double ratio, int pred, cudaStream_t s) {
   ProfScope ps_("k_params", s);
-  k_params<<<1, 256, 0, s>>>(dp, part, nparts, dtype, eb_mode, eb, L, R);
+  k_params<<<1, 256, 0, s>>>(dp, part, nparts, dtype, eb_mode, eb, L, R, ratio, pred);
   return cuda_ok(cudaGetLastError());
 }
 

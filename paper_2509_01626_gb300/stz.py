@@ -58,6 +58,17 @@ class FieldJob(ctypes.Structure):
     ]
 
 
+class CompressOpts(ctypes.Structure):
+    """stz_compress_opts: level count, predictor, adaptive-bound ratio."""
+    _fields_ = [("levels", ctypes.c_int), ("predictor", ctypes.c_int),
+                ("eb_ratio", ctypes.c_double)]
+
+
+# predictors of levels 2..L (Sec. 3.1 ablation): opt. 4 cubic (the method),
+# opt. 2 multi-linear, opt. 1 direct
+PREDICTORS = {"cubic": 0, "linear": 1, "direct": 2}
+
+
 class BatchOpts(ctypes.Structure):
     """stz_batch_opts: launch arrangement of a batch (never changes bytes)."""
     _fields_ = [("lanes", ctypes.c_int), ("sm_share_den", ctypes.c_int),
@@ -90,6 +101,13 @@ def lib() -> ctypes.CDLL:
         L.stz_workspace_size.argtypes = [i64p, ctypes.c_int, ctypes.c_int]
         L.stz_compress.argtypes = [vp, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_double, vp, sz, ctypes.POINTER(sz), vp, sz, vp]
+        L.stz_compress_ex.argtypes = [vp, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.POINTER(CompressOpts), vp, sz,
+                                      ctypes.POINTER(sz), vp, sz, vp]
+        L.stz_compress_bound_ex.restype = sz
+        L.stz_compress_bound_ex.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.stz_workspace_size_ex.restype = sz
+        L.stz_workspace_size_ex.argtypes = [i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.stz_info.argtypes = [vp, sz, ctypes.c_int, ctypes.POINTER(_Info)]
         L.stz_decompress_full.argtypes = [vp, sz, vp, sz, vp, sz, vp]
         L.stz_decompress_progressive.argtypes = [vp, sz, ctypes.c_int, vp, sz, i64p, vp, sz, vp]
@@ -148,37 +166,45 @@ def _check(rc: int, what: str):
         raise StzError(rc, what)
 
 
-def compress_bound(shape, dtype) -> int:
-    return int(lib().stz_compress_bound(_i64(shape), len(shape), _dt(dtype)))
+def compress_bound(shape, dtype, levels: int = 3) -> int:
+    return int(lib().stz_compress_bound_ex(_i64(shape), len(shape), _dt(dtype), int(levels)))
 
 
-def workspace_size(shape, dtype) -> int:
-    return int(lib().stz_workspace_size(_i64(shape), len(shape), _dt(dtype)))
+def workspace_size(shape, dtype, levels: int = 3) -> int:
+    return int(lib().stz_workspace_size_ex(_i64(shape), len(shape), _dt(dtype), int(levels)))
 
 
-def alloc_workspace(shape, dtype, device=None) -> torch.Tensor:
-    return torch.empty(workspace_size(shape, dtype), dtype=torch.uint8,
+def alloc_workspace(shape, dtype, device=None, levels: int = 3) -> torch.Tensor:
+    return torch.empty(workspace_size(shape, dtype, levels), dtype=torch.uint8,
                        device=device or torch.device("cuda"))
 
 
 def compress(field: torch.Tensor, eb: float, mode: str = "rel", out: torch.Tensor | None = None,
-             workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """stz_compress: returns the container as a uint8 view of `out`."""
+             workspace: torch.Tensor | None = None, stream=None, levels: int = 3,
+             predictor: str = "cubic", eb_ratio: float = 2.5) -> torch.Tensor:
+    """stz_compress (stz_compress_ex for other levels / predictors / bound
+    ratios): returns the container as a uint8 view of `out`."""
     if not field.is_cuda or not field.is_contiguous():
         raise ValueError("field must be a contiguous CUDA tensor")
     shape = tuple(field.shape)
     dt = _dt(field.dtype)
     if out is None:
-        out = torch.empty(compress_bound(shape, field.dtype), dtype=torch.uint8, device=field.device)
+        out = torch.empty(compress_bound(shape, field.dtype, levels), dtype=torch.uint8,
+                          device=field.device)
     if workspace is None:
-        workspace = alloc_workspace(shape, field.dtype, field.device)
+        workspace = alloc_workspace(shape, field.dtype, field.device, levels)
     nbytes = ctypes.c_size_t(0)
-    rc = lib().stz_compress(ctypes.c_void_p(field.data_ptr()), _i64(shape), len(shape), dt,
-                            EB_REL if mode == "rel" else EB_ABS, float(eb),
-                            ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(nbytes),
-                            ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
-                            _stream(stream))
-    _check(rc, "stz_compress")
+    args = (ctypes.c_void_p(field.data_ptr()), _i64(shape), len(shape), dt,
+            EB_REL if mode == "rel" else EB_ABS, float(eb))
+    rest = (ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(nbytes),
+            ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream))
+    if levels == 3 and predictor == "cubic" and eb_ratio == 2.5:
+        rc = lib().stz_compress(*args, *rest)
+        _check(rc, "stz_compress")
+    else:
+        opts = CompressOpts(int(levels), PREDICTORS[predictor], float(eb_ratio))
+        rc = lib().stz_compress_ex(*args, ctypes.byref(opts), *rest)
+        _check(rc, "stz_compress_ex")
     return out[: nbytes.value]
 
 
@@ -227,7 +253,7 @@ def decompress_full(comp: torch.Tensor, out: torch.Tensor | None = None,
     if out is None:
         out = torch.empty(inf["shape"], dtype=inf["dtype"], device=comp.device)
     if workspace is None:
-        workspace = alloc_workspace(inf["shape"], inf["dtype"], comp.device)
+        workspace = alloc_workspace(inf["shape"], inf["dtype"], comp.device, inf["levels"])
     rc = lib().stz_decompress_full(ctypes.c_void_p(comp.data_ptr()), comp.numel(),
                                    ctypes.c_void_p(out.data_ptr()),
                                    out.numel() * out.element_size(),
@@ -246,7 +272,7 @@ def decompress_progressive(comp: torch.Tensor, level: int, out: torch.Tensor | N
     if out is None:
         out = torch.empty(shape, dtype=inf["dtype"], device=comp.device)
     if workspace is None:
-        workspace = alloc_workspace(inf["shape"], inf["dtype"], comp.device)
+        workspace = alloc_workspace(inf["shape"], inf["dtype"], comp.device, inf["levels"])
     od = (ctypes.c_int64 * 3)()
     rc = lib().stz_decompress_progressive(ctypes.c_void_p(comp.data_ptr()), comp.numel(),
                                           int(level), ctypes.c_void_p(out.data_ptr()),
@@ -273,7 +299,7 @@ def decompress_region(comp: torch.Tensor, lo, hi, level: int | None = None,
             n *= max(1, b - a)
         out = torch.empty(n, dtype=inf["dtype"], device=comp.device)
     if workspace is None:
-        workspace = alloc_workspace(inf["shape"], inf["dtype"], comp.device)
+        workspace = alloc_workspace(inf["shape"], inf["dtype"], comp.device, inf["levels"])
     od = (ctypes.c_int64 * 3)()
     rc = lib().stz_decompress_region(ctypes.c_void_p(comp.data_ptr()), comp.numel(), _i64(lo),
                                      _i64(hi), int(level), ctypes.c_void_p(out.data_ptr()),
