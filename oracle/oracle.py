@@ -16,7 +16,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "stz_oracle.c")]
+_SRC = [os.path.join(_HERE, "stz_oracle.c"), os.path.join(_HERE, "stz_oracle_roi.c")]
 _DEPS = _SRC + [os.path.join(_HERE, "stz_oracle_real.inc"), os.path.join(_HERE, "stz_oracle.h")]
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 
@@ -111,6 +111,10 @@ def lib():
         L.ora_predict_mode_f64.restype = ctypes.c_double
         L.ora_predict_mode_f64.argtypes = [vp, i64p, ctypes.c_int, ctypes.c_int, i64p,
                                            ctypes.c_int]
+        L.ora_roi_units.restype = ctypes.c_int64
+        L.ora_roi_units.argtypes = [i64p, i64p]
+        L.ora_roi_select.argtypes = [vp, ctypes.c_int, i64p, i64p, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, vp, vp, i64p]
         L.ora_stream_pos.restype = ctypes.c_int64
         L.ora_stream_pos.argtypes = [i64p, ctypes.POINTER(ctypes.c_int), i64p]
         _lib = L
@@ -304,6 +308,31 @@ def predict_mode(grid: np.ndarray, levels: int, level: int, g, predictor: str) -
     n = grid.shape if grid.ndim == 3 else (1,) + grid.shape
     return lib().ora_predict_mode_f64(grid.ctypes.data, _i64(n), levels, level, _i64(g),
                                       PREDICTORS[predictor])
+
+
+ROI_METRICS = {"range": 0, "max": 1}
+ROI_MODES = {"threshold": 0, "top": 1}
+
+
+def roi_select(field: np.ndarray, block, metric: str = "range", mode: str = "top",
+               value: float = 0.01):
+    """ROI selection (Sec. 3.3): (selected unit indices ascending, metric of
+    every unit).  block: (bz, by, bx) points ((by, bx) for 2D fields)."""
+    x = np.ascontiguousarray(field)
+    _, d3 = _dims3(x.shape)
+    b3 = tuple(block) if x.ndim == 3 else (1,) + tuple(block)
+    nu = int(lib().ora_roi_units(_i64(d3), _i64(b3)))
+    if nu < 1:
+        raise OracleError(ERR_ARG, "roi_select")
+    met = np.zeros(nu, dtype=np.float64)
+    sel = np.zeros(nu, dtype=np.int64)
+    ns = ctypes.c_int64(0)
+    rc = lib().ora_roi_select(x.ctypes.data, 0 if x.dtype == np.float32 else 1, _i64(d3), _i64(b3),
+                              ROI_METRICS[metric], ROI_MODES[mode], float(value), met.ctypes.data,
+                              sel.ctypes.data, ctypes.byref(ns))
+    if rc != OK:
+        raise OracleError(rc, "roi_select")
+    return sel[: ns.value].copy(), met
 
 
 def stream_pos(e, b, c) -> int:

@@ -154,6 +154,21 @@ double ora_predict_mode_f64(const double* grid, const int64_t n[3], int levels,
 float ora_predict_f32(const float* grid, const int64_t n[3], int levels,
                       int level, const int64_t g[3], int axis, int64_t t);
 
+/* ROI selection module (Sec. 3.3, last paragraph; stz_oracle_roi.c): per
+ * unit -- a block of block[3] points (z, y, x), clipped at the field's edge;
+ * a slice along an axis is a block spanning the other two axes -- the value
+ * range or the maximum of its finite values (-inf without one), then the
+ * units with metric >= value (ORA_ROI_THRESHOLD) or the ceil(value * nunits)
+ * largest, ties to the lower index (ORA_ROI_TOP, 0 < value <= 1).  sel
+ * receives the selected unit indices ascending (room for nunits), metric_out
+ * (may be NULL) every unit's metric. */
+enum { ORA_ROI_RANGE = 0, ORA_ROI_MAX = 1 };
+enum { ORA_ROI_THRESHOLD = 0, ORA_ROI_TOP = 1 };
+int64_t ora_roi_units(const int64_t dims[3], const int64_t block[3]);
+int ora_roi_select(const void* field, int dtype, const int64_t dims[3], const int64_t block[3],
+                   int metric, int mode, double value, double* metric_out, int64_t* sel,
+                   int64_t* nsel);
+
 /* Stream position (brick-major order) of cell c in a sub-block of extent e
  * with brick b.  For tests. */
 int64_t ora_stream_pos(const int64_t e[3], const int b[3], const int64_t c[3]);
