@@ -230,6 +230,46 @@ typedef struct {
 int stz_compress_batch(int n, const stz_field_job* jobs, unsigned long long* sizes_dev,
                        const stz_batch_opts* opts, void* stream);
 
+/* ---- ROI selection (Sec. 3.3, last paragraph) ----
+ * The paper's module that helps users pick the regions of interest to
+ * decompress: per slice or block of a field, the value range (suits
+ * interfaces between fluids) or the maximum (suits over-density halos), then
+ * the units whose metric reaches a threshold or the top x% of units.  It is
+ * meant for a progressive (coarse) decode of a field: the selected units,
+ * scaled by the level's stride, are boxes for stz_decompress_region.
+ *
+ * A unit is a block of block[] points, slowest axis first ({bz, by, bx};
+ * 2D: {by, bx}), clipped at the field's edge; units are numbered in raster
+ * order of (z / bz, y / by, x / bx).  A slice along an axis is the block of
+ * extent 1 along that axis spanning the others.
+ *
+ *   metric   STZ_ROI_RANGE: max - min of the unit's finite values (one
+ *            correctly rounded double subtraction); STZ_ROI_MAX: the
+ *            maximum.  A unit without a finite value has the metric -inf.
+ *            Non-finite values are ignored; -0 orders below +0.
+ *   mode     STZ_ROI_THRESHOLD: units with metric >= value;
+ *            STZ_ROI_TOP: the ceil(value * nunits) units (0 < value <= 1,
+ *            the product in double) with the largest metrics, equal metrics
+ *            taken by lower unit index.
+ *   sel_dev      device int64[sel_cap >= nunits]: the selected unit indices,
+ *                ascending
+ *   metric_dev   device double[nunits] receiving every unit's metric, or NULL
+ *   nsel         host: the number of selected units
+ *   ws_dev       device workspace of stz_roi_workspace_size() bytes
+ *
+ * Waits on the host once, at the end, for nsel.  The result equals the CPU
+ * oracle's bit for bit.  Units must number fewer than 2^31. */
+typedef enum { STZ_ROI_RANGE = 0, STZ_ROI_MAX = 1 } stz_roi_metric;
+typedef enum { STZ_ROI_THRESHOLD = 0, STZ_ROI_TOP = 1 } stz_roi_mode;
+
+/* Number of units (-1 on invalid arguments). */
+int64_t stz_roi_units(const int64_t* dims, int ndim, const int64_t* block);
+size_t stz_roi_workspace_size(const int64_t* dims, int ndim, const int64_t* block);
+int stz_roi_select(const void* field_dev, const int64_t* dims, int ndim, stz_dtype dtype,
+                   const int64_t* block, stz_roi_metric metric, stz_roi_mode mode, double value,
+                   int64_t* sel_dev, size_t sel_cap, double* metric_dev, int64_t* nsel,
+                   void* ws_dev, size_t ws_bytes, void* stream);
+
 /* ---- serving support (no counterpart in the paper) ----
  * A serving loop keeps containers resident and answers many region requests
  * without waiting on the host per request: it parses each container's header

@@ -10,8 +10,9 @@
  * the benchmark's CPU legs load it.
  *
  * Readings (the paper gives the idea, not the rules):
- *   - non-finite values are ignored; a unit without a finite value has the
- *     metric -infinity (never reaches a finite threshold, ranks last);
+ *   - non-finite values are ignored (and -0 orders below +0); a unit without
+ *     a finite value has the metric -infinity (never reaches a finite
+ *     threshold, ranks last);
  *   - range = (double)max - (double)min, one correctly rounded subtraction;
  *   - threshold mode selects metric >= threshold;
  *   - top mode selects k = ceil(fraction * nunits) units (fraction in (0, 1],
@@ -84,12 +85,14 @@ int ora_roi_select(const void* field, int dtype, const int64_t dims[3], const in
                                     : ((const double*)field)[i];
         if (!isfinite(v)) continue;
         int64_t u = ((z / block[0]) * nb[1] + y / block[1]) * nb[2] + x / block[2];
+        /* ties between the zeros are broken as -0 < +0, so that the result
+         * does not depend on the visiting order */
         if (!any[u]) {
           lo[u] = hi[u] = v;
           any[u] = 1;
         } else {
-          if (v < lo[u]) lo[u] = v;
-          if (v > hi[u]) hi[u] = v;
+          if (v < lo[u] || (v == lo[u] && signbit(v) && !signbit(lo[u]))) lo[u] = v;
+          if (v > hi[u] || (v == hi[u] && !signbit(v) && signbit(hi[u]))) hi[u] = v;
         }
       }
   for (int64_t u = 0; u < nu; u++) {

@@ -1,6 +1,7 @@
 // stz_api.cu -- the C ABI (include/stz.h): argument checks, workspace
 // planning, container header parsing and launch sequencing.  Every step of
 // the method runs in the kernels of the other translation units.
+#include <math.h>
 #include <stddef.h>
 #include <stdio.h>
 #include <string.h>
@@ -1523,6 +1524,79 @@ int stz_decompress_region(const void* comp_dev, size_t comp_bytes, const int64_t
   if (level < 1) return STZ_ERR_ARG;
   return decode_impl(comp_dev, comp_bytes, lo, hi, level, 0, out_dev, out_cap, out_dims, ws_dev,
                      ws_bytes, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------ ROI selection
+static int roi_geom(const int64_t* dims, int ndim, const int64_t* block, int64_t n[3],
+                    int64_t b[3], int64_t* nunits) {
+  if (!block || dims3(dims, ndim, n) != STZ_OK) return STZ_ERR_ARG;
+  if (ndim == 3) {
+    for (int a = 0; a < 3; a++) b[a] = block[a];
+  } else {
+    b[0] = 1;
+    b[1] = block[0];
+    b[2] = block[1];
+  }
+  int64_t nu = 1;
+  for (int a = 0; a < 3; a++) {
+    if (b[a] < 1) return STZ_ERR_ARG;
+    nu *= cdiv(n[a], b[a]);
+  }
+  if (nu >= ((int64_t)1 << 31)) return STZ_ERR_ARG;
+  *nunits = nu;
+  return STZ_OK;
+}
+
+int64_t stz_roi_units(const int64_t* dims, int ndim, const int64_t* block) {
+  int64_t n[3], b[3], nu;
+  return roi_geom(dims, ndim, block, n, b, &nu) == STZ_OK ? nu : -1;
+}
+
+size_t stz_roi_workspace_size(const int64_t* dims, int ndim, const int64_t* block) {
+  int64_t n[3], b[3], nu;
+  if (roi_geom(dims, ndim, block, n, b, &nu) != STZ_OK) return 0;
+  return 3 * al256(8 * (size_t)nu) + 256;
+}
+
+int stz_roi_select(const void* field_dev, const int64_t* dims, int ndim, stz_dtype dtype,
+                   const int64_t* block, stz_roi_metric metric, stz_roi_mode mode, double value,
+                   int64_t* sel_dev, size_t sel_cap, double* metric_dev, int64_t* nsel,
+                   void* ws_dev, size_t ws_bytes, void* stream) {
+  int64_t n[3], b[3], nu;
+  if (roi_geom(dims, ndim, block, n, b, &nu) != STZ_OK) return STZ_ERR_ARG;
+  if (dtype != STZ_F32 && dtype != STZ_F64) return STZ_ERR_ARG;
+  if (metric != STZ_ROI_RANGE && metric != STZ_ROI_MAX) return STZ_ERR_ARG;
+  if (mode != STZ_ROI_THRESHOLD && mode != STZ_ROI_TOP) return STZ_ERR_ARG;
+  if (mode == STZ_ROI_TOP && !(value > 0.0 && value <= 1.0)) return STZ_ERR_ARG;
+  if (!field_dev || !sel_dev || !nsel || !ws_dev) return STZ_ERR_ARG;
+  const size_t ps = dtype == STZ_F32 ? 4 : 8;
+  if (((uintptr_t)field_dev % ps) || ((uintptr_t)sel_dev % 8) || ((uintptr_t)ws_dev % 256) ||
+      (metric_dev && ((uintptr_t)metric_dev % 8)))
+    return STZ_ERR_ARG;
+  if (sel_cap < (size_t)nu || ws_bytes < stz_roi_workspace_size(dims, ndim, block))
+    return STZ_ERR_CAPACITY;
+  int64_t k = 0;
+  if (mode == STZ_ROI_TOP) {
+    k = (int64_t)ceil(value * (double)nu);
+    if (k > nu) k = nu;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  uint8_t* ws = (uint8_t*)ws_dev;
+  const size_t a = al256(8 * (size_t)nu);
+  unsigned long long* kmin = (unsigned long long*)ws;
+  unsigned long long* kmax = (unsigned long long*)(ws + a);
+  unsigned long long* mkey = (unsigned long long*)(ws + 2 * a);
+  unsigned long long* cnt = (unsigned long long*)(ws + 3 * a);
+  int rc = launch_roi(field_dev, dtype, n, b, metric, mode, value, k, kmin, kmax, mkey, metric_dev,
+                      sel_dev, cnt, st);
+  if (rc != STZ_OK) return rc;
+  const uint8_t* h = nullptr;
+  if ((rc = readback(cnt, 8, 0, st, &h)) != STZ_OK) return rc;
+  if ((rc = cuda_ok(cudaStreamSynchronize(st))) != STZ_OK) return rc;
+  unsigned long long c;
+  memcpy(&c, h, 8);
+  *nsel = (int64_t)c;
+  return STZ_OK;
 }
 
 // ------------------------------------------------ region decode, no allocation

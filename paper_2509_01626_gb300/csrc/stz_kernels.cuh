@@ -173,6 +173,14 @@ int compress_graph_launch(const CompressJob& j, const void* field, const int64_t
                           int dtype, int eb_mode, double eb, void* out, size_t out_cap, void* ws,
                           size_t ws_bytes, cudaStream_t st, CompressDev* d);
 
+// ---- stz_roi.cu: ROI selection (Sec. 3.3) ----
+// kmin / kmax / mkey: one u64 per unit each; sel: the selection, ascending;
+// nsel: its size; k: units kept in top mode
+int launch_roi(const void* field, int dtype, const int64_t n[3], const int64_t b[3], int metric,
+               int mode, double value, int64_t k, unsigned long long* kmin,
+               unsigned long long* kmax, unsigned long long* mkey, double* metric_out,
+               int64_t* sel, unsigned long long* nsel, cudaStream_t s);
+
 // SMs that one launch sizes a persistent grid for: all of them, unless the
 // calling thread set a share (the batched form runs several fields' kernels
 // side by side and gives each a part of the GPU).

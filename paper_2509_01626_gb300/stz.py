@@ -122,6 +122,12 @@ def lib() -> ctypes.CDLL:
                                                 ctypes.c_int]
         L.stz_region_chunks.argtypes = [vp, sz, sz, i64p, i64p, ctypes.c_int, ctypes.c_int,
                                          i64p, ctypes.c_int]
+        L.stz_roi_units.restype = ctypes.c_int64
+        L.stz_roi_units.argtypes = [i64p, ctypes.c_int, i64p]
+        L.stz_roi_workspace_size.restype = sz
+        L.stz_roi_workspace_size.argtypes = [i64p, ctypes.c_int, i64p]
+        L.stz_roi_select.argtypes = [vp, i64p, ctypes.c_int, ctypes.c_int, i64p, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_double, vp, sz, vp, i64p, vp, sz, vp]
         L.stz_decompress_region_async.argtypes = [vp, sz, vp, sz, vp, i64p, i64p, ctypes.c_int,
                                                   vp, sz, i64p, vp, sz, vp, vp]
         L.stz_launch_count.restype = ctypes.c_ulonglong
@@ -342,6 +348,58 @@ def decompress_region_noalloc(comp: torch.Tensor, lo, hi, level: int, out: torch
     for v in oshape:
         n *= v
     return out.reshape(-1)[:n].view(oshape)
+
+
+ROI_METRICS = {"range": 0, "max": 1}
+ROI_MODES = {"threshold": 0, "top": 1}
+
+
+def roi_select(field: torch.Tensor, block, metric: str = "range", mode: str = "top",
+               value: float = 0.01, metric_out: bool = False, stream=None):
+    """stz_roi_select (Sec. 3.3 ROI module): the selected unit indices
+    (ascending, int64 CUDA tensor) and, with metric_out, every unit's
+    metric (float64 CUDA tensor).  block: (bz, by, bx), or (by, bx) for 2D."""
+    if not field.is_cuda or not field.is_contiguous():
+        raise ValueError("field must be a contiguous CUDA tensor")
+    shape = tuple(field.shape)
+    nd = len(shape)
+    nu = int(lib().stz_roi_units(_i64(shape), nd, _i64(block)))
+    if nu < 1:
+        raise StzError(ERR_ARG, "stz_roi_units")
+    ws = torch.empty(lib().stz_roi_workspace_size(_i64(shape), nd, _i64(block)),
+                     dtype=torch.uint8, device=field.device)
+    sel = torch.empty(nu, dtype=torch.int64, device=field.device)
+    met = torch.empty(nu, dtype=torch.float64, device=field.device) if metric_out else None
+    ns = ctypes.c_int64(0)
+    rc = lib().stz_roi_select(ctypes.c_void_p(field.data_ptr()), _i64(shape), nd,
+                              _dt(field.dtype), _i64(block), ROI_METRICS[metric], ROI_MODES[mode],
+                              float(value), ctypes.c_void_p(sel.data_ptr()), nu,
+                              ctypes.c_void_p(met.data_ptr()) if met is not None else None,
+                              ctypes.byref(ns), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                              _stream(stream))
+    _check(rc, "stz_roi_select")
+    return (sel[: ns.value], met) if metric_out else sel[: ns.value]
+
+
+def roi_boxes(units, grid_shape, block, stride: int = 1, field_shape=None):
+    """Boxes [lo, hi) in field coordinates of ROI units chosen on a grid of
+    shape grid_shape that samples the field every `stride` points (the
+    output of a progressive decode); each box covers its unit's grid points
+    and the field points between them."""
+    nb = [-(-g // b) for g, b in zip(grid_shape, block)]
+    field_shape = field_shape or tuple(g * stride for g in grid_shape)
+    boxes = []
+    for u in (int(v) for v in units):
+        idx = []
+        for n in reversed(nb):
+            idx.append(u % n)
+            u //= n
+        idx = idx[::-1]
+        lo = tuple(i * b * stride for i, b in zip(idx, block))
+        hi = tuple(min(min((i + 1) * b, g) * stride, f)
+                   for i, b, g, f in zip(idx, block, grid_shape, field_shape))
+        boxes.append((lo, hi))
+    return boxes
 
 
 HEADER_MAX_BYTES = 1984  # STZ_HEADER_MAX_BYTES
