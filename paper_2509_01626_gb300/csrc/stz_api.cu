@@ -378,7 +378,7 @@ struct DecPlan {
   int64_t tlo[kMaxLevels + 1][3], tcnt[kMaxLevels + 1][3];
   SlotMap sm[kMaxStreams];
   int64_t nslots;
-  size_t dp, grid[kMaxLevels + 1], codes, lut, total;
+  size_t dp, grid[kMaxLevels + 1], codes, lut, sub_olo, total;
 };
 
 // Coarse support of the G_j coordinates [a, b) along one axis, on G_{j-1}
@@ -486,6 +486,9 @@ static void plan_decode(const Geo& g, int k, const int64_t lo[3], const int64_t 
   o += al256(2 * (size_t)(nslots * g.bvol));
   P->lut = o;
   o += al256(4 * (size_t)g.nstreams * kLutSize);
+  // where each decoded chunk's sub-chunks start in their stream's outlier list
+  P->sub_olo = o;
+  o += al256(4 * (size_t)(kNSub + 1) * (size_t)(nslots > 0 ? nslots : 1));
   P->total = o;
 }
 
@@ -1217,6 +1220,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
   DevParams* dp = (DevParams*)(ws + P.dp);
   uint16_t* codes = (uint16_t*)(ws + P.codes);
   uint16_t* lut = (uint16_t*)(ws + P.lut);
+  uint32_t* sub_olo = (uint32_t*)(ws + P.sub_olo);
   uint32_t* status = &dp->status;
   const uint8_t* comp = (const uint8_t*)comp_dev;
   // decode tables
@@ -1235,6 +1239,9 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     d.off_subs = sh.off_subs;
     d.off_payload = sh.off_payload;
     d.nsub = H.nsub;
+    d.nout = H.d[s].nout;
+    d.off_opos = sh.off_opos;
+    d.dense = dense_outliers(H.d[s].nout, H.d[s].nsym) ? 1 : 0;
   }
   const int ns_needed = 1 + 7 * (level - 1);
   int64_t nblocks = 0;
@@ -1275,7 +1282,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
       STZ_TRY(launch_lut(tb, lut, (uint32_t*)dp, (int)(sizeof(DevParams) / 4), st));
     else
       STZ_TRY(zero_words(dp, (int64_t)(sizeof(DevParams) / 4), st));
-    STZ_TRY(launch_decode_chunks(g, tb, lut, codes, status, dec_bytes, st));
+    STZ_TRY(launch_decode_chunks(g, tb, lut, codes, sub_olo, status, dec_bytes, st));
     const uint8_t* sec0 = comp + H.d[0].sect_off;
     SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps, H.nsub);
     uint8_t* g1buf = have_l1 ? (uint8_t*)o.l1 : ws + P.grid[1];
@@ -1292,6 +1299,9 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
       a.nout = (int64_t)H.d[0].nout;
       a.two_eb = H.two_eb[1];
       a.status = status;
+      a.sub_olo = sub_olo;
+      a.nsub = H.nsub;
+      a.dense = tb.ds[0].dense;
       // the part of level 1 the output depends on: the output box itself, or
       // the coarse cells the level-2 box is predicted from
       int64_t m1[3];
@@ -1350,6 +1360,9 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
       }
       a.two_eb = H.two_eb[j];
       a.status = status;
+      a.sub_olo = sub_olo;
+      a.nsub = H.nsub;
+      for (int K = 1; K <= 7; K++) a.dense[K] = (uint8_t)tb.ds[1 + 7 * (j - 2) + K - 1].dense;
       STZ_TRY(launch_level(a, true, st));
     }
     return STZ_OK;

@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(256) k_base_pass(BaseArgs a, PassGeo p) {
     int sym = a.codes[ad.slot];
     T v;
     if (sym == 0) {
-      if (!find_outlier(a.opos, (const T*)a.oval, a.nout, ad.pos, v)) {
+      if (!outlier_value(a.sub_olo, a.dense != 0, ad.sidx, ad.local, ad.cnt, a.nsub, a.opos,
+                         (const T*)a.oval, a.nout, ad.pos, v)) {
         v = T(0);
         atomicOr(a.status, kStatCorrupt);
       }
@@ -117,8 +118,8 @@ __device__ __forceinline__ T base_predict_cg(const T* g1, int64_t idx, int64_t s
 // Address of level-1 grid point g in stream 0 (32-bit arithmetic: the level-1
 // grid has fewer than 2^31 points).
 struct Addr32 {
-  int64_t slot, pos;
-  int chunk;
+  int64_t slot, pos, sidx;
+  int chunk, local, cnt;
 };
 __device__ __forceinline__ Addr32 addr0(const StreamGeo& sg, const int32_t b[3],
                                         const FastDiv bd[3], int bvol, const SlotMap& sm, int c0,
@@ -134,7 +135,10 @@ __device__ __forceinline__ Addr32 addr0(const StreamGeo& sg, const int32_t b[3],
   r.chunk = (B0 * (int)sg.nb[1] + B1) * (int)sg.nb[2] + B2;
   const int ord = ((B0 - (int)sm.lo[0]) * (int)sm.cnt[1] + (B1 - (int)sm.lo[1])) * (int)sm.cnt[2] +
                   (B2 - (int)sm.lo[2]);
-  r.slot = (sm.base + ord) * (int64_t)bvol + local;
+  r.sidx = sm.base + ord;
+  r.slot = r.sidx * (int64_t)bvol + local;
+  r.local = local;
+  r.cnt = l0 * l1 * l2;
   return r;
 }
 
@@ -169,7 +173,8 @@ __device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p,
     int sym = a.codes[ad.slot];
     T v;
     if (sym == 0) {
-      if (!find_outlier(a.opos, (const T*)a.oval, a.nout, ad.pos, v)) {
+      if (!outlier_value(a.sub_olo, a.dense != 0, ad.sidx, ad.local, ad.cnt, a.nsub, a.opos,
+                         (const T*)a.oval, a.nout, ad.pos, v)) {
         v = T(0);
         atomicOr(a.status, kStatCorrupt);
       }
@@ -199,6 +204,8 @@ __device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint1
   for (int i0 = threadIdx.x; i0 < nsg; i0 += kGather * blockDim.x) {
     int64_t src[kGather];
     int pos[kGather];
+    int64_t sidx[kGather];
+    int loc[kGather], ccnt[kGather];
 #pragma unroll
     for (int u = 0; u < kGather; u++) {
       const int i = i0 + u * blockDim.x;
@@ -212,6 +219,9 @@ __device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint1
         const Addr32 ad = addr0(geo.s[0], geo.b, pl.bd, (int)geo.bvol, a.sm, g0, g1, g2);
         src[u] = ad.slot;
         pos[u] = (int)ad.pos;
+        sidx[u] = ad.sidx;
+        loc[u] = ad.local;
+        ccnt[u] = ad.cnt;
       }
     }
     if (!DEC) {
@@ -232,7 +242,8 @@ __device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint1
         sc[i] = c[u];
         if (c[u] == 0) {
           T v;
-          if (!find_outlier(a.opos, (const T*)a.oval, a.nout, (int64_t)pos[u], v)) {
+          if (!outlier_value(a.sub_olo, a.dense != 0, sidx[u], loc[u], ccnt[u], a.nsub, a.opos,
+                             (const T*)a.oval, a.nout, (int64_t)pos[u], v)) {
             v = T(0);
             atomicOr(a.status, kStatCorrupt);
           }

@@ -106,6 +106,8 @@ struct CellAddr {
   int64_t pos;    // stream position (outlier indices refer to it)
   int64_t slot;   // code buffer entry
   int64_t chunk;  // chunk index within the stream
+  int64_t sidx;   // chunk slot
+  int local, cnt; // index within the chunk, symbols of the chunk
 };
 
 STZ_HD CellAddr cell_addr(const StreamGeo& sg, const int32_t b[3], int64_t bvol,
@@ -120,7 +122,10 @@ STZ_HD CellAddr cell_addr(const StreamGeo& sg, const int32_t b[3], int64_t bvol,
   r.pos = B0 * b[0] * sg.e[1] * sg.e[2] + B1 * b[1] * l0 * sg.e[2] + B2 * b[2] * l0 * l1 + local;
   r.chunk = (B0 * sg.nb[1] + B1) * sg.nb[2] + B2;
   int64_t ord = ((B0 - sm.lo[0]) * sm.cnt[1] + (B1 - sm.lo[1])) * sm.cnt[2] + (B2 - sm.lo[2]);
-  r.slot = (sm.base + ord) * bvol + local;
+  r.sidx = sm.base + ord;
+  r.slot = r.sidx * bvol + local;
+  r.local = (int)local;
+  r.cnt = (int)(l0 * l1 * l2);
   return r;
 }
 
@@ -256,18 +261,39 @@ __device__ __forceinline__ T dequantize(int sym, T pred, T two_eb, int R) {
   return op_add(pred, op_mul(from_int(sym - R, T()), two_eb));
 }
 
-// Outlier value at stream position pos: binary search in the ascending list.
+// Outliers when decoding.  A stream's outliers are listed by ascending
+// stream position, and a chunk's positions are contiguous (brick-major
+// order), so the outliers of each sub-chunk are a contiguous part of the
+// list.  For streams dense in outliers (dense_outliers(): at least one per
+// 2048 symbols) the chunk decoder records, per decoded chunk slot, where each
+// of its sub-chunks starts in that list (sub_olo[slot * (kNSub + 1) + u],
+// u = 0 .. nsub; entry nsub is the chunk's end), and an outlier's value is
+// found by a binary search over its own sub-chunk's few entries; for sparse
+// streams the search runs over the whole (short) list.  A symbol 0 whose
+// position is not listed means a corrupt container.
+inline bool dense_outliers(uint64_t nout, uint64_t nsym) { return nout > 0 && nout * 2048 >= nsym; }
+
 template <typename T>
-__device__ __forceinline__ bool find_outlier(const uint32_t* pos, const T* val, int64_t n,
-                                             int64_t p, T& out) {
-  int64_t lo = 0, hi = n;
+__device__ __forceinline__ bool outlier_value(const uint32_t* __restrict__ sub_olo, bool dense,
+                                              int64_t sidx, int local, int cnt, int nsub,
+                                              const uint32_t* opos, const T* oval, int64_t nout,
+                                              int64_t pos, T& out) {
+  if (nout <= 0 || cnt <= 0) return false;
+  int64_t lo = 0, hi = nout;
+  if (dense) {
+    const int per = (cnt + nsub - 1) / nsub;
+    const uint32_t* r = sub_olo + sidx * (kNSub + 1) + local / per;
+    lo = imin((int64_t)r[0], nout);
+    hi = imin((int64_t)r[1], nout);
+  }
+  const int64_t end = hi;
   while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if ((int64_t)pos[mid] < p) lo = mid + 1;
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)opos[mid] < pos) lo = mid + 1;
     else hi = mid;
   }
-  if (lo < n && (int64_t)pos[lo] == p) {
-    out = val[lo];
+  if (lo < end && (int64_t)opos[lo] == pos) {
+    out = oval[lo];
     return true;
   }
   return false;

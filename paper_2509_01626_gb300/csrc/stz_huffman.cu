@@ -929,10 +929,22 @@ static_assert((sizeof(uint32_t) * kStageWords) % 16 == 0 &&
                   (sizeof(uint32_t) * kStageWords + sizeof(uint16_t) * kLutSize) % 8 == 0,
               "shared arrays of the chunk decoder must stay aligned");
 
+// first index i in the ascending list p[0, n) with p[i] >= v
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ p, int64_t n,
+                                                    int64_t v) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)__ldg(p + mid) < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return (uint32_t)lo;
+}
+
 __global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
     const __grid_constant__ Geo g, const __grid_constant__ DecTables tb,
     const uint16_t* __restrict__ lut, uint16_t* __restrict__ codes,
-    uint32_t* __restrict__ status) {
+    uint32_t* __restrict__ sub_olo, uint32_t* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char dsm[];
   // arrays in order of alignment: the 16-byte-loaded table first, then 4-byte
   uint32_t* stage = (uint32_t*)dsm;
@@ -1060,18 +1072,41 @@ __global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
     }
     a = b;
   }
+  // where this sub-chunk's outliers start in the stream's outlier list (the
+  // list is ascending by stream position and a chunk's positions are
+  // contiguous): one search per sub-chunk here instead of one per outlier in
+  // the predictors
+  if (d.dense && c < nch) {
+    const uint32_t* opos = (const uint32_t*)(d.sect + d.off_opos);
+    const int64_t jl = cjl[c];
+    const int64_t B0 = jl / (sg.nb[1] * sg.nb[2]), B1 = (jl / sg.nb[2]) % sg.nb[1],
+                  B2 = jl % sg.nb[2];
+    const int64_t l0 = imin(g.b[0], sg.e[0] - B0 * g.b[0]);
+    const int64_t l1 = imin(g.b[1], sg.e[1] - B1 * g.b[1]);
+    const int64_t l2 = imin(g.b[2], sg.e[2] - B2 * g.b[2]);
+    const int64_t start = B0 * g.b[0] * sg.e[1] * sg.e[2] + B1 * g.b[1] * l0 * sg.e[2] +
+                          B2 * g.b[2] * l0 * l1;
+    const int cntc = (int)(l0 * l1 * l2);
+    const int per = (cntc + nsub - 1) / nsub;
+    uint32_t* dst = sub_olo + (job.slot_base + qb + c) * (kNSub + 1);
+    const int64_t n = (int64_t)d.nout;
+    dst[u] = lower_bound_u32(opos, n, start + min(u * per, cntc));
+    if (u == nsub - 1) dst[nsub] = lower_bound_u32(opos, n, start + cntc);
+  }
   if (bad) atomicOr(status, kStatCorrupt);
 }
 
 int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint16_t* lut,
-                         uint16_t* codes, uint32_t* status, double bytes, cudaStream_t s) {
+                         uint16_t* codes, uint32_t* sub_olo, uint32_t* status, double bytes,
+                         cudaStream_t s) {
   if (tb.nblocks == 0) return STZ_OK;
   static_assert(kDecThreads == 256, "block_scan_256 assumes 256 threads");
   if (cudaFuncSetAttribute(k_decode_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kDecSmem) != cudaSuccess)
     return STZ_ERR_CUDA;
   ProfScope ps_("k_decode_chunks", s, bytes);
-  k_decode_chunks<<<(unsigned)tb.nblocks, kDecThreads, kDecSmem, s>>>(g, tb, lut, codes, status);
+  k_decode_chunks<<<(unsigned)tb.nblocks, kDecThreads, kDecSmem, s>>>(g, tb, lut, codes, sub_olo,
+                                                                      status);
   return cuda_ok(cudaGetLastError());
 }
 

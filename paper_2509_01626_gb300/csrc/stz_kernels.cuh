@@ -34,6 +34,9 @@ struct BaseArgs {
   int64_t nout;
   double two_eb;              // decode: 2 eb_1 in the field precision
   uint32_t* status;           // decode: corrupt flag
+  const uint32_t* sub_olo;    // decode: first outlier index per (slot, sub-chunk)
+  int nsub;                   // decode: sub-chunks per chunk
+  int dense;                  // decode: sub_olo holds stream 0's ranges
   int region;                 // decode: only the box [rlo, rhi) of the level-1 grid is needed
   int64_t rlo[3], rhi[3];
 };
@@ -62,6 +65,9 @@ struct LevelArgs {
   int64_t nout[8];
   double two_eb;              // decode
   uint32_t* status;
+  const uint32_t* sub_olo;    // decode: first outlier index per (slot, sub-chunk)
+  int nsub;                   // decode: sub-chunks per chunk
+  uint8_t dense[8];           // decode: sub_olo holds sub-block K's ranges
   int64_t tlo[3], tcnt[3];    // tiles (bricks of cells) to process
 };
 int launch_level(const LevelArgs& a, bool decode, cudaStream_t s);
@@ -98,8 +104,9 @@ int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
 // (len 0: no code starts with i)
 struct DecStream {
   const uint8_t* sect;        // section start in the container
-  uint64_t nlive, nchunks, pw;
-  uint64_t off_syms, off_lens, off_chunks, off_subs, off_payload;
+  uint64_t nlive, nchunks, pw, nout;
+  int dense;                  // sub_olo ranges recorded (dense_outliers)
+  uint64_t off_syms, off_lens, off_chunks, off_subs, off_payload, off_opos;
   int nsub;
 };
 // entropy-decode the chunks of bricks [lo, lo+cnt) of each stream into slots
@@ -122,9 +129,13 @@ struct DecTables {
 // zero-fills the nclear words at clear
 int launch_lut(const DecTables& tb, uint16_t* lut, uint32_t* clear, int nclear,
                cudaStream_t s);
-// bytes: the launch's algorithmic bytes (payload read, codes written)
+// bytes: the launch's algorithmic bytes (payload read, codes written).
+// For streams with outliers, sub_olo[slot * (kNSub + 1) + u] receives where
+// sub-chunk u of each decoded chunk starts in the stream's outlier list
+// (u = nsub: where the chunk ends).
 int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint16_t* lut,
-                         uint16_t* codes, uint32_t* status, double bytes, cudaStream_t s);
+                         uint16_t* codes, uint32_t* sub_olo, uint32_t* status, double bytes,
+                         cudaStream_t s);
 
 // ---- stz_container.cu: layout, header, sections, outliers ----
 struct SectDev {

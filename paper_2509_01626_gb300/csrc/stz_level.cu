@@ -75,7 +75,9 @@ __device__ __forceinline__ void do_point(const LevelArgs& a, const TileCtx& tc, 
       int sym = a.codes[s_slot[K] + local];
       T val;
       if (sym == 0) {
-        if (!find_outlier(a.opos[K], (const T*)a.oval[K], a.nout[K], s_pos[K] + local, val)) {
+        if (!outlier_value(a.sub_olo, a.dense[K] != 0, s_slot[K] / geo.bvol, (int)local,
+                           ll[0] * ll[1] * ll[2], a.nsub, a.opos[K], (const T*)a.oval[K],
+                           a.nout[K], s_pos[K] + local, val)) {
           val = T(0);
           atomicOr(a.status, kStatCorrupt);
         }
@@ -547,8 +549,9 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
       for (int K = 1; K <= 7; K++) {
         if (on[K - 1] && cv[K - 1] == 0) {  // outlier: its value from the list
           const int64_t local = cp[K - 1] - (a.codes + ti.slot[K]);
-          if (!find_outlier(a.opos[K], (const T*)a.oval[K], a.nout[K], ti.pos[K] + local,
-                            val[K - 1])) {
+          if (!outlier_value(a.sub_olo, a.dense[K] != 0, ti.slot[K] / a.geo.bvol, (int)local,
+                             ti.l[K][0] * ti.l[K][1] * ti.l[K][2], a.nsub, a.opos[K],
+                             (const T*)a.oval[K], a.nout[K], ti.pos[K] + local, val[K - 1])) {
             val[K - 1] = T(0);
             atomicOr(a.status, kStatCorrupt);
           }
@@ -877,7 +880,8 @@ __global__ void __launch_bounds__(256, DEC ? 4 : 2)
             const int64_t pos = (int64_t)Bc[0] * geo.b[0] * sg.e[1] * sg.e[2] +
                                 (int64_t)Bc[1] * geo.b[1] * l0 * sg.e[2] +
                                 (int64_t)Bc[2] * geo.b[2] * l0 * l1 + local;
-            if (!find_outlier(a.opos[K], (const T*)a.oval[K], a.nout[K], pos, val)) {
+            if (!outlier_value(a.sub_olo, a.dense[K] != 0, sm.base + ord, local, l0 * l1 * l2,
+                               a.nsub, a.opos[K], (const T*)a.oval[K], a.nout[K], pos, val)) {
               val = T(0);
               atomicOr(a.status, kStatCorrupt);
             }
