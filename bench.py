@@ -498,28 +498,35 @@ def run_served(args, dev):
     # cached level-1 grids and parsed headers -- isolates what the overlap of
     # requests (continuous batching) adds beyond the caching
     srv1 = serve.Server(comps, budget_bytes=budget, max_edge=256, max_slots=1)
+    # every admission round decoded by one stz_decode_requests call: a fixed
+    # number of launches per round, rounds overlapping on their streams
+    bsrv = serve.BatchServer(comps, budget_bytes=budget, max_edge=256, max_batch=16)
     reg_out = torch.empty(256 ** 3 * 4, dtype=torch.uint8, device=dev)
     rates = [float(r) for r in args.serve_rates.split(",") if r]
     # warm both paths
     warm = serve.poisson_requests([shape] * len(comps), 20, 1e5, synth.seed_for(5, 99))
     srv.run(warm)
     srv1.run(warm)
+    bsrv.run(warm)
     serve.serial(comps, warm, ws, reg_out, realtime=False)
     per_rate = []
     for k, rate in enumerate(rates):
         reqs = serve.poisson_requests([shape] * len(comps), args.serve_requests, rate,
                                       synth.seed_for(5, 200 + k))
         res, wall = srv.run(reqs)
+        bres, bwall = bsrv.run(reqs)
         cres, cwall = srv1.run(reqs)
         sres, swall = serve.serial(comps, reqs, ws, reg_out)
-        per_rate.append({"rate_rps": rate, "served": serve.latency_stats(res, wall),
+        per_rate.append({"rate_rps": rate, "served_batched": serve.latency_stats(bres, bwall),
+                         "served": serve.latency_stats(res, wall),
                          "serial_cached": serve.latency_stats(cres, cwall),
                          "serial": serve.latency_stats(sres, swall)})
     out = {"workload": f"{len(comps)} resident {size}^3 f32 k^-5/3 GRFs (rel eb 1e-3); "
                        "Poisson requests, box edge U[16,256] per axis, level U{1,2,3}",
            "resident_gb": round(resident / 1e9, 3), "raw_gb": round(raw / 1e9, 3),
-           "slots": srv.nslots, "budget_gb": round(budget / 1e9, 2), "per_rate": per_rate}
-    del srv, srv1, comps, ws, reg_out
+           "slots": srv.nslots, "batch": {"max_batch": bsrv.max_batch, "inflight": bsrv.nbatch},
+           "budget_gb": round(budget / 1e9, 2), "per_rate": per_rate}
+    del srv, srv1, bsrv, comps, ws, reg_out
     torch.cuda.empty_cache()
     return out
 

@@ -361,6 +361,56 @@ int stz_decompress_region_noalloc(const void* comp_dev, size_t comp_bytes, const
                                   const int64_t* hi, int level, void* out_dev, size_t out_cap,
                                   int64_t* out_dims, void* stream);
 
+/* ---- batched serving: many region requests in a fixed number of launches ----
+ * (no counterpart in the paper).  A serving loop that keeps fields resident
+ * decodes every admitted request of an iteration with one call: the chunk
+ * decoding of all of them is one kernel launch, each finer level's
+ * prediction one launch of the interior and one of the boundary kernel, and
+ * the level-1 copies one launch -- whatever the number of requests.  Each
+ * result is bitwise that of stz_decompress_region.
+ *
+ * Per field, once: its level-1 grid (stz_decompress_progressive at level 1)
+ * and its decode tables (stz_decode_tables). */
+size_t stz_decode_tables_size(const void* hdr_host, size_t hdr_bytes, size_t comp_bytes);
+int stz_decode_tables(const void* comp_dev, size_t comp_bytes, const void* hdr_host,
+                      size_t hdr_bytes, void* tables_dev, size_t tables_bytes, void* stream);
+
+typedef struct {
+  const void* comp_dev;     /* the container (device) */
+  size_t comp_bytes;
+  const void* hdr_host;     /* host copy of its first bytes (STZ_HEADER_MAX_BYTES) */
+  size_t hdr_bytes;
+  const void* level1_dev;   /* its decoded level-1 grid */
+  const void* tables_dev;   /* its decode tables (stz_decode_tables) */
+} stz_served_field;
+
+typedef struct {
+  int field;                /* index into the fields array */
+  int level;                /* 1..L */
+  int64_t lo[3], hi[3];     /* the box, axis order as for stz_decompress_region */
+  void* out_dev;            /* output (device), out_cap bytes */
+  size_t out_cap;
+  int64_t out_dims[3];      /* receives the output shape */
+} stz_region_request;
+
+/* Workspace bytes of stz_decode_requests for these requests (0 on invalid
+ * arguments). */
+size_t stz_decode_requests_workspace(int n, const stz_region_request* reqs,
+                                     const stz_served_field* fields, int nfields);
+
+/*
+ * Decode n region requests on `stream` without waiting on the host.  All
+ * fields must have the same dtype.  status_dev: device u32[n], receives 0 or
+ * a nonzero status per request (corrupt container).  Arguments are checked
+ * for every request before any work is queued (STZ_ERR_ARG /
+ * STZ_ERR_CAPACITY / STZ_ERR_CORRUPT for a bad header).  The call copies
+ * the launch arguments to the workspace from host memory it owns; the
+ * workspace must not be in use by another call in flight.
+ */
+int stz_decode_requests(int n, stz_region_request* reqs, const stz_served_field* fields,
+                        int nfields, void* ws_dev, size_t ws_bytes, uint32_t* status_dev,
+                        void* stream);
+
 /* ---- tracing (no counterpart in the paper, which reports wall times only) ----
  * Every kernel launch of the library is counted.  With profiling enabled an
  * event pair is recorded around each launch on its stream; stz_profile_read

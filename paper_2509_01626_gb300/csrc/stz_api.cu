@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "stz_kernels.cuh"
 #include "stz_prof.cuh"
@@ -816,6 +817,29 @@ __global__ void k_copy_box(const T* __restrict__ src, T* __restrict__ dst, int64
   }
 }
 
+namespace stz {
+// a level-1 request of a batch: a box of the cached level-1 grid copied to
+// the output
+struct CopyJob {
+  const void* src;
+  void* dst;
+  int64_t a[3], e[3], m1, m2;
+};
+}  // namespace stz
+
+template <typename T>
+__global__ void k_copy_boxes(const CopyJob* __restrict__ jobs) {
+  const CopyJob& j = jobs[blockIdx.y];
+  const int64_t n = j.e[0] * j.e[1] * j.e[2];
+  const T* __restrict__ src = (const T*)j.src;
+  T* __restrict__ dst = (T*)j.dst;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = i % j.e[2], y = (i / j.e[2]) % j.e[1], z = i / (j.e[1] * j.e[2]);
+    dst[i] = src[((z + j.a[0]) * j.m1 + (y + j.a[1])) * j.m2 + (x + j.a[2])];
+  }
+}
+
 extern "C" {
 
 const char* stz_strerror(int code) {
@@ -1609,6 +1633,297 @@ int stz_roi_select(const void* field_dev, const int64_t* dims, int ndim, stz_dty
   unsigned long long c;
   memcpy(&c, h, 8);
   *nsel = (int64_t)c;
+  return STZ_OK;
+}
+
+// ---------------------------------------------------------- batched serving
+// decode-side description of stream s of a parsed container
+static void dec_stream(const Hdr& H, const uint8_t* comp, int s, DecStream* d) {
+  const size_t ps = H.dtype == STZ_F32 ? 4 : 8;
+  SectHost sh = sect_host(H.d[s].nlive, H.d[s].nch, H.d[s].pw, H.d[s].nout, ps, H.nsub);
+  memset(d, 0, sizeof(*d));
+  d->sect = comp + H.d[s].sect_off;
+  d->nlive = H.d[s].nlive;
+  d->nchunks = H.d[s].nch;
+  d->pw = H.d[s].pw;
+  d->off_syms = sh.off_syms;
+  d->off_lens = sh.off_lens;
+  d->off_chunks = sh.off_chunks;
+  d->off_subs = sh.off_subs;
+  d->off_payload = sh.off_payload;
+  d->nsub = H.nsub;
+  d->nout = H.d[s].nout;
+  d->off_opos = sh.off_opos;
+  d->dense = dense_outliers(H.d[s].nout, H.d[s].nsym) ? 1 : 0;
+}
+
+size_t stz_decode_tables_size(const void* hdr_host, size_t hdr_bytes, size_t comp_bytes) {
+  Hdr H;
+  if (!hdr_host || parse_hdr((const uint8_t*)hdr_host, hdr_bytes, comp_bytes, &H) != STZ_OK)
+    return 0;
+  return sizeof(uint16_t) * (size_t)kLutSize * (size_t)H.ns;
+}
+
+int stz_decode_tables(const void* comp_dev, size_t comp_bytes, const void* hdr_host,
+                      size_t hdr_bytes, void* tables_dev, size_t tables_bytes, void* stream) {
+  if (!comp_dev || !hdr_host || !tables_dev || ((uintptr_t)tables_dev % 16)) return STZ_ERR_ARG;
+  Hdr H;
+  const int rc = parse_hdr((const uint8_t*)hdr_host, hdr_bytes, comp_bytes, &H);
+  if (rc != STZ_OK) return rc;
+  if (tables_bytes < sizeof(uint16_t) * (size_t)kLutSize * (size_t)H.ns) return STZ_ERR_CAPACITY;
+  Geo g;
+  make_geo(H.n, H.ndim, H.dtype, H.L, H.b, &g);
+  DecTables tb;
+  memset(&tb, 0, sizeof(tb));
+  for (int s = 0; s < H.ns; s++) {
+    dec_stream(H, (const uint8_t*)comp_dev, s, &tb.ds[s]);
+    if (g.s[s].nsym > 0) tb.lut_sid[tb.nlut++] = s;
+  }
+  if (tb.nlut == 0) return STZ_OK;
+  return launch_lut(tb, (uint16_t*)tables_dev, nullptr, 0, (cudaStream_t)stream);
+}
+
+
+namespace {
+// The plan of one stz_decode_requests call: parsed fields, per-request decode
+// plans and boxes, and the workspace layout (argument arenas, then one region
+// per request decoded beyond level 1).
+struct BatchPlan {
+  std::vector<Hdr> H;
+  std::vector<Geo> G;
+  std::vector<DecPlan> P;
+  std::vector<int64_t> npts;
+  std::vector<size_t> req_off;
+  int maxlevel = 1, dtype = 0, njobs = 0, ncopy = 0;
+  size_t o_jobs = 0, o_copy = 0, o_level[kMaxLevels + 1] = {}, total = 0;
+};
+}  // namespace
+
+static int plan_batch(int n, stz_region_request* reqs, const stz_served_field* fields, int nf,
+                      BatchPlan* B) {
+  if (n < 1 || nf < 1 || !reqs || !fields) return STZ_ERR_ARG;
+  B->H.resize(nf);
+  B->G.resize(nf);
+  for (int f = 0; f < nf; f++) {
+    const stz_served_field& F = fields[f];
+    if (!F.comp_dev || !F.hdr_host || !F.level1_dev || !F.tables_dev) return STZ_ERR_ARG;
+    if ((uintptr_t)F.comp_dev % 8) return STZ_ERR_ARG;
+    const int rc = parse_hdr((const uint8_t*)F.hdr_host, F.hdr_bytes, F.comp_bytes, &B->H[f]);
+    if (rc != STZ_OK) return rc;
+    const Hdr& H = B->H[f];
+    if (f == 0) B->dtype = H.dtype;
+    if (H.dtype != B->dtype) return STZ_ERR_ARG;
+    if ((uintptr_t)F.level1_dev % (H.dtype == STZ_F32 ? 4 : 8)) return STZ_ERR_ARG;
+    make_geo(H.n, H.ndim, H.dtype, H.L, H.b, &B->G[f]);
+  }
+  const size_t ps = B->dtype == STZ_F32 ? 4 : 8;
+  B->P.resize(n);
+  B->npts.assign(n, 0);
+  B->req_off.assign(n, 0);
+  int nlev[kMaxLevels + 1] = {};
+  for (int i = 0; i < n; i++) {
+    stz_region_request& r = reqs[i];
+    if (r.field < 0 || r.field >= nf) return STZ_ERR_ARG;
+    const Hdr& H = B->H[r.field];
+    const Geo& g = B->G[r.field];
+    if (r.level < 1 || r.level > H.L || !r.out_dev || ((uintptr_t)r.out_dev % ps))
+      return STZ_ERR_ARG;
+    int64_t lo[3], hi[3];
+    box3(H, r.lo, r.hi, lo, hi);
+    for (int a = 0; a < 3; a++)
+      if (lo[a] < 0 || hi[a] > g.n[a] || lo[a] >= hi[a]) return STZ_ERR_ARG;
+    DecPlan& P = B->P[i];
+    plan_decode(g, r.level, lo, hi, &P, true);
+    int64_t od[3];
+    for (int a = 0; a < 3; a++) od[a] = imax(0, P.OB[a] - P.OA[a]);
+    if (H.ndim == 3) {
+      for (int a = 0; a < 3; a++) r.out_dims[a] = od[a];
+    } else {
+      r.out_dims[0] = od[1];
+      r.out_dims[1] = od[2];
+      r.out_dims[2] = 1;
+    }
+    B->npts[i] = od[0] * od[1] * od[2];
+    if ((size_t)B->npts[i] * ps > r.out_cap) return STZ_ERR_CAPACITY;
+    if (B->npts[i] == 0) continue;
+    if (r.level == 1) {
+      B->ncopy++;
+      continue;
+    }
+    B->maxlevel = r.level > B->maxlevel ? r.level : B->maxlevel;
+    B->njobs += 7 * (r.level - 1);
+    for (int j = 2; j <= r.level; j++) nlev[j]++;
+  }
+  size_t o = 0;
+  B->o_jobs = o;
+  o += al256(sizeof(DecJobMulti) * (size_t)(B->njobs > 0 ? B->njobs : 1));
+  B->o_copy = o;
+  o += al256(sizeof(CopyJob) * (size_t)(B->ncopy > 0 ? B->ncopy : 1));
+  for (int j = 2; j <= B->maxlevel; j++) {
+    B->o_level[j] = o;
+    o += al256(level_multi_arena_bytes(nlev[j]));
+  }
+  for (int i = 0; i < n; i++) {
+    if (B->npts[i] == 0 || reqs[i].level == 1) continue;
+    B->req_off[i] = o;
+    o += al256(B->P[i].total);
+  }
+  B->total = o;
+  return STZ_OK;
+}
+
+size_t stz_decode_requests_workspace(int n, const stz_region_request* reqs,
+                                     const stz_served_field* fields, int nfields) {
+  if (n < 1 || !reqs) return 0;
+  std::vector<stz_region_request> copy(reqs, reqs + n);  // out_dims are written
+  BatchPlan B;
+  return plan_batch(n, copy.data(), fields, nfields, &B) == STZ_OK ? B.total : 0;
+}
+
+int stz_decode_requests(int n, stz_region_request* reqs, const stz_served_field* fields,
+                        int nfields, void* ws_dev, size_t ws_bytes, uint32_t* status_dev,
+                        void* stream) {
+  if (!ws_dev || !status_dev || ((uintptr_t)ws_dev % 256) || ((uintptr_t)status_dev % 4))
+    return STZ_ERR_ARG;
+  BatchPlan B;
+  int rc = plan_batch(n, reqs, fields, nfields, &B);
+  if (rc != STZ_OK) return rc;
+  if (B.total > ws_bytes) return STZ_ERR_CAPACITY;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint8_t* ws = (uint8_t*)ws_dev;
+  const size_t ps = B.dtype == STZ_F32 ? 4 : 8;
+  // every request's status word starts at zero; the kernels OR into it
+  if ((rc = zero_words(status_dev, n, st)) != STZ_OK) return rc;
+  // chunk jobs of all requests, and the level-1 copies
+  std::vector<DecJobMulti> jobs;
+  std::vector<CopyJob> copies;
+  jobs.reserve(B.njobs);
+  int64_t nblocks = 0, copy_max = 0;
+  double dec_bytes = 0.0;
+  for (int i = 0; i < n; i++) {
+    const stz_region_request& r = reqs[i];
+    if (B.npts[i] == 0) continue;
+    const stz_served_field& F = fields[r.field];
+    const Hdr& H = B.H[r.field];
+    const Geo& g = B.G[r.field];
+    const DecPlan& P = B.P[i];
+    if (r.level == 1) {
+      int64_t m1[3];
+      grid_extent(g.n, g.L, 1, m1);
+      CopyJob c;
+      c.src = F.level1_dev;
+      c.dst = r.out_dev;
+      for (int a = 0; a < 3; a++) {
+        c.a[a] = P.OA[a];
+        c.e[a] = P.OB[a] - P.OA[a];
+      }
+      c.m1 = m1[1];
+      c.m2 = m1[2];
+      copies.push_back(c);
+      copy_max = imax(copy_max, B.npts[i]);
+      continue;
+    }
+    uint8_t* base = ws + B.req_off[i];
+    for (int sid = 1; sid < 1 + 7 * (r.level - 1); sid++) {
+      if (g.s[sid].nsym == 0) continue;
+      const SlotMap& sm = P.sm[sid];
+      const int64_t c = sm.cnt[0] * sm.cnt[1] * sm.cnt[2];
+      if (c == 0) continue;
+      DecJobMulti m;
+      memset(&m, 0, sizeof(m));
+      m.job.sid = sid;
+      for (int a = 0; a < 3; a++) {
+        m.job.lo[a] = sm.lo[a];
+        m.job.cnt[a] = sm.cnt[a];
+        m.b[a] = g.b[a];
+      }
+      m.job.slot_base = sm.base;
+      m.job.nchunks_job = c;
+      m.job.block0 = nblocks;
+      nblocks += cdiv(c * H.nsub, kDecThreads);
+      dec_stream(H, (const uint8_t*)F.comp_dev, sid, &m.ds);
+      m.sg = g.s[sid];
+      m.bvol = g.bvol;
+      m.lut = (const uint16_t*)F.tables_dev + (int64_t)sid * kLutSize;
+      m.codes = (uint16_t*)(base + P.codes);
+      m.sub_olo = (uint32_t*)(base + P.sub_olo);
+      m.status = status_dev + i;
+      if (H.d[sid].nch > 0)
+        dec_bytes += (2.0 * (double)H.d[sid].nsym + 4.0 * (double)H.d[sid].pw) * (double)c /
+                     (double)H.d[sid].nch;
+      jobs.push_back(m);
+    }
+  }
+#define STZ_TRY(x)               \
+  do {                           \
+    rc = (x);                    \
+    if (rc != STZ_OK) return rc; \
+  } while (0)
+  if (!copies.empty()) {
+    CopyJob* dcopy = (CopyJob*)(ws + B.o_copy);
+    STZ_TRY(cuda_ok(cudaMemcpyAsync(dcopy, copies.data(), sizeof(CopyJob) * copies.size(),
+                                    cudaMemcpyHostToDevice, st)));
+    const dim3 grid((unsigned)imin(cdiv(copy_max, 256), 256), (unsigned)copies.size());
+    ProfScope ps_("k_copy_box", st);
+    if (ps == 4) k_copy_boxes<float><<<grid, 256, 0, st>>>(dcopy);
+    else k_copy_boxes<double><<<grid, 256, 0, st>>>(dcopy);
+    STZ_TRY(cuda_ok(cudaGetLastError()));
+  }
+  if (!jobs.empty()) {
+    DecJobMulti* djobs = (DecJobMulti*)(ws + B.o_jobs);
+    STZ_TRY(cuda_ok(cudaMemcpyAsync(djobs, jobs.data(), sizeof(DecJobMulti) * jobs.size(),
+                                    cudaMemcpyHostToDevice, st)));
+    STZ_TRY(launch_decode_chunks_multi(djobs, (int)jobs.size(), nblocks, dec_bytes, st));
+  }
+  // each finer level of every request: one launch of each level kernel
+  std::vector<LevelArgs> la;
+  for (int j = 2; j <= B.maxlevel; j++) {
+    la.clear();
+    for (int i = 0; i < n; i++) {
+      const stz_region_request& r = reqs[i];
+      if (B.npts[i] == 0 || r.level < j) continue;
+      const stz_served_field& F = fields[r.field];
+      const Hdr& H = B.H[r.field];
+      const DecPlan& P = B.P[i];
+      uint8_t* base = ws + B.req_off[i];
+      LevelArgs a;
+      memset(&a, 0, sizeof(a));
+      a.geo = B.G[r.field];
+      a.level = j;
+      a.pred = H.pred;
+      a.dp = (const DevParams*)(base + P.dp);
+      a.coarse = j == 2 ? F.level1_dev : (const void*)(base + P.grid[j - 1]);
+      a.fine = j == r.level ? r.out_dev : (void*)(base + P.grid[j]);
+      for (int d = 0; d < 3; d++) {
+        a.clo[d] = P.A[j - 1][d];
+        a.chi[d] = P.B[j - 1][d];
+        a.flo[d] = P.A[j][d];
+        a.fhi[d] = P.B[j][d];
+        a.tlo[d] = P.tlo[j][d];
+        a.tcnt[d] = P.tcnt[j][d];
+      }
+      a.codes = (uint16_t*)(base + P.codes);
+      for (int K = 1; K <= 7; K++) {
+        const int sid = 1 + 7 * (j - 2) + K - 1;
+        a.sm[K] = P.sm[sid];
+        const uint8_t* sec = (const uint8_t*)F.comp_dev + H.d[sid].sect_off;
+        SectHost sh = sect_host(H.d[sid].nlive, H.d[sid].nch, H.d[sid].pw, H.d[sid].nout, ps,
+                                H.nsub);
+        a.opos[K] = (const uint32_t*)(sec + sh.off_opos);
+        a.oval[K] = sec + sh.off_oval;
+        a.nout[K] = (int64_t)H.d[sid].nout;
+        a.dense[K] = dense_outliers(H.d[sid].nout, H.d[sid].nsym) ? 1 : 0;
+      }
+      a.two_eb = H.two_eb[j];
+      a.status = status_dev + i;
+      a.sub_olo = (const uint32_t*)(base + P.sub_olo);
+      a.nsub = H.nsub;
+      if (level_multi_ok(a)) la.push_back(a);
+      else STZ_TRY(launch_level(a, true, st));  // other bricks or predictors: on its own
+    }
+    if (!la.empty()) STZ_TRY(launch_level_multi(la.data(), (int)la.size(), ws + B.o_level[j], st));
+  }
+#undef STZ_TRY
   return STZ_OK;
 }
 

@@ -941,10 +941,14 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__
   return (uint32_t)lo;
 }
 
-__global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
-    const __grid_constant__ Geo g, const __grid_constant__ DecTables tb,
-    const uint16_t* __restrict__ lut, uint16_t* __restrict__ codes,
-    uint32_t* __restrict__ sub_olo, uint32_t* __restrict__ status) {
+// One block's share of a chunk job: chunks [bidx * cpb, ...) of the job's
+// brick range of one stream.  lutg: the stream's decode table.
+__device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecStream& d,
+                                             const StreamGeo& sg, const int32_t gb[3],
+                                             int64_t bvol, const uint16_t* __restrict__ lutg,
+                                             uint16_t* __restrict__ codes,
+                                             uint32_t* __restrict__ sub_olo,
+                                             uint32_t* __restrict__ status, int64_t bidx) {
   extern __shared__ __align__(16) unsigned char dsm[];
   // arrays in order of alignment: the 16-byte-loaded table first, then 4-byte
   uint32_t* stage = (uint32_t*)dsm;
@@ -955,20 +959,13 @@ __global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
   int* ccnt = (int*)(cjl + kDecThreads);                          // symbols; -1: bad chunk
   __shared__ uint32_t wsum[8];
   const int tid = threadIdx.x;
-  int jb = 0;
-  for (int k = 1; k < tb.njobs; k++)
-    if (tb.jobs[k].block0 <= (int64_t)blockIdx.x) jb = k;
-  const DecChunkJob& job = tb.jobs[jb];
-  const int sid = job.sid;
   {
-    const uint4* src = (const uint4*)(lut + (int64_t)sid * kLutSize);
+    const uint4* src = (const uint4*)lutg;
     for (int i = tid; i < kLutSize / 8; i += blockDim.x) ((uint4*)t)[i] = __ldg(src + i);
   }
-  const DecStream& d = tb.ds[sid];
-  const StreamGeo& sg = g.s[sid];
   const int nsub = d.nsub;
   const int cpb = kDecThreads / nsub;  // chunks per block
-  const int64_t qb = ((int64_t)blockIdx.x - job.block0) * cpb;
+  const int64_t qb = bidx * cpb;
   const int nch = (int)min((int64_t)cpb, job.nchunks_job - qb);
   const uint32_t* coff = (const uint32_t*)(d.sect + d.off_chunks);
   const uint32_t* pay = (const uint32_t*)(d.sect + d.off_payload);
@@ -979,9 +976,9 @@ __global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
     const int r0 = q32 / (c1 * c2), rr = q32 - r0 * c1 * c2, r1 = rr / c2, r2 = rr - r1 * c2;
     const int B0 = (int)job.lo[0] + r0, B1 = (int)job.lo[1] + r1, B2 = (int)job.lo[2] + r2;
     const int64_t jl = ((int64_t)B0 * sg.nb[1] + B1) * sg.nb[2] + B2;
-    const int cnt = min(g.b[0], (int)sg.e[0] - B0 * g.b[0]) *
-                    min(g.b[1], (int)sg.e[1] - B1 * g.b[1]) *
-                    min(g.b[2], (int)sg.e[2] - B2 * g.b[2]);
+    const int cnt = min(gb[0], (int)sg.e[0] - B0 * gb[0]) *
+                    min(gb[1], (int)sg.e[1] - B1 * gb[1]) *
+                    min(gb[2], (int)sg.e[2] - B2 * gb[2]);
     const uint64_t w0 = coff[jl];
     const uint64_t w1 = jl + 1 < (int64_t)d.nchunks ? coff[jl + 1] : d.pw;
     const bool ok = w0 <= w1 && w1 <= d.pw && w1 - w0 <= (uint64_t)kMaxChunkWords;
@@ -1022,7 +1019,7 @@ __global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
       const int cnt = ccnt[c];
       const int per = (max(cnt, 0) + nsub - 1) / nsub;
       const int i0 = min(max(cnt, 0), u * per), i1 = min(max(cnt, 0), (u + 1) * per);
-      uint16_t* out = codes + (job.slot_base + qb + c) * g.bvol;
+      uint16_t* out = codes + (job.slot_base + qb + c) * bvol;
       const uint32_t words = S[c + 1] - S[c] - 2;  // garbage when the chunk is bad (unused)
       const uint64_t cbits = (uint64_t)words * 32;
       const uint16_t* soff = (const uint16_t*)(d.sect + d.off_subs) + (int64_t)cjl[c] * (nsub - 1);
@@ -1081,11 +1078,11 @@ __global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
     const int64_t jl = cjl[c];
     const int64_t B0 = jl / (sg.nb[1] * sg.nb[2]), B1 = (jl / sg.nb[2]) % sg.nb[1],
                   B2 = jl % sg.nb[2];
-    const int64_t l0 = imin(g.b[0], sg.e[0] - B0 * g.b[0]);
-    const int64_t l1 = imin(g.b[1], sg.e[1] - B1 * g.b[1]);
-    const int64_t l2 = imin(g.b[2], sg.e[2] - B2 * g.b[2]);
-    const int64_t start = B0 * g.b[0] * sg.e[1] * sg.e[2] + B1 * g.b[1] * l0 * sg.e[2] +
-                          B2 * g.b[2] * l0 * l1;
+    const int64_t l0 = imin(gb[0], sg.e[0] - B0 * gb[0]);
+    const int64_t l1 = imin(gb[1], sg.e[1] - B1 * gb[1]);
+    const int64_t l2 = imin(gb[2], sg.e[2] - B2 * gb[2]);
+    const int64_t start = B0 * gb[0] * sg.e[1] * sg.e[2] + B1 * gb[1] * l0 * sg.e[2] +
+                          B2 * gb[2] * l0 * l1;
     const int cntc = (int)(l0 * l1 * l2);
     const int per = (cntc + nsub - 1) / nsub;
     uint32_t* dst = sub_olo + (job.slot_base + qb + c) * (kNSub + 1);
@@ -1094,6 +1091,45 @@ __global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
     if (u == nsub - 1) dst[nsub] = lower_bound_u32(opos, n, start + cntc);
   }
   if (bad) atomicOr(status, kStatCorrupt);
+}
+
+__global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
+    const __grid_constant__ Geo g, const __grid_constant__ DecTables tb,
+    const uint16_t* __restrict__ lut, uint16_t* __restrict__ codes,
+    uint32_t* __restrict__ sub_olo, uint32_t* __restrict__ status) {
+  int jb = 0;
+  for (int k = 1; k < tb.njobs; k++)
+    if (tb.jobs[k].block0 <= (int64_t)blockIdx.x) jb = k;
+  const DecChunkJob& job = tb.jobs[jb];
+  const int sid = job.sid;
+  decode_block(job, tb.ds[sid], g.s[sid], g.b, g.bvol, lut + (int64_t)sid * kLutSize, codes,
+               sub_olo, status, (int64_t)blockIdx.x - job.block0);
+}
+
+// The chunk jobs of many region decodes in one launch (the batched served
+// form): each job carries its own stream, decode table and outputs.
+__global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks_multi(
+    const DecJobMulti* __restrict__ jobs, int njobs) {
+  int lo = 0, hi = njobs - 1;  // the last job whose first block is <= blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].job.block0 <= (int64_t)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const DecJobMulti& m = jobs[lo];
+  decode_block(m.job, m.ds, m.sg, m.b, m.bvol, m.lut, m.codes, m.sub_olo, m.status,
+               (int64_t)blockIdx.x - m.job.block0);
+}
+
+int launch_decode_chunks_multi(const DecJobMulti* jobs_dev, int njobs, int64_t nblocks,
+                               double bytes, cudaStream_t s) {
+  if (nblocks == 0 || njobs == 0) return STZ_OK;
+  if (cudaFuncSetAttribute(k_decode_chunks_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kDecSmem) != cudaSuccess)
+    return STZ_ERR_CUDA;
+  ProfScope ps_("k_decode_chunks", s, bytes);
+  k_decode_chunks_multi<<<(unsigned)nblocks, kDecThreads, kDecSmem, s>>>(jobs_dev, njobs);
+  return cuda_ok(cudaGetLastError());
 }
 
 int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint16_t* lut,

@@ -71,6 +71,14 @@ struct LevelArgs {
   int64_t tlo[3], tcnt[3];    // tiles (bricks of cells) to process
 };
 int launch_level(const LevelArgs& a, bool decode, cudaStream_t s);
+// The decode of level a.level for many requests in one launch of each of the
+// interior and boundary kernels (the batched served form).  Every request
+// must pass level_multi_ok and share the level and dtype.  arena_dev: device
+// memory of level_multi_arena_bytes(n) bytes that receives the arguments (a
+// copy queued on s; the host array may be reused on return).
+bool level_multi_ok(const LevelArgs& a);
+size_t level_multi_arena_bytes(int n);
+int launch_level_multi(const LevelArgs* h, int n, uint8_t* arena_dev, cudaStream_t s);
 
 // ---- stz_huffman.cu: histograms, codebooks, chunk coding ----
 // histogram of stream 0 from its slots
@@ -136,6 +144,22 @@ int launch_lut(const DecTables& tb, uint16_t* lut, uint32_t* clear, int nclear,
 int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint16_t* lut,
                          uint16_t* codes, uint32_t* sub_olo, uint32_t* status, double bytes,
                          cudaStream_t s);
+
+// Chunk jobs of many decodes in one launch (the batched served form); jobs
+// in device memory, ascending block0, each with its own table and outputs.
+struct DecJobMulti {
+  DecChunkJob job;
+  DecStream ds;
+  StreamGeo sg;
+  int32_t b[3];
+  int64_t bvol;
+  const uint16_t* lut;        // the stream's decode table
+  uint16_t* codes;
+  uint32_t* sub_olo;
+  uint32_t* status;
+};
+int launch_decode_chunks_multi(const DecJobMulti* jobs_dev, int njobs, int64_t nblocks,
+                               double bytes, cudaStream_t s);
 
 // ---- stz_container.cu: layout, header, sections, outliers ----
 struct SectDev {

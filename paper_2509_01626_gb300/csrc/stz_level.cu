@@ -19,6 +19,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <vector>
+
 namespace stz {
 
 constexpr int kLevelThreads = 256;
@@ -744,23 +746,15 @@ __device__ __forceinline__ T shell_predict(const ShellTaps<T>& t, const bool cub
   }
 }
 
-// 4 blocks per SM when decoding: the loads of a cell's taps and codes are its
-// latency.  Compressing, the shared histograms leave room for 3 at most, and
-// the registers that 3 would cost spill more than the extra warps hide.
+// One cell of the boundary shell: cell i of the shell's enumeration (cv:
+// i is inside it), its 7 fine points predicted with the per-axis rules and
+// quantized (compress) or reconstructed (decode).
 template <typename T, bool DEC>
-__global__ void __launch_bounds__(256, DEC ? 4 : 2)
-    k_level_shell(const __grid_constant__ LevelArgs a, const __grid_constant__ ShellGeo sh) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* hist = (uint32_t*)smem;
+__device__ __forceinline__ void shell_cell(const LevelArgs& a, const ShellGeo& sh, int64_t i,
+                                           bool cv, const QConst<T>& q, uint32_t* hist,
+                                           uint32_t (&nR)[7]) {
   const Geo& geo = a.geo;
   const int l = a.level;
-  const int lane = threadIdx.x & 31;
-  QConst<T> q;
-  if (!DEC) {
-    q.load(a.dp, l, kRadius);
-    for (int w = threadIdx.x; w < 7 * kHistWords; w += blockDim.x) hist[w] = 0;
-    __syncthreads();
-  }
   int64_t m64[3];
   grid_extent(geo.n, geo.L, l, m64);
   const int m[3] = {(int)m64[0], (int)m64[1], (int)m64[2]};
@@ -772,129 +766,147 @@ __global__ void __launch_bounds__(256, DEC ? 4 : 2)
   const int64_t s = level_stride(geo.L, l);
   const int64_t xst[3] = {s * geo.n[1] * geo.n[2], s * geo.n[2], s};  // field strides
   const int64_t fst[3] = {fe1 * fe2, fe2, 1};                        // fine box strides
+  int c[3] = {0, 0, 0};
+  if (cv) {
+    const int64_t nx = sh.hi[2] - sh.lo[2], ny = sh.hi[1] - sh.lo[1];
+    if (i < sh.nA) {
+      const int64_t r = i / (ny * nx);
+      c[0] = (int)sh.bv[0][r];
+      c[1] = (int)(sh.lo[1] + (i / nx) % ny);
+      c[2] = (int)(sh.lo[2] + i % nx);
+    } else if (i < sh.nA + sh.nB) {
+      const int64_t k = i - sh.nA, nbyx = sh.nb[1] * nx;
+      c[0] = (int)(sh.ilo[0] + k / nbyx);
+      c[1] = (int)sh.bv[1][(k / nx) % sh.nb[1]];
+      c[2] = (int)(sh.lo[2] + k % nx);
+    } else {
+      const int64_t k = i - sh.nA - sh.nB, iyn = sh.ihi[1] - sh.ilo[1];
+      c[0] = (int)(sh.ilo[0] + k / (iyn * sh.nb[2]));
+      c[1] = (int)(sh.ilo[1] + (k / sh.nb[2]) % iyn);
+      c[2] = (int)sh.bv[2][k % sh.nb[2]];
+    }
+  }
+  // per axis: the odd point's existence, stencil and rule; clamped taps
+  ShellTaps<T> tp;
+  bool odd_in[3], cub[3];
+  int rule[3];
+  int64_t cbase = 0;
+#pragma unroll
+  for (int ax = 0; ax < 3; ax++) {
+    const int lc = c[ax] - (int)a.clo[ax];
+    cbase += (int64_t)lc * cst[ax];
+    int* o = ax == 0 ? tp.oz : (ax == 1 ? tp.oy : tp.ox);
+#pragma unroll
+    for (int d = -1; d <= 2; d++) o[d + 1] = (min(max(lc + d, 0), ce[ax] - 1) - lc) * cst[ax];
+    const int go = 2 * c[ax] + 1;
+    odd_in[ax] = go < m[ax];
+    cub[ax] = go >= 3 && go + 3 < m[ax];
+    rule[ax] = go + 1 < m[ax] ? kMid : (go >= 3 ? kExt : kCopy);
+  }
+  tp.cb = (const T*)a.coarse + cbase;
+  const int64_t g0[3] = {2 * (int64_t)c[0], 2 * (int64_t)c[1], 2 * (int64_t)c[2]};
+  bool ev_box = true;  // the even point (copied coarse value) inside the fine box
+#pragma unroll
+  for (int ax = 0; ax < 3; ax++) ev_box = ev_box && g0[ax] >= a.flo[ax] && g0[ax] < a.fhi[ax];
+  const int64_t fidx0 = ((g0[0] - a.flo[0]) * fe1 + (g0[1] - a.flo[1])) * fe2 + (g0[2] - a.flo[2]);
+  if (cv && a.fine && ev_box) ((T*)a.fine)[fidx0] = tp(0, 0, 0);
+  // the cell's brick and place in it (the same for the 7 sub-blocks)
+  const int Bc[3] = {c[0] / geo.b[0], c[1] / geo.b[1], c[2] / geo.b[2]};
+  const int rc[3] = {c[0] - Bc[0] * geo.b[0], c[1] - Bc[1] * geo.b[1], c[2] - Bc[2] * geo.b[2]};
+  const int64_t xbase = DEC ? 0 : g0[0] * xst[0] + g0[1] * xst[1] + g0[2] * xst[2];
+#pragma unroll
+  for (int K = 1; K <= 7; K++) {
+    const int o[3] = {(K >> 2) & 1, (K >> 1) & 1, K & 1};
+    bool v = cv;
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+      if (o[ax]) v = v && odd_in[ax];
+      if (DEC) {
+        const int64_t g = g0[ax] + o[ax];
+        v = v && g >= a.flo[ax] && g < a.fhi[ax];
+      }
+    }
+    const int sid = 1 + 7 * (l - 2) + (K - 1);
+    int sym = -1;
+    if (v) {
+      const StreamGeo& sg = geo.s[sid];
+      const SlotMap& sm = a.sm[K];
+      const int l0 = min(geo.b[0], (int)sg.e[0] - Bc[0] * geo.b[0]);
+      const int l1 = min(geo.b[1], (int)sg.e[1] - Bc[1] * geo.b[1]);
+      const int l2 = min(geo.b[2], (int)sg.e[2] - Bc[2] * geo.b[2]);
+      const int local = (rc[0] * l1 + rc[1]) * l2 + rc[2];
+      const int64_t ord = ((Bc[0] - sm.lo[0]) * sm.cnt[1] + (Bc[1] - sm.lo[1])) * sm.cnt[2] +
+                          (Bc[2] - sm.lo[2]);
+      const int64_t slot = (sm.base + ord) * geo.bvol + local;
+      const int64_t fidx = fidx0 + o[0] * fst[0] + o[1] * fst[1] + o[2] * fst[2];
+      T pred;
+      switch (K) {
+        case 1: pred = shell_predict<1>(tp, cub, rule); break;
+        case 2: pred = shell_predict<2>(tp, cub, rule); break;
+        case 3: pred = shell_predict<3>(tp, cub, rule); break;
+        case 4: pred = shell_predict<4>(tp, cub, rule); break;
+        case 5: pred = shell_predict<5>(tp, cub, rule); break;
+        case 6: pred = shell_predict<6>(tp, cub, rule); break;
+        default: pred = shell_predict<7>(tp, cub, rule); break;
+      }
+      if (!DEC) {
+        const T x = __ldg((const T*)a.field + xbase + o[0] * xst[0] + o[1] * xst[1] +
+                          o[2] * xst[2]);
+        T xq;
+        sym = quantize_sel(x, pred, q, kRadius, xq);
+        a.codes[slot] = (uint16_t)sym;
+        if (a.fine) ((T*)a.fine)[fidx] = xq;
+        if (sym == 0) {
+          const int64_t chunk = ((int64_t)Bc[0] * sg.nb[1] + Bc[1]) * sg.nb[2] + Bc[2];
+          atomicAdd(&a.chunk_outliers[sg.chunk0 + chunk], 1u);
+        }
+      } else {
+        const int sy = a.codes[slot];
+        T val = dequantize(sy, pred, two_eb, kRadius);
+        if (sy == 0) {
+          const int64_t pos = (int64_t)Bc[0] * geo.b[0] * sg.e[1] * sg.e[2] +
+                              (int64_t)Bc[1] * geo.b[1] * l0 * sg.e[2] +
+                              (int64_t)Bc[2] * geo.b[2] * l0 * l1 + local;
+          if (!outlier_value(a.sub_olo, a.dense[K] != 0, sm.base + ord, local, l0 * l1 * l2,
+                             a.nsub, a.opos[K], (const T*)a.oval[K], a.nout[K], pos, val)) {
+            val = T(0);
+            atomicOr(a.status, kStatCorrupt);
+          }
+        }
+        ((T*)a.fine)[fidx] = val;
+      }
+    }
+    if (!DEC) {
+      nR[K - 1] += sym == kRadius;
+      if (sym >= 0 && sym != kRadius)
+        atomicAdd(&hist[(K - 1) * kHistWords + sym], 1u);
+    }
+  }
+}
+
+// 4 blocks per SM when decoding: the loads of a cell's taps and codes are its
+// latency.  Compressing, the shared histograms leave room for 3 at most, and
+// the registers that 3 would cost spill more than the extra warps hide.
+template <typename T, bool DEC>
+__global__ void __launch_bounds__(256, DEC ? 4 : 2)
+    k_level_shell(const __grid_constant__ LevelArgs a, const __grid_constant__ ShellGeo sh) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* hist = (uint32_t*)smem;
+  const int l = a.level;
+  const int lane = threadIdx.x & 31;
+  QConst<T> q;
+  if (!DEC) {
+    q.load(a.dp, l, kRadius);
+    for (int w = threadIdx.x; w < 7 * kHistWords; w += blockDim.x) hist[w] = 0;
+    __syncthreads();
+  }
   const int64_t total = sh.nA + sh.nB + sh.nC;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   const int64_t iters = cdiv(total, nth);
   uint32_t nR[7] = {0, 0, 0, 0, 0, 0, 0};  // zero-error symbols per stream, added at the end
   for (int64_t it = 0; it < iters; it++) {
     const int64_t i = it * nth + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool cv = i < total;
-    int c[3] = {0, 0, 0};
-    if (cv) {
-      const int64_t nx = sh.hi[2] - sh.lo[2], ny = sh.hi[1] - sh.lo[1];
-      if (i < sh.nA) {
-        const int64_t r = i / (ny * nx);
-        c[0] = (int)sh.bv[0][r];
-        c[1] = (int)(sh.lo[1] + (i / nx) % ny);
-        c[2] = (int)(sh.lo[2] + i % nx);
-      } else if (i < sh.nA + sh.nB) {
-        const int64_t k = i - sh.nA, nbyx = sh.nb[1] * nx;
-        c[0] = (int)(sh.ilo[0] + k / nbyx);
-        c[1] = (int)sh.bv[1][(k / nx) % sh.nb[1]];
-        c[2] = (int)(sh.lo[2] + k % nx);
-      } else {
-        const int64_t k = i - sh.nA - sh.nB, iyn = sh.ihi[1] - sh.ilo[1];
-        c[0] = (int)(sh.ilo[0] + k / (iyn * sh.nb[2]));
-        c[1] = (int)(sh.ilo[1] + (k / sh.nb[2]) % iyn);
-        c[2] = (int)sh.bv[2][k % sh.nb[2]];
-      }
-    }
-    // per axis: the odd point's existence, stencil and rule; clamped taps
-    ShellTaps<T> tp;
-    bool odd_in[3], cub[3];
-    int rule[3];
-    int64_t cbase = 0;
-#pragma unroll
-    for (int ax = 0; ax < 3; ax++) {
-      const int lc = c[ax] - (int)a.clo[ax];
-      cbase += (int64_t)lc * cst[ax];
-      int* o = ax == 0 ? tp.oz : (ax == 1 ? tp.oy : tp.ox);
-#pragma unroll
-      for (int d = -1; d <= 2; d++) o[d + 1] = (min(max(lc + d, 0), ce[ax] - 1) - lc) * cst[ax];
-      const int go = 2 * c[ax] + 1;
-      odd_in[ax] = go < m[ax];
-      cub[ax] = go >= 3 && go + 3 < m[ax];
-      rule[ax] = go + 1 < m[ax] ? kMid : (go >= 3 ? kExt : kCopy);
-    }
-    tp.cb = (const T*)a.coarse + cbase;
-    const int64_t g0[3] = {2 * (int64_t)c[0], 2 * (int64_t)c[1], 2 * (int64_t)c[2]};
-    bool ev_box = true;  // the even point (copied coarse value) inside the fine box
-#pragma unroll
-    for (int ax = 0; ax < 3; ax++) ev_box = ev_box && g0[ax] >= a.flo[ax] && g0[ax] < a.fhi[ax];
-    const int64_t fidx0 = ((g0[0] - a.flo[0]) * fe1 + (g0[1] - a.flo[1])) * fe2 + (g0[2] - a.flo[2]);
-    if (cv && a.fine && ev_box) ((T*)a.fine)[fidx0] = tp(0, 0, 0);
-    // the cell's brick and place in it (the same for the 7 sub-blocks)
-    const int Bc[3] = {c[0] / geo.b[0], c[1] / geo.b[1], c[2] / geo.b[2]};
-    const int rc[3] = {c[0] - Bc[0] * geo.b[0], c[1] - Bc[1] * geo.b[1], c[2] - Bc[2] * geo.b[2]};
-    const int64_t xbase = DEC ? 0 : g0[0] * xst[0] + g0[1] * xst[1] + g0[2] * xst[2];
-#pragma unroll
-    for (int K = 1; K <= 7; K++) {
-      const int o[3] = {(K >> 2) & 1, (K >> 1) & 1, K & 1};
-      bool v = cv;
-#pragma unroll
-      for (int ax = 0; ax < 3; ax++) {
-        if (o[ax]) v = v && odd_in[ax];
-        if (DEC) {
-          const int64_t g = g0[ax] + o[ax];
-          v = v && g >= a.flo[ax] && g < a.fhi[ax];
-        }
-      }
-      const int sid = 1 + 7 * (l - 2) + (K - 1);
-      int sym = -1;
-      if (v) {
-        const StreamGeo& sg = geo.s[sid];
-        const SlotMap& sm = a.sm[K];
-        const int l0 = min(geo.b[0], (int)sg.e[0] - Bc[0] * geo.b[0]);
-        const int l1 = min(geo.b[1], (int)sg.e[1] - Bc[1] * geo.b[1]);
-        const int l2 = min(geo.b[2], (int)sg.e[2] - Bc[2] * geo.b[2]);
-        const int local = (rc[0] * l1 + rc[1]) * l2 + rc[2];
-        const int64_t ord = ((Bc[0] - sm.lo[0]) * sm.cnt[1] + (Bc[1] - sm.lo[1])) * sm.cnt[2] +
-                            (Bc[2] - sm.lo[2]);
-        const int64_t slot = (sm.base + ord) * geo.bvol + local;
-        const int64_t fidx = fidx0 + o[0] * fst[0] + o[1] * fst[1] + o[2] * fst[2];
-        T pred;
-        switch (K) {
-          case 1: pred = shell_predict<1>(tp, cub, rule); break;
-          case 2: pred = shell_predict<2>(tp, cub, rule); break;
-          case 3: pred = shell_predict<3>(tp, cub, rule); break;
-          case 4: pred = shell_predict<4>(tp, cub, rule); break;
-          case 5: pred = shell_predict<5>(tp, cub, rule); break;
-          case 6: pred = shell_predict<6>(tp, cub, rule); break;
-          default: pred = shell_predict<7>(tp, cub, rule); break;
-        }
-        if (!DEC) {
-          const T x = __ldg((const T*)a.field + xbase + o[0] * xst[0] + o[1] * xst[1] +
-                            o[2] * xst[2]);
-          T xq;
-          sym = quantize_sel(x, pred, q, kRadius, xq);
-          a.codes[slot] = (uint16_t)sym;
-          if (a.fine) ((T*)a.fine)[fidx] = xq;
-          if (sym == 0) {
-            const int64_t chunk = ((int64_t)Bc[0] * sg.nb[1] + Bc[1]) * sg.nb[2] + Bc[2];
-            atomicAdd(&a.chunk_outliers[sg.chunk0 + chunk], 1u);
-          }
-        } else {
-          const int sy = a.codes[slot];
-          T val = dequantize(sy, pred, two_eb, kRadius);
-          if (sy == 0) {
-            const int64_t pos = (int64_t)Bc[0] * geo.b[0] * sg.e[1] * sg.e[2] +
-                                (int64_t)Bc[1] * geo.b[1] * l0 * sg.e[2] +
-                                (int64_t)Bc[2] * geo.b[2] * l0 * l1 + local;
-            if (!outlier_value(a.sub_olo, a.dense[K] != 0, sm.base + ord, local, l0 * l1 * l2,
-                               a.nsub, a.opos[K], (const T*)a.oval[K], a.nout[K], pos, val)) {
-              val = T(0);
-              atomicOr(a.status, kStatCorrupt);
-            }
-          }
-          ((T*)a.fine)[fidx] = val;
-        }
-      }
-      if (!DEC) {
-        nR[K - 1] += sym == kRadius;
-        if (sym >= 0 && sym != kRadius)
-          atomicAdd(&hist[(K - 1) * kHistWords + sym], 1u);
-      }
-    }
+    shell_cell<T, DEC>(a, sh, i, i < total, q, hist, nR);
   }
   if (!DEC) {
 #pragma unroll
@@ -904,6 +916,99 @@ __global__ void __launch_bounds__(256, DEC ? 4 : 2)
     }
     __syncthreads();
     flush_hist<T>(hist, a.hist, l);
+  }
+}
+
+// ------------------------------------------------------ many decodes at once
+// The batched served form: the level-l decode of many region requests in one
+// launch.  args[r] (device memory) is request r's LevelArgs; its tiles
+// (shell cells) are the global indices [tile0[r], tile0[r + 1]).  Every tile
+// runs exactly as in k_level_fast (k_level_shell) with its own request's
+// arguments, so each output is bitwise the single-request decode.
+__device__ __forceinline__ int request_of(const int64_t* __restrict__ first, int n, int64_t t) {
+  int lo = 0, hi = n - 1;  // the last r with first[r] <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, bool PAIR>
+__global__ void __launch_bounds__(kLevelThreads, 2)
+    k_level_fast_multi(const LevelArgs* __restrict__ args, const int64_t* __restrict__ tile0,
+                       int n) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileInfo s_ti[2];
+  constexpr int tvol = (kFBZ + 3) * kFEZY;
+  constexpr size_t tbytes = ((size_t)tvol * sizeof(T) + 15) & ~(size_t)15;
+  T* tiles[2] = {(T*)smem, (T*)(smem + tbytes)};
+  const int64_t ntiles = tile0[n];
+  constexpr int epc = 16 / sizeof(T);
+  auto prefetch = [&](const LevelArgs& a, int64_t t, T* tile) {
+    const bool vec = ((uintptr_t)a.coarse & 15) == 0 && (a.chi[2] - a.clo[2]) % epc == 0 &&
+                     a.clo[2] % epc == 0;
+    if (vec) tile_prefetch<T, true>(a, t, tile);
+    else tile_prefetch<T, false>(a, t, tile);
+  };
+  QConst<T> q;  // unused when decoding
+  int64_t tt = blockIdx.x;
+  int b = 0;
+  if (tt < ntiles) {
+    const int r = request_of(tile0, n, tt);
+    tile_info(args[r], tt - tile0[r], s_ti[0]);
+    prefetch(args[r], tt - tile0[r], tiles[0]);
+  }
+  for (; tt < ntiles; tt += gridDim.x, b ^= 1) {
+    cp_async_wait_all();
+    __syncthreads();
+    const int r = request_of(tile0, n, tt);
+    const LevelArgs& a = args[r];
+    const int64_t nt = tt + gridDim.x;
+    if (nt < ntiles) {
+      const int r2 = request_of(tile0, n, nt);
+      tile_info(args[r2], nt - tile0[r2], s_ti[b ^ 1]);
+      prefetch(args[r2], nt - tile0[r2], tiles[b ^ 1]);
+    }
+    const Geo& geo = a.geo;
+    int64_t M64[3];
+    grid_extent(geo.n, geo.L, a.level - 1, M64);
+    const int M[3] = {(int)M64[0], (int)M64[1], (int)M64[2]};
+    const int64_t sl = level_stride(geo.L, a.level);
+    const int xdz = (int)(sl * geo.n[1] * geo.n[2]), xdy = (int)(sl * geo.n[2]), xdx = (int)sl;
+    const int fe2 = (int)(a.fhi[2] - a.flo[2]);
+    const int fdz = (int)((a.fhi[1] - a.flo[1]) * fe2);
+    const T two_eb = (T)a.two_eb;
+    const TileInfo& ti = s_ti[b];
+    bool full = true;
+#pragma unroll
+    for (int K = 1; K <= 7; K++)
+      full = full && ti.l[K][0] == kFBZ && ti.l[K][1] == kFBY && ti.l[K][2] == kFBX;
+    if (full)
+      fast_tile<T, true, true, PAIR>(a, tiles[b], ti, M, q, two_eb, nullptr, xdz, xdy, xdx, fe2,
+                                     fdz);
+    else
+      fast_tile<T, true, false, PAIR>(a, tiles[b], ti, M, q, two_eb, nullptr, xdz, xdy, xdx, fe2,
+                                      fdz);
+  }
+  cp_async_wait_all();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 4)
+    k_level_shell_multi(const LevelArgs* __restrict__ args, const ShellGeo* __restrict__ shs,
+                        const int64_t* __restrict__ cell0, int n) {
+  QConst<T> q;  // unused when decoding
+  uint32_t nR[7] = {0, 0, 0, 0, 0, 0, 0};
+  const int64_t total = cell0[n];
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = cdiv(total, nth);
+  for (int64_t it = 0; it < iters; it++) {
+    const int64_t i = it * nth + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool cv = i < total;
+    const int r = cv ? request_of(cell0, n, i) : 0;
+    shell_cell<T, true>(args[r], shs[r], cv ? i - cell0[r] : 0, cv, q, nullptr, nR);
   }
 }
 
@@ -1049,6 +1154,94 @@ static int run_level(const LevelArgs& a, cudaStream_t s) {
   int rc = run_level_fast<T, DEC>(a, M, (double)(cells - nshell) * bpc, s);
   if (rc != STZ_OK) return rc;
   return run_level_shell<T, DEC>(a, sh, (double)nshell * bpc, s);
+}
+
+// ---- the batched served form: one level of many region decodes ----
+bool level_multi_ok(const LevelArgs& a) {
+  const int64_t sl = level_stride(a.geo.L, a.level);
+  const int64_t fe = (a.fhi[1] - a.flo[1]) * (a.fhi[2] - a.flo[2]);
+  return a.pred == kPredCubic && a.geo.b[0] == kFBZ && a.geo.b[1] == kFBY &&
+         a.geo.b[2] == kFBX && 2 * kFBZ * sl * a.geo.n[1] * a.geo.n[2] < ((int64_t)1 << 31) &&
+         2 * kFBZ * fe < ((int64_t)1 << 31);
+}
+
+static size_t al256l(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t level_multi_arena_bytes(int n) {
+  return al256l(sizeof(LevelArgs) * (size_t)n) + al256l(sizeof(ShellGeo) * (size_t)n) +
+         2 * al256l(sizeof(int64_t) * (size_t)(n + 1));
+}
+
+template <typename T>
+static int run_level_multi(const LevelArgs* h, int n, uint8_t* arena, cudaStream_t s) {
+  std::vector<uint8_t> buf(level_multi_arena_bytes(n), 0);
+  const size_t o_sh = al256l(sizeof(LevelArgs) * (size_t)n);
+  const size_t o_t0 = o_sh + al256l(sizeof(ShellGeo) * (size_t)n);
+  const size_t o_c0 = o_t0 + al256l(sizeof(int64_t) * (size_t)(n + 1));
+  ShellGeo* shs = (ShellGeo*)(buf.data() + o_sh);
+  int64_t* tile0 = (int64_t*)(buf.data() + o_t0);
+  int64_t* cell0 = (int64_t*)(buf.data() + o_c0);
+  memcpy(buf.data(), h, sizeof(LevelArgs) * (size_t)n);
+  bool pair = true;
+  double fast_bytes = 0.0, shell_bytes = 0.0;
+  tile0[0] = cell0[0] = 0;
+  for (int r = 0; r < n; r++) {
+    const LevelArgs& a = h[r];
+    int64_t M[3];
+    grid_extent(a.geo.n, a.geo.L, a.level - 1, M);
+    const int64_t cells = shell_geo(a, M, &shs[r]);
+    const int64_t nshell = shs[r].nA + shs[r].nB + shs[r].nC;
+    // interior cells exist only with M >= 4 on every axis
+    const bool interior = M[0] >= 4 && M[1] >= 4 && M[2] >= 4 && cells > 0;
+    tile0[r + 1] = tile0[r] + (interior ? a.tcnt[0] * a.tcnt[1] * a.tcnt[2] : 0);
+    cell0[r + 1] = cell0[r] + nshell;
+    const uintptr_t a2 = 2 * sizeof(T);
+    pair = pair && (uintptr_t)a.fine % a2 == 0 && (a.fhi[2] - a.flo[2]) % 2 == 0 &&
+           a.flo[2] % 2 == 0;
+    const double bpc = cell_bytes<T, true>(a);
+    fast_bytes += (double)(cells - nshell) * bpc;
+    shell_bytes += (double)nshell * bpc;
+  }
+  if (cudaMemcpyAsync(arena, buf.data(), buf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return STZ_ERR_CUDA;
+  const LevelArgs* args = (const LevelArgs*)arena;
+  const ShellGeo* dsh = (const ShellGeo*)(arena + o_sh);
+  const int64_t* dt0 = (const int64_t*)(arena + o_t0);
+  const int64_t* dc0 = (const int64_t*)(arena + o_c0);
+  char nm[48];
+  if (tile0[n] > 0) {
+    const size_t smem = 2 * (((size_t)(kFBZ + 3) * kFEZY * sizeof(T) + 15) & ~(size_t)15);
+    auto kern = pair ? k_level_fast_multi<T, true> : k_level_fast_multi<T, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return STZ_ERR_CUDA;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLevelThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = imin(tile0[n], (int64_t)sm_count() * per_sm);
+    snprintf(nm, sizeof(nm), "k_level%d_dec_%s", h[0].level, sizeof(T) == 4 ? "f32" : "f64");
+    ProfScope ps_(nm, s, fast_bytes);
+    kern<<<(unsigned)grid, kLevelThreads, smem, s>>>(args, dt0, n);
+    if (cudaGetLastError() != cudaSuccess) return STZ_ERR_CUDA;
+  }
+  if (cell0[n] > 0) {
+    const int64_t grid = imin(cdiv(cell0[n], 256), (int64_t)sm_count() * 4);
+    snprintf(nm, sizeof(nm), "k_level%d_shell_dec_%s", h[0].level,
+             sizeof(T) == 4 ? "f32" : "f64");
+    ProfScope ps_(nm, s, shell_bytes);
+    k_level_shell_multi<T><<<(unsigned)grid, 256, 0, s>>>(args, dsh, dc0, n);
+    if (cudaGetLastError() != cudaSuccess) return STZ_ERR_CUDA;
+  }
+  return STZ_OK;
+}
+
+int launch_level_multi(const LevelArgs* h, int n, uint8_t* arena_dev, cudaStream_t s) {
+  if (n <= 0) return STZ_OK;
+  for (int r = 0; r < n; r++)
+    if (!level_multi_ok(h[r]) || h[r].level != h[0].level || h[r].geo.dtype != h[0].geo.dtype)
+      return STZ_ERR_ARG;
+  return h[0].geo.dtype == STZ_F32 ? run_level_multi<float>(h, n, arena_dev, s)
+                                   : run_level_multi<double>(h, n, arena_dev, s);
 }
 
 int launch_level(const LevelArgs& a, bool decode, cudaStream_t s) {

@@ -12,6 +12,9 @@ grid is decoded once when the field is loaded and reused by every request
 from a host copy.  Completion is polled with events; latency = completion
 time - arrival time, on the host clock.
 
+``BatchServer`` batches the requests of each admission round into one
+``stz_decode_requests`` call: a fixed number of kernel launches per round.
+
 ``serial`` is the plain path for comparison: one synchronous
 ``stz_decompress_region`` per request, in arrival order.
 """
@@ -157,6 +160,131 @@ class Server:
                     results.append(Result(r, now - r.arrival, shape, 0, out))
                     index.append(i)
                     free.append(s)
+        wall = time.perf_counter() - t0
+        torch.cuda.synchronize(self.device)
+        st = status.cpu().numpy()
+        for res, i in zip(results, index):
+            res.status = int(st[i])
+        if st.any():
+            raise RuntimeError(f"{int((st != 0).sum())} request decodes reported a corrupt "
+                               "container")
+        return results, wall
+
+
+class BatchServer:
+    """The served form with batched launches: every admission round takes up
+    to ``max_batch`` waiting requests (in arrival order) and decodes them
+    with one ``stz_decode_requests`` call -- a fixed number of kernel
+    launches whatever the number of requests -- on one of ``nbatch`` streams;
+    rounds that start while others run overlap with them on the GPU
+    (continuous batching).  Each field's level-1 grid and decode tables are
+    built once when the field is loaded."""
+
+    def __init__(self, containers, budget_bytes: int, max_edge: int = 256, max_batch: int = 16,
+                 max_inflight: int = 4, device=None):
+        self.device = device or containers[0].device
+        self.max_edge = int(max_edge)
+        self.fields = [_Field(c, True) for c in containers]
+        self.tables = [stz.decode_tables(f.comp, f.hdr) for f in self.fields]
+        self.farr = stz.served_fields([(f.comp, f.hdr, f.level1, t)
+                                       for f, t in zip(self.fields, self.tables)])
+        # the largest request: a max_edge box at full resolution, sized for
+        # any placement (128 points wider, as in Server); a batch of them
+        # bounds every batch's workspace
+        shape = self.fields[0].meta["shape"]
+        itemsize = 8 if self.fields[0].meta["dtype"] == torch.float64 else 4
+        npts = 1
+        for d in shape:
+            npts *= min(max_edge, d)
+        self.slot_out = npts * itemsize
+        probe_out = torch.empty(16, dtype=torch.uint8, device=self.device)
+        mb = int(max_batch)
+        while True:
+            reqs = (stz.RegionRequest * mb)()
+            for q in reqs:
+                q.field = 0
+                q.level = self.fields[0].meta["levels"]
+                for a, d in enumerate(shape):
+                    q.lo[a] = 0
+                    q.hi[a] = min(max_edge + 128, d)
+                q.out_dev = probe_out.data_ptr()
+                q.out_cap = 1 << 62
+            ws = stz.decode_requests_workspace(reqs, self.farr)
+            if ws == 0:
+                raise ValueError("cannot size the batch workspace")
+            per = ws + mb * self.slot_out
+            if per * 2 <= budget_bytes or mb == 1:
+                break
+            mb = max(1, mb // 2)
+        self.max_batch = mb
+        self.nbatch = int(max(1, min(max_inflight, budget_bytes // per)))
+        self.ws = [torch.empty(ws, dtype=torch.uint8, device=self.device)
+                   for _ in range(self.nbatch)]
+        self.outs = [torch.empty(mb * self.slot_out, dtype=torch.uint8, device=self.device)
+                     for _ in range(self.nbatch)]
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.nbatch)]
+        self.events = [torch.cuda.Event() for _ in range(self.nbatch)]
+
+    def _launch(self, b: int, batch, status: torch.Tensor):
+        reqs = (stz.RegionRequest * len(batch))()
+        base = self.outs[b].data_ptr()
+        for k, (q, (_, r)) in enumerate(zip(reqs, batch)):
+            if any(h - l > self.max_edge for l, h in zip(r.lo, r.hi)):
+                raise ValueError(f"box edge above the server's maximum {self.max_edge}: {r}")
+            q.field = r.field
+            q.level = r.level
+            for a in range(len(r.lo)):
+                q.lo[a] = r.lo[a]
+                q.hi[a] = r.hi[a]
+            q.out_dev = base + k * self.slot_out
+            q.out_cap = self.slot_out
+        stz.decode_requests(reqs, self.farr, self.ws[b], status, stream=self.streams[b])
+        self.events[b].record(self.streams[b])
+        return [tuple(int(v) for v in q.out_dims[:len(self.fields[q.field].meta["shape"])])
+                for q in reqs]
+
+    def run(self, requests, keep_outputs: bool = False, realtime: bool = True):
+        """Serve the requests; returns the results in completion order and the
+        wall time of the run (as Server.run)."""
+        order = sorted(range(len(requests)), key=lambda i: requests[i].arrival)
+        pending = collections.deque(requests[i] for i in order)
+        # one status word per request, in arrival order: a batch's requests are
+        # consecutive in that order, so its words are one contiguous run
+        status = torch.zeros(max(1, len(requests)), dtype=torch.int32, device=self.device)
+        waiting = collections.deque()
+        free = list(range(self.nbatch - 1, -1, -1))
+        inflight = {}
+        results, index = [], []
+        moved = 0  # requests moved to `waiting` so far = arrival-order index of the next
+        t0 = time.perf_counter()
+        while pending or waiting or inflight:
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0].arrival <= now):
+                waiting.append((moved, pending.popleft()))
+                moved += 1
+            while waiting and free:
+                batch = [waiting.popleft() for _ in range(min(self.max_batch, len(waiting)))]
+                b = free.pop()
+                k0 = batch[0][0]
+                shapes = self._launch(b, batch, status[k0:k0 + len(batch)])
+                inflight[b] = (batch, shapes)
+            done = [b for b in inflight if self.events[b].query()]
+            if done:
+                now = time.perf_counter() - t0
+                for b in done:
+                    batch, shapes = inflight.pop(b)
+                    for k, ((i, r), shape) in enumerate(zip(batch, shapes)):
+                        out = None
+                        if keep_outputs:
+                            n = int(np.prod(shape)) if len(shape) else 0
+                            dt = self.fields[r.field].meta["dtype"]
+                            with torch.cuda.stream(self.streams[b]):
+                                off = k * self.slot_out
+                                out = self.outs[b][off:off + self.slot_out].view(dt)[:n] \
+                                    .reshape(shape).clone()
+                        results.append(Result(r, now - r.arrival, shape, 0, out))
+                        index.append(i)
+                    free.append(b)
         wall = time.perf_counter() - t0
         torch.cuda.synchronize(self.device)
         st = status.cpu().numpy()

@@ -75,6 +75,22 @@ class BatchOpts(ctypes.Structure):
                 ("use_graph", ctypes.c_int)]
 
 
+class ServedField(ctypes.Structure):
+    """stz_served_field: a resident container with its cached level-1 grid
+    and decode tables."""
+    _fields_ = [("comp_dev", ctypes.c_void_p), ("comp_bytes", ctypes.c_size_t),
+                ("hdr_host", ctypes.c_void_p), ("hdr_bytes", ctypes.c_size_t),
+                ("level1_dev", ctypes.c_void_p), ("tables_dev", ctypes.c_void_p)]
+
+
+class RegionRequest(ctypes.Structure):
+    """stz_region_request: one box of a batched decode."""
+    _fields_ = [("field", ctypes.c_int), ("level", ctypes.c_int),
+                ("lo", ctypes.c_int64 * 3), ("hi", ctypes.c_int64 * 3),
+                ("out_dev", ctypes.c_void_p), ("out_cap", ctypes.c_size_t),
+                ("out_dims", ctypes.c_int64 * 3)]
+
+
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_ulonglong),
                 ("total_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double)]
@@ -130,6 +146,15 @@ def lib() -> ctypes.CDLL:
                                      ctypes.c_int, ctypes.c_double, vp, sz, vp, i64p, vp, sz, vp]
         L.stz_decompress_region_async.argtypes = [vp, sz, vp, sz, vp, i64p, i64p, ctypes.c_int,
                                                   vp, sz, i64p, vp, sz, vp, vp]
+        L.stz_decode_tables_size.restype = sz
+        L.stz_decode_tables_size.argtypes = [vp, sz, sz]
+        L.stz_decode_tables.argtypes = [vp, sz, vp, sz, vp, sz, vp]
+        L.stz_decode_requests_workspace.restype = sz
+        L.stz_decode_requests_workspace.argtypes = [ctypes.c_int, ctypes.POINTER(RegionRequest),
+                                                    ctypes.POINTER(ServedField), ctypes.c_int]
+        L.stz_decode_requests.argtypes = [ctypes.c_int, ctypes.POINTER(RegionRequest),
+                                          ctypes.POINTER(ServedField), ctypes.c_int, vp, sz, vp,
+                                          vp]
         L.stz_launch_count.restype = ctypes.c_ulonglong
         L.stz_profile_enable.argtypes = [ctypes.c_int]
         L.stz_profile_read.argtypes = [ctypes.POINTER(_KernelTime), ctypes.c_int]
@@ -444,6 +469,49 @@ def decompress_region_async(comp: torch.Tensor, hdr: bytes, lo, hi, level: int,
         workspace.numel(), ctypes.c_void_p(status.data_ptr()), _stream(stream))
     _check(rc, "stz_decompress_region_async")
     return tuple(int(v) for v in od[: len(lo)])
+
+
+def decode_tables(comp: torch.Tensor, hdr: bytes, stream=None) -> torch.Tensor:
+    """stz_decode_tables: the container's decode tables (uint8 CUDA tensor),
+    built once per resident field for stz_decode_requests."""
+    n = int(lib().stz_decode_tables_size(hdr, len(hdr), comp.numel()))
+    if n == 0:
+        raise StzError(ERR_CORRUPT, "stz_decode_tables_size")
+    t = torch.empty(n, dtype=torch.uint8, device=comp.device)
+    rc = lib().stz_decode_tables(ctypes.c_void_p(comp.data_ptr()), comp.numel(), hdr, len(hdr),
+                                 ctypes.c_void_p(t.data_ptr()), n, _stream(stream))
+    _check(rc, "stz_decode_tables")
+    return t
+
+
+def served_fields(entries):
+    """ctypes array of ServedField from (comp, hdr bytes, level1, tables)
+    tuples; the caller keeps the tensors and the bytes alive."""
+    arr = (ServedField * len(entries))()
+    for f, (comp, hdr, level1, tables) in zip(arr, entries):
+        f.comp_dev = comp.data_ptr()
+        f.comp_bytes = comp.numel()
+        f.hdr_host = ctypes.cast(ctypes.c_char_p(hdr), ctypes.c_void_p).value
+        f.hdr_bytes = len(hdr)
+        f.level1_dev = level1.data_ptr()
+        f.tables_dev = tables.data_ptr()
+    return arr
+
+
+def decode_requests_workspace(reqs, fields) -> int:
+    return int(lib().stz_decode_requests_workspace(len(reqs), reqs, fields, len(fields)))
+
+
+def decode_requests(reqs, fields, workspace: torch.Tensor, status: torch.Tensor,
+                    stream=None) -> None:
+    """stz_decode_requests: decode every request of the ctypes RegionRequest
+    array `reqs` in a fixed number of launches, without waiting; `status`
+    (int32 CUDA tensor, one entry per request) receives each request's
+    status, and reqs[i].out_dims its output shape."""
+    rc = lib().stz_decode_requests(len(reqs), reqs, fields, len(fields),
+                                   ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                   ctypes.c_void_p(status.data_ptr()), _stream(stream))
+    _check(rc, "stz_decode_requests")
 
 
 def launch_count() -> int:
