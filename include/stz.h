@@ -198,7 +198,9 @@ int stz_decompress_region(const void* comp_dev, size_t comp_bytes, const int64_t
  *               all as for stz_compress; no two jobs may share a workspace
  *   sizes_dev   device array of n u64 (8-byte aligned): receives the
  *               container size of field i, with bit 63 set when out_cap was
- *               too small (the low bits then hold the size needed)
+ *               too small (the low bits then hold the size needed) and bit 62
+ *               set when a bounded wait for an asynchronous copy ran out
+ *               (STZ_ERR_TIMEOUT of stz_compress)
  *   opts        NULL for defaults (lanes 4, sm_share_den 1, no graph)
  *   stream      the caller's stream; the batch is ordered after the work
  *               queued on it before the call, and work queued after the call

@@ -648,6 +648,7 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
     a.codes = codes;
     a.chunk_outliers = chunk_out;
     a.hist = hist;
+    a.status = &dp->status;
     for (int K = 1; K <= 7; K++) {
       const StreamGeo& sg = g.s[1 + 7 * (l - 2) + K - 1];
       for (int d = 0; d < 3; d++) {
@@ -920,6 +921,7 @@ int stz_compress_ex(const void* field_dev, const int64_t* dims, int ndim, stz_dt
   memcpy(r, hres, sizeof(r));
   *out_bytes = (size_t)r[0];
   prof_add_bytes("k_pack", 4.0 * (double)r[1]);
+  if (r[2] & kStatTimeout) return STZ_ERR_TIMEOUT;
   if (r[2] & kStatCapacity) return STZ_ERR_CAPACITY;
   return STZ_OK;
 }
@@ -1425,6 +1427,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     uint32_t hs = 0;
     STZ_TRY(cuda_ok(cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st)));
     STZ_TRY(cuda_ok(cudaStreamSynchronize(st)));
+    if (hs & kStatTimeout) return STZ_ERR_TIMEOUT;
     return (hs & kStatCorrupt) ? STZ_ERR_CORRUPT : STZ_OK;
   }
   // the status word, and for a cached header the header bytes beside it
@@ -1450,6 +1453,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     return decode_core(comp_dev, comp_bytes, lo_in, hi_in, level, whole, out_dev, out_cap,
                        out_dims, ws_dev, ws_bytes, st, o2);
   }
+  if (hstat & kStatTimeout) return STZ_ERR_TIMEOUT;
   return (hstat & kStatCorrupt) ? STZ_ERR_CORRUPT : STZ_OK;
 #undef STZ_EARLY
 }

@@ -31,6 +31,7 @@ __global__ void k_batch_size(const unsigned long long* __restrict__ total,
   if (threadIdx.x == 0) {
     unsigned long long v = *total;
     if (*status & kStatCapacity) v |= 1ull << 63;
+    if (*status & kStatTimeout) v |= 1ull << 62;
     *out = v;
   }
 }

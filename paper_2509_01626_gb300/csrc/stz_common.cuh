@@ -38,6 +38,7 @@ constexpr int kBrick2D[3] = {1, 32, 64};
 // status bits written by kernels into DevParams::status
 constexpr uint32_t kStatCorrupt = 1u;
 constexpr uint32_t kStatCapacity = 2u;
+constexpr uint32_t kStatTimeout = 4u;  // a bounded wait for an asynchronous copy ran out
 
 #define STZ_HD __host__ __device__ __forceinline__
 
