@@ -66,6 +66,12 @@ def parse_args():
     p.add_argument("--no-large", action="store_true",
                    help="skip the 1024^3 f32 / 768^3 f64 section")
     p.add_argument("--no-ablation", action="store_true", help="skip the predictor ablation")
+    p.add_argument("--write-traffic", nargs=4, metavar=("KERNEL", "NCU_RAW_CSV", "BENCH_JSON",
+                                                        "CAPTURE"),
+                   help="record KERNEL's DRAM traffic per algorithmic byte in "
+                        "profiles/ncu_traffic.json from an ncu raw CSV (ncu -i REP --page raw "
+                        "--csv) of one bench step and that step's bench line (same size, with "
+                        "the kernel timer on); CAPTURE describes the ncu command; then exit")
     return p.parse_args()
 
 
@@ -95,7 +101,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
             time.sleep(0.3)
         except (OSError, FileNotFoundError):
@@ -183,6 +189,57 @@ def traffic_ratio(kernel):
     if h.hexdigest() != e["sources_sha256"]:
         return None
     return float(e["dram_bytes"]) / float(e["algo_bytes"])
+
+
+# sources whose hash keys a recorded traffic ratio (any change voids it)
+TRAFFIC_SOURCES = {
+    "k_decode_chunks": ["paper_2509_01626_gb300/csrc/stz_huffman.cu"],
+    "k_level": ["paper_2509_01626_gb300/csrc/stz_level.cu",
+                "paper_2509_01626_gb300/csrc/stz_predict.cuh"],
+}
+COMMON_SOURCES = ["paper_2509_01626_gb300/csrc/stz_common.cuh",
+                  "paper_2509_01626_gb300/csrc/stz_kernels.cuh",
+                  "paper_2509_01626_gb300/csrc/stz_prof.cuh", "include/stz.h"]
+
+
+def write_traffic(kernel, ncu_csv, bench_json, capture):
+    """DRAM bytes (read + written) of every captured launch of `kernel` over
+    the algorithmic bytes the library counted for one bench step, into
+    profiles/ncu_traffic.json.  The capture must hold exactly one step's
+    launches of the kernel (ncu -c with the step's launch count)."""
+    import csv
+
+    rows = list(csv.reader(open(ncu_csv)))
+    head = rows[0]
+    ci = {n: i for i, n in enumerate(head)}
+    dram = 0.0
+    n = 0
+    for r in rows[2:]:  # row 1 holds the units
+        if len(r) < len(head):
+            continue
+        scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+        for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            dram += float(r[ci[m]].replace(",", "")) * scale.get(rows[1][ci[m]], 1.0)
+        n += 1
+    line = [ln for ln in open(bench_json) if ln.startswith("{")][0]
+    d = json.loads(line)
+    k = [e for e in d["kernels"] if e["kernel"] == kernel][0]
+    algo = k["achieved_gbs"] * 1e9 * k["ms_per_step"] * 1e-3  # bytes of one step
+    if abs(k["launches_per_step"] - n) > 1e-6:
+        raise SystemExit(f"captured {n} launches, the step has {k['launches_per_step']}")
+    key = "k_decode_chunks" if kernel.startswith("k_decode") else "k_level"
+    srcs = TRAFFIC_SOURCES[key] + COMMON_SOURCES
+    h = hashlib.sha256()
+    for src in srcs:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    table = json.load(open(path)) if os.path.exists(path) else {}
+    table[kernel] = {"sources": srcs, "sources_sha256": h.hexdigest(), "dram_bytes": dram,
+                     "algo_bytes": algo, "launches": n, "capture": capture}
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1)
+    print(json.dumps({kernel: table[kernel]}))
 
 
 # ------------------------------------------------------------------ our arm
@@ -294,6 +351,31 @@ def run_ours(args, rank, world, local_rank):
         stz.decompress_region(comp, lo, hi, int(lv), out=reg_out, workspace=ws, meta=meta)
         lat.append((time.perf_counter() - a) * 1e3)
     lat = np.array(lat)
+
+    # the ROI workflow of Sec. 3.3: decode level 1 (the 1/64 coarse grid),
+    # select the top 1% of its 4^3 blocks by value range, decode those regions
+    # at full resolution
+    coarse = stz.decompress_progressive(comp, 1, workspace=ws, meta=meta).clone()
+    for _ in range(3):
+        stz.roi_select(coarse, (4, 4, 4), "range", "top", 0.01)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    roi_ms = []
+    for _ in range(10):
+        ev[0].record(stream)
+        sel = stz.roi_select(coarse, (4, 4, 4), "range", "top", 0.01)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        roi_ms.append(ev[0].elapsed_time(ev[1]))
+    boxes_roi = stz.roi_boxes(sel.cpu().numpy(), tuple(coarse.shape), (4, 4, 4), 4, shape)
+    t = time.perf_counter()
+    for lo, hi in boxes_roi:
+        stz.decompress_region(comp, lo, hi, 3, out=reg_out, workspace=ws, meta=meta)
+    torch.cuda.synchronize()
+    roi = {"select_ms": round(float(np.median(roi_ms)), 4), "units": int(coarse.numel() // 64),
+           "selected": len(boxes_roi),
+           "regions_ms": round((time.perf_counter() - t) * 1e3, 3),
+           "workflow": "level-1 decode, top 1% of 4^3 blocks by range, 16^3 regions at level 3"}
 
     # end to end through the same calls, host buffers, copies timed.  The
     # copies run on two copy streams (one per direction) beside the compute:
@@ -409,7 +491,7 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(field_bytes + comp_bytes),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)}
 
-    return dict(ms_step=ms_step, op_ms=op_ms, lat=lat, kernels=kernels, e2e=e2e, clk=clk,
+    return dict(ms_step=ms_step, op_ms=op_ms, lat=lat, kernels=kernels, e2e=e2e, clk=clk, roi=roi,
                 comp_bytes=comp_bytes, field_bytes=field_bytes, launches=launches,
                 x_host=x_host)
 
@@ -704,7 +786,9 @@ def oracle_sample(x, edge):
     return np.ascontiguousarray(x[:s, :s, :s])
 
 
-def run_cpu_baseline(x, eb, edge=256):
+def run_cpu_baseline(x, eb, edge=512):
+    """One step of the oracle, single-threaded, on the bench's own field (the
+    whole 512^3 field: about 20 s of CPU work)."""
     from oracle import oracle as ora
 
     ora.build()
@@ -712,9 +796,11 @@ def run_cpu_baseline(x, eb, edge=256):
     t = time.perf_counter()
     oracle_step(ora, xs, eb)
     dt = time.perf_counter() - t
+    whole = xs.shape[0] == x.shape[0]
     return {"value": round(xs.nbytes / dt / 1e9, 5), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"one step (compress, full, progressive 1-2, 64^3 box, slice) on the "
-                      f"{xs.shape[0]}^3 corner of the field, single thread",
+            "sample": "one step (compress, full, progressive 1-2, 64^3 box, slice) on "
+                      + ("the whole field" if whole else f"the {xs.shape[0]}^3 corner of the field")
+                      + ", single thread",
             "seconds": round(dt, 3)}
 
 
@@ -762,6 +848,9 @@ def workload_config(args):
 # ---------------------------------------------------------------------- main
 def main():
     args = parse_args()
+    if args.write_traffic:
+        write_traffic(*args.write_traffic)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -858,6 +947,7 @@ def main():
                               "p99": round(float(np.percentile(lat, 99)), 4),
                               "n": int(lat.size), "edges": "16-256", "levels": "1-3"},
         "compression_ratio": round(fb / r["comp_bytes"], 3),
+        "roi": r["roi"],
         "roofline": roofline, "cpu_baseline": cpu, "e2e": r["e2e"],
         "gpu_launches": int(r["launches"]), "clocks": r["clk"], "kernels": breakdown[:12],
         "bounds": bounds, "large": large, "ablation": ablation,

@@ -142,6 +142,20 @@ __device__ __forceinline__ Addr32 addr0(const StreamGeo& sg, const int32_t b[3],
   return r;
 }
 
+// The value of an outlier of stream 0 at address ad (a rare path, kept out of
+// line so that it costs the passes no registers); a missing entry marks the
+// container corrupt and gives 0.
+template <typename T>
+__device__ __noinline__ T base_outlier(const BaseArgs& a, const Addr32& ad) {
+  T v;
+  if (!outlier_value(a.sub_olo, a.dense != 0, ad.sidx, ad.local, ad.cnt, a.nsub, a.opos,
+                     (const T*)a.oval, a.nout, ad.pos, v)) {
+    v = T(0);
+    atomicOr(a.status, kStatCorrupt);
+  }
+  return v;
+}
+
 template <typename T, bool DEC>
 __device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p,
                                            const FastDiv bd[3], unsigned i, const int64_t m[3],
@@ -171,16 +185,7 @@ __device__ __forceinline__ void base_point(const BaseArgs& a, const PassGeo& p,
     if (sym == 0) atomicAdd(&a.chunk_outliers[geo.s[0].chunk0 + ad.chunk], 1u);
   } else {
     int sym = a.codes[ad.slot];
-    T v;
-    if (sym == 0) {
-      if (!outlier_value(a.sub_olo, a.dense != 0, ad.sidx, ad.local, ad.cnt, a.nsub, a.opos,
-                         (const T*)a.oval, a.nout, ad.pos, v)) {
-        v = T(0);
-        atomicOr(a.status, kStatCorrupt);
-      }
-    } else {
-      v = dequantize(sym, pred, (T)a.two_eb, kRadius);
-    }
+    const T v = sym == 0 ? base_outlier<T>(a, ad) : dequantize(sym, pred, (T)a.two_eb, kRadius);
     __stcg(grid + idx, v);
   }
 }
@@ -203,9 +208,6 @@ __device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint1
   constexpr int kGather = 8;
   for (int i0 = threadIdx.x; i0 < nsg; i0 += kGather * blockDim.x) {
     int64_t src[kGather];
-    int pos[kGather];
-    int64_t sidx[kGather];
-    int loc[kGather], ccnt[kGather];
 #pragma unroll
     for (int u = 0; u < kGather; u++) {
       const int i = i0 + u * blockDim.x;
@@ -216,12 +218,7 @@ __device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint1
       if (!DEC) {
         src[u] = (((int64_t)g0 * s1) * geo.n[1] + (int64_t)g1 * s1) * geo.n[2] + (int64_t)g2 * s1;
       } else {
-        const Addr32 ad = addr0(geo.s[0], geo.b, pl.bd, (int)geo.bvol, a.sm, g0, g1, g2);
-        src[u] = ad.slot;
-        pos[u] = (int)ad.pos;
-        sidx[u] = ad.sidx;
-        loc[u] = ad.local;
-        ccnt[u] = ad.cnt;
+        src[u] = addr0(geo.s[0], geo.b, pl.bd, (int)geo.bvol, a.sm, g0, g1, g2).slot;
       }
     }
     if (!DEC) {
@@ -241,13 +238,13 @@ __device__ void coarse_phase(const BaseArgs& a, const PassList& pl, T* sg, uint1
         if (i >= nsg) continue;
         sc[i] = c[u];
         if (c[u] == 0) {
-          T v;
-          if (!outlier_value(a.sub_olo, a.dense != 0, sidx[u], loc[u], ccnt[u], a.nsub, a.opos,
-                             (const T*)a.oval, a.nout, (int64_t)pos[u], v)) {
-            v = T(0);
-            atomicOr(a.status, kStatCorrupt);
-          }
-          sg[i] = v;
+          // the point's stream address again, on this rare path only (keeping
+          // it for every gathered point costs registers the block has not got)
+          const unsigned r = fdiv((unsigned)i, pl.fsm2), z = fdiv(r, pl.fsm1);
+          const int x = i - (int)r * sm2, y = (int)r - (int)z * sm1;
+          const Addr32 ad =
+              addr0(geo.s[0], geo.b, pl.bd, (int)geo.bvol, a.sm, (int)z * ts, y * ts, x * ts);
+          sg[i] = base_outlier<T>(a, ad);
         }
       }
     }
