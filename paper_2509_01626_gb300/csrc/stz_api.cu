@@ -511,6 +511,38 @@ int launch_sms() {
   return v > 0 ? v : 1;
 }
 
+namespace {
+struct SmemLimit {
+  const void* func;
+  int dev, bytes;
+};
+constexpr int kSmemLimits = 512;  // kernel instances x devices, with room
+std::mutex g_smem_mu;
+SmemLimit g_smem[kSmemLimits];
+int g_nsmem = 0;
+}  // namespace
+
+int allow_smem(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return STZ_OK;  // within the default limit
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return STZ_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  SmemLimit* e = nullptr;
+  for (int i = 0; i < g_nsmem; i++)
+    if (g_smem[i].func == func && g_smem[i].dev == dev) e = &g_smem[i];
+  if (e && (size_t)e->bytes >= bytes) return STZ_OK;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+      cudaSuccess)
+    return STZ_ERR_CUDA;
+  if (!e && g_nsmem < kSmemLimits) {
+    e = &g_smem[g_nsmem++];
+    e->func = func;
+    e->dev = dev;
+  }
+  if (e) e->bytes = (int)bytes;
+  return STZ_OK;
+}
+
 // ------------------------------------------------------------- compression
 // The three words a compression reports, gathered for one read-back:
 // container bytes, payload words, status bits.

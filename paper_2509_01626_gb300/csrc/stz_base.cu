@@ -477,8 +477,7 @@ static int run_coop(const BaseArgs& a, cudaStream_t s, bool allow_coop = true) {
   const size_t smem = (sizeof(T) + sizeof(uint16_t)) * nsg;
   {
     auto ck = k_base_coarse<T, DEC>;
-    if (cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (allow_smem((const void*)ck, smem) != STZ_OK)
       return STZ_ERR_CUDA;
     ProfScope ps_(DEC ? "k_base_coarse_dec" : "k_base_coarse_enc", s);
     ck<<<1, 1024, smem, s>>>(a, pl);

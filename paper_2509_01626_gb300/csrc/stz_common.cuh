@@ -189,8 +189,14 @@ __device__ __forceinline__ double round_q(double v, int& q) {
   q = (int)(__double_as_longlong(t) - kMagicDBits);
   return __dsub_rn(t, kMagicD);
 }
+// The integer add is opaque to the compiler: otherwise it folds the pair back
+// into an int-to-float conversion instruction, which this GPU issues on its
+// narrow FP64 pipe (the float decode kernels then spend half that pipe's
+// issue rate on conversions).  The result is the same value either way.
 __device__ __forceinline__ float from_int(int v, float) {
-  return __fsub_rn(__int_as_float(kMagicFBits + v), kMagicF);
+  int b;
+  asm("add.s32 %0, %1, %2;" : "=r"(b) : "r"(v), "n"(kMagicFBits));
+  return __fsub_rn(__int_as_float(b), kMagicF);
 }
 __device__ __forceinline__ double from_int(int v, double) {
   return __dsub_rn(__longlong_as_double(kMagicDBits + v), kMagicD);

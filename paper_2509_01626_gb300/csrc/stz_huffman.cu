@@ -1124,8 +1124,7 @@ __global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks_multi(
 int launch_decode_chunks_multi(const DecJobMulti* jobs_dev, int njobs, int64_t nblocks,
                                double bytes, cudaStream_t s) {
   if (nblocks == 0 || njobs == 0) return STZ_OK;
-  if (cudaFuncSetAttribute(k_decode_chunks_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kDecSmem) != cudaSuccess)
+  if (allow_smem((const void*)k_decode_chunks_multi, kDecSmem) != STZ_OK)
     return STZ_ERR_CUDA;
   ProfScope ps_("k_decode_chunks", s, bytes);
   k_decode_chunks_multi<<<(unsigned)nblocks, kDecThreads, kDecSmem, s>>>(jobs_dev, njobs);
@@ -1137,8 +1136,7 @@ int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint16_t* lut,
                          cudaStream_t s) {
   if (tb.nblocks == 0) return STZ_OK;
   static_assert(kDecThreads == 256, "block_scan_256 assumes 256 threads");
-  if (cudaFuncSetAttribute(k_decode_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kDecSmem) != cudaSuccess)
+  if (allow_smem((const void*)k_decode_chunks, kDecSmem) != STZ_OK)
     return STZ_ERR_CUDA;
   ProfScope ps_("k_decode_chunks", s, bytes);
   k_decode_chunks<<<(unsigned)tb.nblocks, kDecThreads, kDecSmem, s>>>(g, tb, lut, codes, sub_olo,

@@ -222,4 +222,10 @@ int launch_roi(const void* field, int dtype, const int64_t n[3], const int64_t b
 int launch_sms();
 void set_launch_share(int num, int den);
 
+// Lets kernel `func` take `bytes` of dynamic shared memory on the current
+// device.  The function's limit only ever rises: a graph captured earlier
+// with a larger launch keeps a valid limit when a later call needs less.
+// STZ_OK or STZ_ERR_CUDA.
+int allow_smem(const void* func, size_t bytes);
+
 }  // namespace stz

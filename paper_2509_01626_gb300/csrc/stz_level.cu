@@ -300,7 +300,6 @@ struct TileInfo {
   int64_t slot[8], pos[8], chunk[8];
   int l[8][3];
   int c0[3];
-  int full;
 };
 
 __device__ __forceinline__ void tile_info(const LevelArgs& a, int64_t tt, TileInfo& ti) {
@@ -382,12 +381,26 @@ __device__ __noinline__ void tile_prefetch(const LevelArgs& a, int64_t tt, T* ti
 }
 
 // Two consecutive values as one 8- or 16-byte access.
+// A tile takes fast_tile's FULL form when all 7 of its sub-block bricks are
+// whole and, when decoding, all its fine points lie inside the fine box.
+__device__ __forceinline__ bool tile_full(const LevelArgs& a, const TileInfo& ti, bool dec) {
+  bool full = true;
+#pragma unroll
+  for (int K = 1; K <= 7; K++)
+    full = full && ti.l[K][0] == kFBZ && ti.l[K][1] == kFBY && ti.l[K][2] == kFBX;
+  if (!dec) return full;
+  return full && 2 * ti.c0[0] >= a.flo[0] && 2 * (ti.c0[0] + kFBZ) <= a.fhi[0] &&
+         2 * ti.c0[1] >= a.flo[1] && 2 * (ti.c0[1] + kFBY) <= a.fhi[1] &&
+         2 * ti.c0[2] >= a.flo[2] && 2 * (ti.c0[2] + kFBX) <= a.fhi[2];
+}
+
 template <typename T> struct Pair2;
 template <> struct Pair2<float> { using type = float2; };
 template <> struct Pair2<double> { using type = double2; };
 
 // One tile of the fast path.  FULL: all 7 sub-block bricks of the tile are
-// whole, so a cell has the same local code index lz*256 + tid in every stream.
+// whole, so a cell has the same local code index lz*256 + tid in every stream,
+// and (when decoding) all the tile's fine points lie inside the fine box.
 // The 7 global loads of a cell (x when compressing, codes when decoding) are
 // issued one cell ahead of their use.  PAIR: the fine box and (at stride 1)
 // the field have even, aligned rows, so the x-neighbour points of a cell
@@ -424,7 +437,7 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
                  : nullptr;
   // the tile's fine points all inside the fine box (every tile of a full
   // decode): its cells need no per-point box test
-  const bool tile_in = !DEC || (2 * c0z >= flo0 && 2 * (c0z + kFBZ) <= fhi0 &&
+  const bool tile_in = FULL || !DEC || (2 * c0z >= flo0 && 2 * (c0z + kFBZ) <= fhi0 &&
                                 2 * ti.c0[1] >= flo1 && 2 * (ti.c0[1] + kFBY) <= fhi1 &&
                                 2 * ti.c0[2] >= flo2 && 2 * (ti.c0[2] + kFBX) <= fhi2);
   // cell lz is "on" for sub-block K if interior (and its point inside the box)
@@ -478,6 +491,22 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
       }
     }
   };
+  // all 8 points of a cell, unconditionally (whole tiles)
+  auto store8_all = [&](const T (&v)[8]) {
+#pragma unroll
+    for (int pr = 0; pr < 4; pr++) {
+      T* dst = fp + (pr >> 1) * fdz + (pr & 1) * fe2;
+      if (PAIR) {
+        P2 w;
+        w.x = v[2 * pr];
+        w.y = v[2 * pr + 1];
+        *(P2*)dst = w;
+      } else {
+        dst[0] = v[2 * pr];
+        dst[1] = v[2 * pr + 1];
+      }
+    }
+  };
   // loads of cell 0
   T xv[7];
   int cv[7];
@@ -496,7 +525,11 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
   load_plane(w0, tile, tb - kFEZY);
   load_plane(w1, tile, tb);
   load_plane(w2, tile, tb + kFEZY);
-#pragma unroll 1
+  // whole tiles, decoding: two cells per iteration, so that half the plane
+  // copies become register renames (level 3 decode 0.395 -> 0.341 ms at
+  // 512^3; encoding, whose cells carry more live values, runs slower unrolled)
+  static_assert(kFBZ % 2 == 0, "the unrolled z loop takes two cells at a time");
+#pragma unroll((FULL && DEC) ? 2 : 1)
   for (int lz = 0; lz < kFBZ; lz++) {
     load_plane(w3, tile, tb + (lz + 2) * kFEZY);
     const int cz = c0z + lz;
@@ -525,19 +558,44 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
       T xq[7];
 #pragma unroll
       for (int K = 0; K < 7; K++) sym[K] = quantize_sel(xv[K], p[K], q, kRadius, xq[K]);
+      if (FULL) {
+        // a whole tile: a cell's 7 codes and 8 points are all written or
+        // none (interior), under one test; outliers counted under another
+        if (interior) {
+          bool anyout = false;
 #pragma unroll
-      for (int K = 1; K <= 7; K++) {
-        if (!on[K - 1]) {
-          sym[K - 1] = -1;
-          continue;
+          for (int K = 1; K <= 7; K++) {
+            *cp[K - 1] = (uint16_t)sym[K - 1];
+            anyout = anyout || sym[K - 1] == 0;
+          }
+          if (anyout) {
+#pragma unroll
+            for (int K = 1; K <= 7; K++)
+              if (sym[K - 1] == 0) atomicAdd(&a.chunk_outliers[ti.chunk[K]], 1u);
+          }
+          if (fp) {
+            const T v8[8] = {w1[1], xq[0], xq[1], xq[2], xq[3], xq[4], xq[5], xq[6]};
+            store8_all(v8);
+          }
+        } else {
+#pragma unroll
+          for (int K = 0; K < 7; K++) sym[K] = -1;
         }
-        *cp[K - 1] = (uint16_t)sym[K - 1];
-        if (sym[K - 1] == 0) atomicAdd(&a.chunk_outliers[ti.chunk[K]], 1u);
-      }
-      if (fp) {
-        const T v8[8] = {w1[1], xq[0], xq[1], xq[2], xq[3], xq[4], xq[5], xq[6]};
-        const bool o8[8] = {copy_on, on[0], on[1], on[2], on[3], on[4], on[5], on[6]};
-        store8(v8, o8);
+      } else {
+#pragma unroll
+        for (int K = 1; K <= 7; K++) {
+          if (!on[K - 1]) {
+            sym[K - 1] = -1;
+            continue;
+          }
+          *cp[K - 1] = (uint16_t)sym[K - 1];
+          if (sym[K - 1] == 0) atomicAdd(&a.chunk_outliers[ti.chunk[K]], 1u);
+        }
+        if (fp) {
+          const T v8[8] = {w1[1], xq[0], xq[1], xq[2], xq[3], xq[4], xq[5], xq[6]};
+          const bool o8[8] = {copy_on, on[0], on[1], on[2], on[3], on[4], on[5], on[6]};
+          store8(v8, o8);
+        }
       }
 #pragma unroll
       for (int K = 1; K <= 7; K++) {
@@ -550,21 +608,33 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
       T val[7];
 #pragma unroll
       for (int K = 0; K < 7; K++) val[K] = dequantize(cv[K], p[K], two_eb, kRadius);
+      // one test for the cell's 7 codes; the rare outliers point by point
+      bool anyout = false;
 #pragma unroll
-      for (int K = 1; K <= 7; K++) {
-        if (on[K - 1] && cv[K - 1] == 0) {  // outlier: its value from the list
-          const int64_t local = cp[K - 1] - (a.codes + ti.slot[K]);
-          if (!outlier_value(a.sub_olo, a.dense[K] != 0, ti.slot[K] / a.geo.bvol, (int)local,
-                             ti.l[K][0] * ti.l[K][1] * ti.l[K][2], a.nsub, a.opos[K],
-                             (const T*)a.oval[K], a.nout[K], ti.pos[K] + local, val[K - 1])) {
-            val[K - 1] = T(0);
-            atomicOr(a.status, kStatCorrupt);
+      for (int K = 0; K < 7; K++) anyout = anyout || (on[K] && cv[K] == 0);
+      if (anyout) {
+#pragma unroll
+        for (int K = 1; K <= 7; K++) {
+          if (on[K - 1] && cv[K - 1] == 0) {  // outlier: its value from the list
+            const int64_t local = cp[K - 1] - (a.codes + ti.slot[K]);
+            if (!outlier_value(a.sub_olo, a.dense[K] != 0, ti.slot[K] / a.geo.bvol, (int)local,
+                               ti.l[K][0] * ti.l[K][1] * ti.l[K][2], a.nsub, a.opos[K],
+                               (const T*)a.oval[K], a.nout[K], ti.pos[K] + local, val[K - 1])) {
+              val[K - 1] = T(0);
+              atomicOr(a.status, kStatCorrupt);
+            }
           }
         }
       }
       const T v8[8] = {w1[1], val[0], val[1], val[2], val[3], val[4], val[5], val[6]};
-      const bool o8[8] = {copy_on, on[0], on[1], on[2], on[3], on[4], on[5], on[6]};
-      store8(v8, o8);
+      if (FULL) {
+        // a whole tile inside the box: a cell's 8 points are all stored or
+        // none (interior), under one test
+        if (interior) store8_all(v8);
+      } else {
+        const bool o8[8] = {copy_on, on[0], on[1], on[2], on[3], on[4], on[5], on[6]};
+        store8(v8, o8);
+      }
     }
     if (!DEC) xp += 2 * xdz;
     if (fp) fp += 2 * fdz;
@@ -722,11 +792,7 @@ __global__ void __launch_bounds__(kLevelThreads, 2)
       prefetch(nt, b ^ 1);
     }
     const TileInfo& ti = s_ti[b];
-    bool full = true;
-#pragma unroll
-    for (int K = 1; K <= 7; K++)
-      full = full && ti.l[K][0] == kFBZ && ti.l[K][1] == kFBY && ti.l[K][2] == kFBX;
-    if (full)
+    if (tile_full(a, ti, DEC))
       fast_tile<T, DEC, true, PAIR>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2, fdz);
     else
       fast_tile<T, DEC, false, PAIR>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2,
@@ -1069,11 +1135,7 @@ __global__ void __launch_bounds__(kLevelThreads, 2)
     const int fdz = (int)((a.fhi[1] - a.flo[1]) * fe2);
     const T two_eb = (T)a.two_eb;
     const TileInfo& ti = s_ti[b];
-    bool full = true;
-#pragma unroll
-    for (int K = 1; K <= 7; K++)
-      full = full && ti.l[K][0] == kFBZ && ti.l[K][1] == kFBY && ti.l[K][2] == kFBX;
-    if (full)
+    if (tile_full(a, ti, true))
       fast_tile<T, true, true, PAIR>(a, tiles[b], ti, M, q, two_eb, nullptr, xdz, xdy, xdx, fe2,
                                      fdz);
     else
@@ -1112,8 +1174,7 @@ static int run_level_generic(const LevelArgs& a, double bytes, cudaStream_t s) {
   size_t smem = (((size_t)tvol * sizeof(T) + 15) & ~(size_t)15);
   if (!DEC) smem += sizeof(uint32_t) * 7 * kHistWords;
   auto kern = k_level<T, DEC>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+  if (allow_smem((const void*)kern, smem) != STZ_OK)
     return STZ_ERR_CUDA;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLevelThreads, smem);
@@ -1193,8 +1254,7 @@ static int run_level_fast(const LevelArgs& a, const int64_t M[3], double bytes, 
   constexpr bool kTma = !DEC;  // the decode kernels are not built with TMA tiles
   auto kern = pair ? (tma ? k_level_fast<T, DEC, true, kTma> : k_level_fast<T, DEC, true, false>)
                    : (tma ? k_level_fast<T, DEC, false, kTma> : k_level_fast<T, DEC, false, false>);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+  if (allow_smem((const void*)kern, smem) != STZ_OK)
     return STZ_ERR_CUDA;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLevelThreads, smem);
@@ -1248,8 +1308,7 @@ static int run_level_shell(const LevelArgs& a, const ShellGeo& sh, double bytes,
   const size_t smem = DEC ? 0 : sizeof(uint32_t) * 7 * kHistWords;
   auto kern = k_level_shell<T, DEC>;
   if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
+      allow_smem((const void*)kern, smem) != STZ_OK)
     return STZ_ERR_CUDA;
   int64_t grid = imin(cdiv(total, 256), (int64_t)sm_count() * 4);
   char nm[48];
@@ -1348,8 +1407,7 @@ static int run_level_multi(const LevelArgs* h, int n, uint8_t* arena, cudaStream
   if (tile0[n] > 0) {
     const size_t smem = 2 * (((size_t)(kFBZ + 3) * kFEZY * sizeof(T) + 15) & ~(size_t)15);
     auto kern = pair ? k_level_fast_multi<T, true> : k_level_fast_multi<T, false>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (allow_smem((const void*)kern, smem) != STZ_OK)
       return STZ_ERR_CUDA;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLevelThreads, smem);

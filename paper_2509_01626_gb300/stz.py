@@ -514,6 +514,66 @@ def decode_requests(reqs, fields, workspace: torch.Tensor, status: torch.Tensor,
     _check(rc, "stz_decode_requests")
 
 
+def decode_regions(comp: torch.Tensor, boxes, level: int | None = None,
+                   level1: torch.Tensor | None = None, tables: torch.Tensor | None = None,
+                   hdr: bytes | None = None, stream=None, meta: dict | None = None,
+                   check: bool = True):
+    """Decode many boxes [lo, hi) of one container with a single
+    stz_decode_requests call: a fixed number of kernel launches however many
+    boxes there are.  Each returned tensor equals decompress_region of its
+    box bit for bit.  `level1` (decompress_progressive at level 1) and
+    `tables` (decode_tables) are built here unless given.  With check=True
+    the call waits and raises StzError if any box's decode reported a
+    corrupt container; with check=False it returns (outputs, status) without
+    waiting, status an int32 CUDA tensor with one entry per box."""
+    inf = meta or info(comp)
+    level = inf["levels"] if level is None else int(level)
+    boxes = [(tuple(int(v) for v in lo), tuple(int(v) for v in hi)) for lo, hi in boxes]
+    status = torch.zeros(max(1, len(boxes)), dtype=torch.int32, device=comp.device)
+    if not boxes:
+        return [] if check else ([], status[:0])
+    hdr = hdr or header_bytes(comp)
+    if level1 is None:
+        level1 = decompress_progressive(comp, 1, stream=stream, meta=inf)
+    if tables is None:
+        tables = decode_tables(comp, hdr, stream)
+    fields = served_fields([(comp, hdr, level1, tables)])
+    reqs = (RegionRequest * len(boxes))()
+    offs, off = [], 0
+    for lo, hi in boxes:
+        offs.append(off)
+        n = 1
+        for a, b in zip(lo, hi):
+            n *= max(1, b - a)
+        off += -(-n // 64) * 64
+    out = torch.empty(off, dtype=inf["dtype"], device=comp.device)
+    es = out.element_size()
+    for q, (lo, hi), o in zip(reqs, boxes, offs):
+        q.field = 0
+        q.level = level
+        for a in range(len(lo)):
+            q.lo[a] = lo[a]
+            q.hi[a] = hi[a]
+        q.out_dev = out.data_ptr() + o * es
+        q.out_cap = (off - o) * es
+    ws = torch.empty(max(1, decode_requests_workspace(reqs, fields)), dtype=torch.uint8,
+                     device=comp.device)
+    decode_requests(reqs, fields, ws, status, stream)
+    outs = []
+    for q, o in zip(reqs, offs):
+        shape = _shape_out(q.out_dims, inf["ndim"])
+        n = 1
+        for v in shape:
+            n *= v
+        outs.append(out[o:o + n].view(shape))
+    if not check:
+        return outs, status
+    bad = torch.nonzero(status.cpu()).reshape(-1)
+    if len(bad):
+        raise StzError(ERR_CORRUPT, f"stz_decode_requests: box {int(bad[0])}")
+    return outs
+
+
 def launch_count() -> int:
     """Kernel launches made by the library so far (all streams)."""
     return int(lib().stz_launch_count())

@@ -4,7 +4,8 @@ selection.  The selection and every unit's metric equal the oracle's bit for
 bit, on fields with ties and non-finite values, on slices along each axis,
 on ragged blocks, in 2D and f64.  The paper's workflow -- decode the coarse
 level, pick the regions of interest on it, decode only those at full
-resolution -- gives regions equal to the oracle's decodes of the same boxes.
+resolution, one by one or all in one batched call -- gives regions equal to
+the oracle's decodes of the same boxes.
 """
 import numpy as np
 import pytest
@@ -63,8 +64,9 @@ def test_roi_2d_and_smooth_fields(stzg, ora):
 
 def test_roi_workflow_coarse_then_regions(stzg, ora):
     """Decode level 1 (the 1/64 coarse grid), select the top 2% of its 4^3
-    blocks by value range, then decode those regions at full resolution:
-    each equals the oracle's region decode."""
+    blocks by value range, then decode those regions at full resolution,
+    one by one and with one decode_regions call: each equals the oracle's
+    region decode."""
     x = synth.grf((128, 128, 128), synth.seed_for(2, 9))
     ref = ora.compress(x, 1e-3, "rel")
     comp = torch.from_numpy(ref).cuda()
@@ -74,10 +76,21 @@ def test_roi_workflow_coarse_then_regions(stzg, ora):
     assert np.array_equal(sel.cpu().numpy(), wsel)
     boxes = stzg.roi_boxes(sel.cpu().numpy(), tuple(coarse.shape), (4, 4, 4), 4, x.shape)
     assert len(boxes) == int(np.ceil(0.02 * 8 ** 3))
-    for lo, hi in boxes:
+    batched = stzg.decode_regions(comp, boxes, 3, level1=coarse)
+    assert len(batched) == len(boxes)
+    for (lo, hi), b in zip(boxes, batched):
+        want = ora.decompress_region(ref, lo, hi, 3).view(np.uint32)
         r = stzg.decompress_region(comp, lo, hi, 3).cpu().numpy()
-        assert np.array_equal(r.view(np.uint32),
-                              ora.decompress_region(ref, lo, hi, 3).view(np.uint32)), (lo, hi)
+        assert np.array_equal(r.view(np.uint32), want), (lo, hi)
+        assert np.array_equal(b.cpu().numpy().view(np.uint32), want), (lo, hi)
+    # the same boxes at level 2 (every other point), tables given, without waiting
+    tables = stzg.decode_tables(comp, stzg.header_bytes(comp))
+    outs, status = stzg.decode_regions(comp, boxes[:5], 2, level1=coarse, tables=tables,
+                                       check=False)
+    assert (status.cpu().numpy() == 0).all()
+    for (lo, hi), b in zip(boxes[:5], outs):
+        want = ora.decompress_region(ref, lo, hi, 2).view(np.uint32)
+        assert np.array_equal(b.cpu().numpy().view(np.uint32), want), (lo, hi)
 
 
 def test_roi_rejects_bad_arguments(stzg):
