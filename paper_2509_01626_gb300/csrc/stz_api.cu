@@ -1277,7 +1277,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
   uint8_t* ws = (uint8_t*)ws_dev;
   DevParams* dp = (DevParams*)(ws + P.dp);
   uint16_t* codes = (uint16_t*)(ws + P.codes);
-  uint16_t* lut = (uint16_t*)(ws + P.lut);
+  uint32_t* lut = (uint32_t*)(ws + P.lut);
   uint32_t* sub_olo = (uint32_t*)(ws + P.sub_olo);
   uint32_t* status = &dp->status;
   const uint8_t* comp = (const uint8_t*)comp_dev;
@@ -1697,7 +1697,7 @@ size_t stz_decode_tables_size(const void* hdr_host, size_t hdr_bytes, size_t com
   Hdr H;
   if (!hdr_host || parse_hdr((const uint8_t*)hdr_host, hdr_bytes, comp_bytes, &H) != STZ_OK)
     return 0;
-  return sizeof(uint16_t) * (size_t)kLutSize * (size_t)H.ns;
+  return sizeof(uint32_t) * (size_t)kLutSize * (size_t)H.ns;
 }
 
 int stz_decode_tables(const void* comp_dev, size_t comp_bytes, const void* hdr_host,
@@ -1706,7 +1706,7 @@ int stz_decode_tables(const void* comp_dev, size_t comp_bytes, const void* hdr_h
   Hdr H;
   const int rc = parse_hdr((const uint8_t*)hdr_host, hdr_bytes, comp_bytes, &H);
   if (rc != STZ_OK) return rc;
-  if (tables_bytes < sizeof(uint16_t) * (size_t)kLutSize * (size_t)H.ns) return STZ_ERR_CAPACITY;
+  if (tables_bytes < sizeof(uint32_t) * (size_t)kLutSize * (size_t)H.ns) return STZ_ERR_CAPACITY;
   Geo g;
   make_geo(H.n, H.ndim, H.dtype, H.L, H.b, &g);
   DecTables tb;
@@ -1716,7 +1716,7 @@ int stz_decode_tables(const void* comp_dev, size_t comp_bytes, const void* hdr_h
     if (g.s[s].nsym > 0) tb.lut_sid[tb.nlut++] = s;
   }
   if (tb.nlut == 0) return STZ_OK;
-  return launch_lut(tb, (uint16_t*)tables_dev, nullptr, 0, (cudaStream_t)stream);
+  return launch_lut(tb, (uint32_t*)tables_dev, nullptr, 0, (cudaStream_t)stream);
 }
 
 
@@ -1880,7 +1880,7 @@ int stz_decode_requests(int n, stz_region_request* reqs, const stz_served_field*
       dec_stream(H, (const uint8_t*)F.comp_dev, sid, &m.ds);
       m.sg = g.s[sid];
       m.bvol = g.bvol;
-      m.lut = (const uint16_t*)F.tables_dev + (int64_t)sid * kLutSize;
+      m.lut = (const uint32_t*)F.tables_dev + (int64_t)sid * kLutSize;
       m.codes = (uint16_t*)(base + P.codes);
       m.sub_olo = (uint32_t*)(base + P.sub_olo);
       m.status = status_dev + i;

@@ -91,6 +91,10 @@ __global__ void __launch_bounds__(256) k_base_pass(BaseArgs a, PassGeo p) {
 // never through a possibly stale L1 line.
 constexpr int kMaxPasses = 64;
 constexpr int64_t kLocalPoints = 32768;  // fine-pass points kept in the single block
+#ifndef STZ_BASE_SUBGRID_KB
+#define STZ_BASE_SUBGRID_KB 16
+#endif
+constexpr int64_t kBaseSubgridBytes = (int64_t)STZ_BASE_SUBGRID_KB * 1024;
 struct PassList {
   PassGeo p[kMaxPasses];
   SubPass sp[kMaxPasses];  // the first nsmall passes in subgrid units
@@ -421,8 +425,8 @@ static int run_coop(const BaseArgs& a, cudaStream_t s, bool allow_coop = true) {
     if (n == 0) return STZ_OK;
   }
   // coarse phase: the passes with t >= ts, ts the smallest power of two whose
-  // subgrid fits in 128 KiB of shared memory
-  const int64_t cap = (128 * 1024) / (int64_t)sizeof(T);
+  // subgrid fits in kBaseSubgridBytes of shared memory
+  const int64_t cap = kBaseSubgridBytes / (int64_t)sizeof(T);
   int64_t ts = 1;
   while (cdiv(m[0], ts) * cdiv(m[1], ts) * cdiv(m[2], ts) > cap) ts <<= 1;
   pl.ts = (int)ts;

@@ -823,38 +823,56 @@ int launch_pack(const Geo& g, const uint16_t* codes, const uint16_t* enc,
 // Block 0 also clears the decode's parameter words (its status among them).
 // A table that cannot be built is left empty: every lookup then fails, so the
 // decode of any chunk of that stream reports the container corrupt.
+// Decode table of a stream: one 32-bit entry per 12-bit window, holding the
+// first code that starts the window and, when the second code also ends
+// inside it, that one too:
+//   bits  0-10 first symbol,  bits 11-14 its length (0: no code starts so)
+//   bits 16-26 second symbol, bits 27-30 its length (0: not inside the window)
+// so that (entry & 0x07FF07FF) is the two symbols as a pair of u16.
+// kLutParts blocks per stream, each filling an equal share of the windows
+constexpr int kLutParts = 8;
+static_assert(kLutSize % (kLutParts * 256) == 0, "a block fills whole rounds of windows");
 __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables tb,
-                                             uint16_t* __restrict__ lut,
+                                             uint32_t* __restrict__ lut,
                                              uint32_t* __restrict__ clear, int nclear) {
   __shared__ int cnt[32];
   __shared__ uint32_t fcode[32];
   __shared__ int fidx[32];
+  __shared__ int start[32];  // first codebook entry of each length, -1: none
   __shared__ int bad;
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < nclear; i += blockDim.x) clear[i] = 0u;
-  const int sid = tb.lut_sid[blockIdx.x];
+  const int sid = tb.lut_sid[blockIdx.x / kLutParts];
+  const int part = blockIdx.x % kLutParts;  // this block's share of the windows
   const DecStream& d = tb.ds[sid];
-  uint16_t* t = lut + (int64_t)sid * kLutSize;
+  uint32_t* t = lut + (int64_t)sid * kLutSize;
   const int tid = threadIdx.x;
-  if (tid < 32) cnt[tid] = 0;
+  if (tid < 32) start[tid] = -1;
   if (tid == 0) bad = 0;
   __syncthreads();
   const uint16_t* syms = (const uint16_t*)(d.sect + d.off_syms);
   const uint8_t* lens = d.sect + d.off_lens;
-  for (int64_t k = tid; k < (int64_t)d.nlive; k += blockDim.x) {
-    int L = lens[k], sym = syms[k];
+  const int nlive = d.nlive > (uint64_t)kAlphabet ? kAlphabet : (int)d.nlive;
+  if (d.nlive > (uint64_t)kAlphabet && tid == 0) bad = 1;
+  // the codebook lists (symbol, length) by (length, symbol): each length's
+  // entries are one run, found from where the length changes
+  for (int k = tid; k < nlive; k += blockDim.x) {
+    const int L = lens[k], sym = syms[k];
     if (L < 1 || L > kMaxCodeLen || sym >= kAlphabet) {
       bad = 1;
       continue;
     }
-    if (k > 0) {
-      int Lp = lens[k - 1], sp = syms[k - 1];
-      if (!(L > Lp || (L == Lp && sym > sp))) bad = 1;
-    }
-    atomicAdd(&cnt[L], 1);
+    const int Lp = k > 0 ? lens[k - 1] : 0, sp = k > 0 ? syms[k - 1] : -1;
+    if (!(L > Lp || (L == Lp && sym > sp))) bad = 1;
+    else if (L != Lp) start[L] = k;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (tid == 0 && !bad) {
+    int next = nlive;  // start of the next longer length present
+    for (int L = kMaxCodeLen; L >= 1; L--) {
+      cnt[L] = start[L] < 0 ? 0 : next - start[L];
+      if (start[L] >= 0) next = start[L];
+    }
     uint32_t code = 0;
     int idx = 0;
     long long kraft = 0;
@@ -868,30 +886,37 @@ __global__ void __launch_bounds__(256) k_lut(const __grid_constant__ DecTables t
     if (kraft > kLutSize) bad = 1;
   }
   __syncthreads();
+  constexpr int kPart = kLutSize / kLutParts;
   if (bad) {  // an empty table: every lookup then flags the chunk as corrupt
-    for (int i = tid; i < kLutSize; i += blockDim.x) t[i] = 0;
+    for (int i = part * kPart + tid; i < (part + 1) * kPart; i += blockDim.x) t[i] = 0;
     return;
   }
-  // each window i of the table: the one length L whose L-bit prefix of i
-  // falls in that length's range of canonical codes (0: no code starts so)
-  for (int i = tid; i < kLutSize; i += blockDim.x) {
-    uint16_t v = 0;
-    for (int L = 1; L <= kMaxCodeLen; L++) {
-      const uint32_t r = ((uint32_t)i >> (kMaxCodeLen - L)) - fcode[L];
-      if (r < (uint32_t)cnt[L]) {
-        v = (uint16_t)(syms[fidx[L] + (int)r] | (L << 11));
-        break;
-      }
+  // the code that starts window w (its top bits; only lengths <= maxlen
+  // count): symbol | length << 11, or 0 when none does.  A code of length L
+  // starts w when the L-bit prefix of w falls in length L's range of
+  // canonical codes.
+  auto first = [&](uint32_t w, int maxlen) -> uint32_t {
+    for (int L = 1; L <= maxlen; L++) {
+      const uint32_t r = (w >> (kMaxCodeLen - L)) - fcode[L];
+      if (r < (uint32_t)cnt[L]) return (uint32_t)syms[fidx[L] + (int)r] | ((uint32_t)L << 11);
     }
-    t[i] = v;
+    return 0u;
+  };
+  for (int i = part * kPart + tid; i < (part + 1) * kPart; i += blockDim.x) {
+    const uint32_t e0 = first((uint32_t)i, kMaxCodeLen);
+    const int L0 = (int)(e0 >> 11);
+    uint32_t e1 = 0;
+    if (L0 > 0 && L0 < kMaxCodeLen)  // the window's remaining 12 - L0 bits
+      e1 = first(((uint32_t)i << L0) & (kLutSize - 1), kMaxCodeLen - L0);
+    t[i] = e0 | (e1 << 16);
   }
 }
 
-int launch_lut(const DecTables& tb, uint16_t* lut, uint32_t* clear, int nclear,
+int launch_lut(const DecTables& tb, uint32_t* lut, uint32_t* clear, int nclear,
                cudaStream_t s) {
   if (tb.nlut == 0) return STZ_ERR_ARG;
   ProfScope ps_("k_lut", s);
-  k_lut<<<tb.nlut, 256, 0, s>>>(tb, lut, clear, nclear);
+  k_lut<<<tb.nlut * kLutParts, 256, 0, s>>>(tb, lut, clear, nclear);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -916,17 +941,23 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// 24 KiB of payload per block: with 8 runs per chunk (32 chunks per block)
-// 768 bytes per chunk, 3 bits per symbol, at once; 6 blocks share an SM
-constexpr int kStageWords = 6144;
+// Blocks of the chunk decoder per SM, and the payload words a block stages
+// at once: beside the 16 KiB decode table, 5 blocks per SM leave room for a
+// 24 KiB stage (8 runs per chunk, 32 chunks per block: 3 bits per symbol at
+// once); 6 blocks would leave 16.9 KiB (measured slower: more staging rounds)
+#ifndef STZ_DEC_BLOCKS
+#define STZ_DEC_BLOCKS 5
+#endif
+constexpr int kDecBlocks = STZ_DEC_BLOCKS;
+constexpr int kStageWords = kDecBlocks >= 6 ? 4320 : 6144;
 constexpr int kMaxChunkWords = (4096 * kMaxCodeLen + 31) / 32;  // bricks hold <= 4096 cells
 static_assert(kMaxChunkWords + 2 <= kStageWords, "a chunk must fit the stage");
-constexpr size_t kDecSmem = sizeof(uint32_t) * kStageWords + sizeof(uint16_t) * kLutSize +
+constexpr size_t kDecSmem = sizeof(uint32_t) * kStageWords + sizeof(uint32_t) * kLutSize +
                             sizeof(uint32_t) * kDecThreads +
                             sizeof(uint32_t) * (kDecThreads + 1) + sizeof(uint32_t) * kDecThreads +
                             sizeof(int) * kDecThreads;
 static_assert((sizeof(uint32_t) * kStageWords) % 16 == 0 &&
-                  (sizeof(uint32_t) * kStageWords + sizeof(uint16_t) * kLutSize) % 8 == 0,
+                  (sizeof(uint32_t) * kStageWords + sizeof(uint32_t) * kLutSize) % 16 == 0,
               "shared arrays of the chunk decoder must stay aligned");
 
 // first index i in the ascending list p[0, n) with p[i] >= v
@@ -945,14 +976,14 @@ __device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__
 // brick range of one stream.  lutg: the stream's decode table.
 __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecStream& d,
                                              const StreamGeo& sg, const int32_t gb[3],
-                                             int64_t bvol, const uint16_t* __restrict__ lutg,
+                                             int64_t bvol, const uint32_t* __restrict__ lutg,
                                              uint16_t* __restrict__ codes,
                                              uint32_t* __restrict__ sub_olo,
                                              uint32_t* __restrict__ status, int64_t bidx) {
   extern __shared__ __align__(16) unsigned char dsm[];
   // arrays in order of alignment: the 16-byte-loaded table first, then 4-byte
   uint32_t* stage = (uint32_t*)dsm;
-  uint16_t* t = (uint16_t*)(stage + kStageWords);
+  uint32_t* t = stage + kStageWords;
   uint32_t* cw0 = (uint32_t*)(t + kLutSize);     // chunk's first word in the stream payload
   uint32_t* S = cw0 + kDecThreads;               // padded-size prefix sums
   uint32_t* cjl = S + kDecThreads + 1;                            // chunk index in stream
@@ -961,7 +992,7 @@ __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecSt
   const int tid = threadIdx.x;
   {
     const uint4* src = (const uint4*)lutg;
-    for (int i = tid; i < kLutSize / 8; i += blockDim.x) ((uint4*)t)[i] = __ldg(src + i);
+    for (int i = tid; i < kLutSize / 4; i += blockDim.x) ((uint4*)t)[i] = __ldg(src + i);
   }
   const int nsub = d.nsub;
   const int cpb = kDecThreads / nsub;  // chunks per block
@@ -1034,12 +1065,12 @@ __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecSt
         int k = (int)(b0 >> 5);
         int pos = (int)(b0 & 31);
         uint32_t cur = sp[k], nxt = sp[k + 1];
-        auto next = [&]() -> uint32_t {
-          const uint32_t win = __funnelshift_l(nxt, cur, pos);
-          const uint32_t ent = t[win >> (32 - kMaxCodeLen)];
-          int L = (int)(ent >> 11);
-          bad |= L == 0;
-          pos += L == 0 ? 1 : L;
+        // the smallest low half of the entries met: below 1 << 11 once a
+        // window starts no code (the position then stops advancing)
+        uint32_t mn = 0xFFFFu;
+        // nbits <= 24 and pos < 32, so one word step brings pos below 32
+        auto advance = [&](uint32_t nbits) {
+          pos += (int)nbits;
           if (pos >= 32) {
             pos -= 32;
             cur = nxt;
@@ -1047,7 +1078,31 @@ __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecSt
             k = min(k + 1, lim - 1);
             nxt = sp[k + 1];
           }
-          return ent & 0x7FFu;
+        };
+        // the next two symbols as a u16 pair: one lookup, and a second one
+        // only when the second code does not end inside the first window
+        auto next2 = [&]() -> uint32_t {
+          const uint32_t win = __funnelshift_l(nxt, cur, pos);
+          const uint32_t e = t[win >> (32 - kMaxCodeLen)];
+          const uint32_t L0 = (e >> 11) & 15u;
+          uint32_t L1 = e >> 27;
+          uint32_t pair = e & 0x07FF07FFu;
+          mn = min(mn, e & 0xFFFFu);
+          if (L1 == 0u) {
+            const uint32_t e1 = t[(win << L0) >> (32 - kMaxCodeLen)];
+            L1 = (e1 >> 11) & 15u;
+            mn = min(mn, e1 & 0xFFFFu);
+            pair = (pair & 0x7FFu) | ((e1 & 0x7FFu) << 16);
+          }
+          advance(L0 + L1);
+          return pair;
+        };
+        auto next1 = [&]() -> uint32_t {
+          const uint32_t win = __funnelshift_l(nxt, cur, pos);
+          const uint32_t e = t[win >> (32 - kMaxCodeLen)];
+          mn = min(mn, e & 0xFFFFu);
+          advance((e >> 11) & 15u);
+          return e & 0x7FFu;
         };
         int i = i0;
         // 8 symbols per 16-byte store where the run start is 16-byte aligned
@@ -1055,14 +1110,12 @@ __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecSt
           for (; i + 8 <= i1; i += 8) {
             uint32_t v[4];
 #pragma unroll
-            for (int m = 0; m < 4; m++) {
-              const uint32_t lo = next();
-              v[m] = lo | (next() << 16);
-            }
+            for (int m = 0; m < 4; m++) v[m] = next2();
             *(uint4*)(out + i) = make_uint4(v[0], v[1], v[2], v[3]);
           }
         }
-        for (; i < i1; i++) out[i] = (uint16_t)next();
+        for (; i < i1; i++) out[i] = (uint16_t)next1();
+        bad |= mn < (1u << 11);
         const uint64_t end = (uint64_t)k * 32 + (uint64_t)pos;
         bad |= u + 1 < nsub ? end != b1 : end > b1;
       }
@@ -1093,9 +1146,9 @@ __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecSt
   if (bad) atomicOr(status, kStatCorrupt);
 }
 
-__global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
+__global__ void __launch_bounds__(kDecThreads, kDecBlocks) k_decode_chunks(
     const __grid_constant__ Geo g, const __grid_constant__ DecTables tb,
-    const uint16_t* __restrict__ lut, uint16_t* __restrict__ codes,
+    const uint32_t* __restrict__ lut, uint16_t* __restrict__ codes,
     uint32_t* __restrict__ sub_olo, uint32_t* __restrict__ status) {
   int jb = 0;
   for (int k = 1; k < tb.njobs; k++)
@@ -1108,7 +1161,7 @@ __global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks(
 
 // The chunk jobs of many region decodes in one launch (the batched served
 // form): each job carries its own stream, decode table and outputs.
-__global__ void __launch_bounds__(kDecThreads, 6) k_decode_chunks_multi(
+__global__ void __launch_bounds__(kDecThreads, kDecBlocks) k_decode_chunks_multi(
     const DecJobMulti* __restrict__ jobs, int njobs) {
   int lo = 0, hi = njobs - 1;  // the last job whose first block is <= blockIdx.x
   while (lo < hi) {
@@ -1131,7 +1184,7 @@ int launch_decode_chunks_multi(const DecJobMulti* jobs_dev, int njobs, int64_t n
   return cuda_ok(cudaGetLastError());
 }
 
-int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint16_t* lut,
+int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,
                          uint16_t* codes, uint32_t* sub_olo, uint32_t* status, double bytes,
                          cudaStream_t s) {
   if (tb.nblocks == 0) return STZ_OK;

@@ -135,13 +135,13 @@ struct DecTables {
 };
 // decode tables of the streams tb.lut_sid[0 .. nlut) (nlut > 0); block 0 also
 // zero-fills the nclear words at clear
-int launch_lut(const DecTables& tb, uint16_t* lut, uint32_t* clear, int nclear,
+int launch_lut(const DecTables& tb, uint32_t* lut, uint32_t* clear, int nclear,
                cudaStream_t s);
 // bytes: the launch's algorithmic bytes (payload read, codes written).
 // For streams with outliers, sub_olo[slot * (kNSub + 1) + u] receives where
 // sub-chunk u of each decoded chunk starts in the stream's outlier list
 // (u = nsub: where the chunk ends).
-int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint16_t* lut,
+int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,
                          uint16_t* codes, uint32_t* sub_olo, uint32_t* status, double bytes,
                          cudaStream_t s);
 
@@ -153,7 +153,7 @@ struct DecJobMulti {
   StreamGeo sg;
   int32_t b[3];
   int64_t bvol;
-  const uint16_t* lut;        // the stream's decode table
+  const uint32_t* lut;        // the stream's decode table (kLutSize entries)
   uint16_t* codes;
   uint32_t* sub_olo;
   uint32_t* status;
