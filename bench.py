@@ -559,7 +559,14 @@ def run_batched(args, dev):
            "batch_gbs": round(nbytes / (batch_ms * 1e-3) / 1e9, 2),
            "speedup": round(loop_ms / batch_ms, 3),
            "autotuned": {"lanes": best.lanes, "sm_share_den": best.sm_share_den,
-                         "graph": best.use_graph},
+                         "graph": best.use_graph, "work_queue": best.persistent,
+                         "schedule": (("level-major", "field-major")[best.schedule]
+                                      if best.persistent else None),
+                         "tiles_per_item": best.tiles_per_item if best.persistent else None},
+           "best_ms_by_arrangement": {
+               "per_field_launches": min((t["ms"] for t in bc.tuning if not t.get("queue")),
+                                         default=None),
+               "work_queue": min((t["ms"] for t in bc.tuning if t.get("queue")), default=None)},
            "identical_to_loop": bool(identical),
            "compression_ratio": round(nbytes / sum(sizes), 3),
            "candidates": len(bc.tuning)}

@@ -227,7 +227,24 @@ typedef struct {
   int lanes;         /* concurrent streams, 1..32 (0: 4) */
   int sm_share_den;  /* persistent grids sized for SMs / den, 1..64 (0: 1) */
   int use_graph;     /* 1: capture once, replay as one graph launch */
+  /* The work-queue arrangement (persistent = 1): every 3D field with the
+   * default predictor runs its level stages 2..L inside ONE persistent launch
+   * per dtype, whose blocks claim (field, level, tile) work items in schedule
+   * order from a counter (an item of level l waits, on the device, for its
+   * field's level l-1); fields' stages up to level 1 and after the levels run
+   * on the lanes before and after it.  Other fields (2D, ablation predictors)
+   * run the per-field path on the lanes meanwhile. */
+  int persistent;      /* 1: the work queue; needs ws_dev */
+  int schedule;        /* 0: every field's level 2, then level 3, ...; 1: field by field */
+  int tiles_per_item;  /* interior brick tiles per work item, 1..64 (0: 1) */
+  int blocks_per_sm;   /* blocks of the queue kernel per SM (0: as many as fit) */
+  void* ws_dev;        /* persistent: 256-byte aligned device memory of */
+  size_t ws_bytes;     /*   stz_compress_batch_workspace_size() bytes */
 } stz_batch_opts;
+
+/* Workspace of the work-queue arrangement of stz_compress_batch for these
+ * jobs (0 on invalid jobs). */
+size_t stz_compress_batch_workspace_size(int n, const stz_field_job* jobs);
 
 int stz_compress_batch(int n, const stz_field_job* jobs, unsigned long long* sizes_dev,
                        const stz_batch_opts* opts, void* stream);

@@ -82,6 +82,10 @@ static int zero_words(void* p, int64_t nwords, cudaStream_t st) {
   return cuda_ok(cudaGetLastError());
 }
 
+int launch_zero_words(uint32_t* p, int64_t nwords, cudaStream_t s) {
+  return zero_words(p, nwords, s);
+}
+
 namespace {
 constexpr int kReadbackBytes = 4096;
 thread_local uint8_t* tl_rb_host = nullptr;  // mapped, pinned, portable
@@ -601,15 +605,105 @@ int compress_check(const void* field_dev, const int64_t* dims, int ndim, int dty
 // Queues every stage of one compression on st without waiting for it.
 // no_coop: run the level-1 passes as plain launches (no cooperative launch),
 // as needed inside a captured graph whose branches run concurrently.
-int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, CompressDev* d) {
+// The compress arguments of level l (2..L) of job j.
+void compress_level_args(const CompressJob& j, int l, LevelArgs* out) {
   const Geo& g = j.g;
-  const int64_t* n = g.n;
-  const int dtype = g.dtype;
-  const int eb_mode = j.eb_mode;
-  const double eb = j.eb;
-  const void* field_dev = j.field;
-  const size_t out_cap = j.out_cap;
-  WsPlan w = plan_compress(g);
+  const WsPlan w = plan_compress(g);
+  uint8_t* ws = (uint8_t*)j.ws;
+  LevelArgs& a = *out;
+  memset(&a, 0, sizeof(a));
+  a.geo = g;
+  a.level = l;
+  a.pred = j.pred;
+  a.dp = (DevParams*)(ws + w.dp);
+  a.field = j.field;
+  int64_t M[3], m[3];
+  grid_extent(g.n, g.L, l - 1, M);
+  grid_extent(g.n, g.L, l, m);
+  a.coarse = ws + w.grid[l - 1];
+  a.fine = l < g.L ? (void*)(ws + w.grid[l]) : nullptr;
+  for (int d = 0; d < 3; d++) {
+    a.clo[d] = 0;
+    a.chi[d] = M[d];
+    a.flo[d] = 0;
+    a.fhi[d] = m[d];
+    a.tlo[d] = 0;
+    a.tcnt[d] = cdiv(M[d], g.b[d]);
+  }
+  a.codes = (uint16_t*)(ws + w.codes);
+  a.chunk_outliers = (uint32_t*)(ws + w.chunk_out);
+  a.hist = (uint32_t*)(ws + w.hist);
+  a.status = &((DevParams*)(ws + w.dp))->status;
+  for (int K = 1; K <= 7; K++) {
+    const StreamGeo& sg = g.s[1 + 7 * (l - 2) + K - 1];
+    for (int d = 0; d < 3; d++) {
+      a.sm[K].lo[d] = 0;
+      a.sm[K].cnt[d] = sg.nb[d];
+    }
+    a.sm[K].base = sg.chunk0;
+  }
+}
+
+#define STZ_TRY(x)               \
+  do {                           \
+    const int rc_ = (x);         \
+    if (rc_ != STZ_OK) return rc_; \
+  } while (0)
+
+// Compression up to level 1: the range pass (which also clears the
+// histograms and the per-chunk outlier counts), the bounds, the level-1
+// coder and level 1's histogram.
+int compress_prologue(const CompressJob& j, bool no_coop, cudaStream_t st) {
+  const Geo& g = j.g;
+  const WsPlan w = plan_compress(g);
+  uint8_t* ws = (uint8_t*)j.ws;
+  DevParams* dp = (DevParams*)(ws + w.dp);
+  uint16_t* codes = (uint16_t*)(ws + w.codes);
+  uint32_t* hist = (uint32_t*)(ws + w.hist);
+  uint32_t* chunk_out = (uint32_t*)(ws + w.chunk_out);
+  {
+    unsigned long long* part = (unsigned long long*)(ws + w.range_part);
+    int nparts = 0;
+    STZ_TRY(launch_range(j.field, g.dtype, j.eb_mode == STZ_EB_REL ? vol(g.n) : 0, part, &nparts,
+                         hist, (int64_t)g.nstreams * kAlphabet, chunk_out, g.total_chunks, st));
+    STZ_TRY(launch_params(dp, part, nparts, g.dtype, j.eb_mode, j.eb, g.L, kRadius, j.eb_ratio,
+                          j.pred, st));
+  }
+  {
+    BaseArgs a;
+    memset(&a, 0, sizeof(a));
+    a.geo = g;
+    a.dp = dp;
+    a.field = j.field;
+    a.g1 = ws + w.grid[1];
+    a.codes = codes;
+    a.chunk_outliers = chunk_out;
+    for (int d = 0; d < 3; d++) {
+      a.sm.lo[d] = 0;
+      a.sm.cnt[d] = g.s[0].nb[d];
+    }
+    a.sm.base = g.s[0].chunk0;
+    STZ_TRY(no_coop ? launch_base_nocoop(a, false, st) : launch_base(a, false, st));
+  }
+  STZ_TRY(launch_stream_hist(g, 0, codes, hist, st));
+  return STZ_OK;
+}
+
+// Levels 2..L of a compression, one level launch after another.
+int compress_levels(const CompressJob& j, cudaStream_t st) {
+  for (int l = 2; l <= j.g.L; l++) {
+    LevelArgs a;
+    compress_level_args(j, l, &a);
+    STZ_TRY(launch_level(a, false, st));
+  }
+  return STZ_OK;
+}
+
+// The entropy stage and the container: codebooks, chunk bit counts, their
+// scans, the section layout, the sections and the payload, the result word.
+int compress_epilogue(const CompressJob& j, cudaStream_t st, CompressDev* d) {
+  const Geo& g = j.g;
+  const WsPlan w = plan_compress(g);
   uint8_t* ws = (uint8_t*)j.ws;
   DevParams* dp = (DevParams*)(ws + w.dp);
   uint16_t* codes = (uint16_t*)(ws + w.codes);
@@ -623,81 +717,13 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
   BookDev* books = (BookDev*)(ws + w.books);
   LayoutDev* lay = (LayoutDev*)(ws + w.lay);
   uint8_t* out = (uint8_t*)j.out;
-  int rc = STZ_OK;
-#define STZ_TRY(x)          \
-  do {                      \
-    rc = (x);               \
-    if (rc != STZ_OK) return rc; \
-  } while (0)
-  {
-    // the range pass (none in absolute mode) also clears the histograms and
-    // the per-chunk outlier counts
-    unsigned long long* part = (unsigned long long*)(ws + w.range_part);
-    int nparts = 0;
-    STZ_TRY(launch_range(field_dev, dtype, eb_mode == STZ_EB_REL ? vol(n) : 0, part, &nparts,
-                         hist, (int64_t)g.nstreams * kAlphabet, chunk_out, g.total_chunks, st));
-    STZ_TRY(launch_params(dp, part, nparts, dtype, eb_mode, eb, g.L, kRadius, j.eb_ratio, j.pred,
-                          st));
-  }
-  {
-    BaseArgs a;
-    memset(&a, 0, sizeof(a));
-    a.geo = g;
-    a.dp = dp;
-    a.field = field_dev;
-    a.g1 = ws + w.grid[1];
-    a.codes = codes;
-    a.chunk_outliers = chunk_out;
-    for (int d = 0; d < 3; d++) {
-      a.sm.lo[d] = 0;
-      a.sm.cnt[d] = g.s[0].nb[d];
-    }
-    a.sm.base = g.s[0].chunk0;
-    STZ_TRY(no_coop ? launch_base_nocoop(a, false, st) : launch_base(a, false, st));
-  }
-  STZ_TRY(launch_stream_hist(g, 0, codes, hist, st));
-  for (int l = 2; l <= g.L; l++) {
-    LevelArgs a;
-    memset(&a, 0, sizeof(a));
-    a.geo = g;
-    a.level = l;
-    a.pred = j.pred;
-    a.dp = dp;
-    a.field = field_dev;
-    int64_t M[3], m[3];
-    grid_extent(g.n, g.L, l - 1, M);
-    grid_extent(g.n, g.L, l, m);
-    a.coarse = ws + w.grid[l - 1];
-    a.fine = l < g.L ? (void*)(ws + w.grid[l]) : nullptr;
-    for (int d = 0; d < 3; d++) {
-      a.clo[d] = 0;
-      a.chi[d] = M[d];
-      a.flo[d] = 0;
-      a.fhi[d] = m[d];
-      a.tlo[d] = 0;
-      a.tcnt[d] = cdiv(M[d], g.b[d]);
-    }
-    a.codes = codes;
-    a.chunk_outliers = chunk_out;
-    a.hist = hist;
-    a.status = &dp->status;
-    for (int K = 1; K <= 7; K++) {
-      const StreamGeo& sg = g.s[1 + 7 * (l - 2) + K - 1];
-      for (int d = 0; d < 3; d++) {
-        a.sm[K].lo[d] = 0;
-        a.sm[K].cnt[d] = sg.nb[d];
-      }
-      a.sm[K].base = sg.chunk0;
-    }
-    STZ_TRY(launch_level(a, false, st));
-  }
   STZ_TRY(launch_codebook(g, hist, enc, books, st));
   STZ_TRY(launch_chunk_words(g, codes, enc, chunk_words, lane_bits, st));
   STZ_TRY(launch_scan2(chunk_words, chunk_out, g.total_chunks,
                        (unsigned long long*)(ws + w.scan_sums), word_off, out_off, st));
-  STZ_TRY(launch_layout(g, dp, eb_mode, word_off, out_off, books, lay, out, out_cap, st));
+  STZ_TRY(launch_layout(g, dp, j.eb_mode, word_off, out_off, books, lay, out, j.out_cap, st));
   STZ_TRY(launch_sections(g, lay, books, word_off, dp, out, st));
-  STZ_TRY(launch_pack(g, codes, enc, lane_bits, word_off, lay->s, out, dp, field_dev, chunk_out,
+  STZ_TRY(launch_pack(g, codes, enc, lane_bits, word_off, lay->s, out, dp, j.field, chunk_out,
                       out_off, st));
   unsigned long long* res = (unsigned long long*)(ws + w.result);
   {
@@ -705,12 +731,19 @@ int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, Compre
     k_result<<<1, 32, 0, st>>>(&lay->total, word_off + g.total_chunks, &dp->status, res);
     STZ_TRY(cuda_ok(cudaGetLastError()));
   }
-#undef STZ_TRY
   d->total = &lay->total;
   d->payload_words = word_off + g.total_chunks;
   d->status = &dp->status;
   d->result = res;
   return STZ_OK;
+}
+#undef STZ_TRY
+
+int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, CompressDev* d) {
+  int rc = compress_prologue(j, no_coop, st);
+  if (rc == STZ_OK) rc = compress_levels(j, st);
+  if (rc == STZ_OK) rc = compress_epilogue(j, st, d);
+  return rc;
 }
 
 // Captured compressions, by their arguments: a repeated stz_compress replays

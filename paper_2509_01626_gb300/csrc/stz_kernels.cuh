@@ -1,6 +1,8 @@
 // stz_kernels.cuh -- host-side launchers of the STZ kernels (one .cu each).
 #pragma once
 
+#include <vector>
+
 #include "stz_common.cuh"
 
 namespace stz {
@@ -79,6 +81,61 @@ int launch_level(const LevelArgs& a, bool decode, cudaStream_t s);
 bool level_multi_ok(const LevelArgs& a);
 size_t level_multi_arena_bytes(int n);
 int launch_level_multi(const LevelArgs* h, int n, uint8_t* arena_dev, cudaStream_t s);
+
+// The level stages (2..L) of many fields of one dtype in one persistent
+// launch over (field, level, tile) work items (the batched form of
+// compression).  h[r]: the compress arguments of one (field, level) group;
+// every group passes level_queue_ok, and a group of level l > 2 has its
+// field's level l-1 among the others (same code buffer).  schedule: 0 every
+// field's level 2 first, then level 3, ...; 1 field by field in the order of
+// h.  gran: interior tiles per work item (1..64).  blocks_per_sm: 0 for the
+// occupancy limit.  arena_dev: 256-byte aligned device memory of
+// level_queue_arena_bytes(n) bytes.  plan_level_queue fills the plan on the
+// host; write_level_queue queues the copy of its arguments into the arena
+// (not inside a stream capture: the source is pageable); run_level_queue
+// zeroes the queue's counters and launches the kernel (capturable).
+struct ShellGeo;
+struct QueueGroup {
+  int64_t ntile;   // interior tiles of the group (0: none)
+  int64_t nshell;  // boundary cells
+  uint32_t items;  // work items: ceil(ntile / gran) + ceil(nshell / 256)
+  int dep;         // the group whose items must all be done first (-1: none)
+  int pair, vec;   // fast_tile's paired accesses; 16-byte tile copies
+};
+struct QueueSeg {
+  int64_t first;  // first work item
+  int group;
+  int kind;       // 0: interior tiles, 1: boundary cells
+};
+struct LevelQueue {
+  const LevelArgs* args;
+  const ShellGeo* shs;
+  const QueueGroup* groups;
+  const QueueSeg* segs;
+  int nseg;
+  uint32_t* done;             // completed items per group
+  unsigned long long* claim;  // next item to claim
+  uint32_t* abort;            // set by a block whose wait ran out
+  int64_t total;
+  int gran;
+};
+struct LevelQueuePlan {
+  std::vector<uint8_t> buf;  // the arena's contents
+  uint8_t* arena;
+  void* counters;            // the words run_level_queue zeroes
+  int64_t counter_words;
+  LevelQueue qa;
+  size_t smem;
+  int64_t grid;              // 0: nothing to do
+  bool f64;
+  double bytes;
+};
+bool level_queue_ok(const LevelArgs& a);
+size_t level_queue_arena_bytes(int n);
+int plan_level_queue(const LevelArgs* h, int n, int schedule, int gran, int blocks_per_sm,
+                     uint8_t* arena_dev, LevelQueuePlan* P);
+int write_level_queue(const LevelQueuePlan& P, cudaStream_t s);
+int run_level_queue(const LevelQueuePlan& P, cudaStream_t s);
 
 // ---- stz_huffman.cu: histograms, codebooks, chunk coding ----
 // histogram of stream 0 from its slots
@@ -202,6 +259,15 @@ int compress_check(const void* field_dev, const int64_t* dims, int ndim, int dty
                    double eb, void* out_dev, size_t out_cap, void* ws_dev, size_t ws_bytes,
                    CompressJob* j, const stz_compress_opts* opts = nullptr);
 int compress_enqueue(const CompressJob& j, bool no_coop, cudaStream_t st, CompressDev* d);
+// compress_enqueue in its three stages: up to level 1 (range, bounds, level-1
+// coder and histogram); levels 2..L (one level launch after another); the
+// entropy stage and the container.  compress_level_args: the arguments of
+// level l of job j (for the batched form's work queue, which runs the levels
+// of many fields in one launch instead of compress_levels).
+int compress_prologue(const CompressJob& j, bool no_coop, cudaStream_t st);
+int compress_levels(const CompressJob& j, cudaStream_t st);
+int compress_epilogue(const CompressJob& j, cudaStream_t st, CompressDev* d);
+void compress_level_args(const CompressJob& j, int l, LevelArgs* out);
 // stz_compress's launch sequence as a graph captured once per argument tuple
 // and replayed
 int compress_graph_launch(const CompressJob& j, const void* field, const int64_t dims[3], int ndim,
@@ -220,6 +286,8 @@ int launch_roi(const void* field, int dtype, const int64_t n[3], const int64_t b
 // calling thread set a share (the batched form runs several fields' kernels
 // side by side and gives each a part of the GPU).
 int launch_sms();
+// zero fill of device words by a kernel
+int launch_zero_words(uint32_t* p, int64_t nwords, cudaStream_t s);
 void set_launch_share(int num, int den);
 
 // Lets kernel `func` take `bytes` of dynamic shared memory on the current

@@ -22,6 +22,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 namespace stz {
@@ -1436,6 +1437,294 @@ int launch_level_multi(const LevelArgs* h, int n, uint8_t* arena_dev, cudaStream
       return STZ_ERR_ARG;
   return h[0].geo.dtype == STZ_F32 ? run_level_multi<float>(h, n, arena_dev, s)
                                    : run_level_multi<double>(h, n, arena_dev, s);
+}
+
+// ---- the batched form: the level stages of many fields in one launch ----
+// Work items are (field, level, tile): `gran` consecutive interior brick
+// tiles of k_level_fast, or 256 boundary cells of k_level_shell, of one
+// (field, level) group.  The host lists them in a schedule order (all fields'
+// level 2, then all level 3, ...; or field by field) and every block claims
+// the next item from one counter.  An item of level l > 2 first waits until
+// every item of level l-1 of its field is done (a count per group, released
+// after the block's writes, read with acquire).  Items are claimed in order
+// and wait only on earlier ones, so the earliest unfinished item can always
+// proceed: no residency assumption is needed.  Each item runs the code of the
+// single-field kernels with its field's arguments; histogram counts of a group
+// gather in shared memory and go to the group's global histograms when the
+// block moves to another group, so every field's codes, grids and histograms
+// are those of its own launches.
+constexpr int kQueueWaitIters = 1 << 24;  // a bound on every wait (about a second)
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// waits until *done >= need; false when the bound ran out or another block
+// gave up (*abort set)
+__device__ bool queue_wait(const uint32_t* done, uint32_t need, const uint32_t* abort) {
+  for (int it = 0; it < kQueueWaitIters; it++) {
+    if (ld_acquire_u32(done) >= need) return true;
+    if (*(volatile const uint32_t*)abort) return false;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kLevelThreads, 2) k_level_queue(const __grid_constant__ LevelQueue qa) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TileInfo s_ti;
+  __shared__ long long s_item;
+  __shared__ int s_ok;
+  constexpr size_t tbytes = fast_tile_bytes<T, false>();
+  T* tile = (T*)smem;
+  uint32_t* hist = (uint32_t*)(smem + tbytes);
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int w = tid; w < 7 * kHistWords; w += blockDim.x) hist[w] = 0;
+  int cur = -1;  // the group whose counts are in the shared histograms
+  QConst<T> q;
+  for (;;) {
+    if (tid == 0) s_item = (long long)atomicAdd(qa.claim, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= qa.total) break;
+    int lo = 0, hi = qa.nseg - 1;  // the last segment whose first item is <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (qa.segs[mid].first <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const QueueSeg sg = qa.segs[lo];
+    const int g = sg.group;
+    const LevelArgs& a = qa.args[g];
+    const QueueGroup& G = qa.groups[g];
+    if (g != cur) {
+      if (cur >= 0) {
+        flush_hist<T>(hist, qa.args[cur].hist, qa.args[cur].level);
+        __syncthreads();
+      }
+      cur = g;
+      q.load(a.dp, a.level, kRadius);
+    }
+    if (tid == 0) {
+      int ok = 1;
+      if (G.dep >= 0) ok = queue_wait(qa.done + G.dep, qa.groups[G.dep].items, qa.abort);
+      if (!ok) {
+        atomicOr(a.status, kStatTimeout);
+        atomicExch(qa.abort, 1u);
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const int64_t k = item - sg.first;
+    if (sg.kind == 0) {
+      int64_t M64[3];
+      grid_extent(a.geo.n, a.geo.L, a.level - 1, M64);
+      const int M[3] = {(int)M64[0], (int)M64[1], (int)M64[2]};
+      const int64_t sl = level_stride(a.geo.L, a.level);
+      const int xdz = (int)(sl * a.geo.n[1] * a.geo.n[2]), xdy = (int)(sl * a.geo.n[2]),
+                xdx = (int)sl;
+      const int fe2 = (int)(a.fhi[2] - a.flo[2]);
+      const int fdz = (int)((a.fhi[1] - a.flo[1]) * fe2);
+      const int64_t t1 = min((k + 1) * (int64_t)qa.gran, G.ntile);
+      for (int64_t t = k * qa.gran; t < t1; t++) {
+        tile_info(a, t, s_ti);
+        if (G.vec) tile_prefetch<T, true>(a, t, tile);
+        else tile_prefetch<T, false>(a, t, tile);
+        cp_async_wait_all();
+        __syncthreads();
+        const bool full = tile_full(a, s_ti, false);
+        if (G.pair) {
+          if (full)
+            fast_tile<T, false, true, true>(a, tile, s_ti, M, q, T(0), hist, xdz, xdy, xdx, fe2, fdz);
+          else
+            fast_tile<T, false, false, true>(a, tile, s_ti, M, q, T(0), hist, xdz, xdy, xdx, fe2,
+                                             fdz);
+        } else {
+          if (full)
+            fast_tile<T, false, true, false>(a, tile, s_ti, M, q, T(0), hist, xdz, xdy, xdx, fe2,
+                                             fdz);
+          else
+            fast_tile<T, false, false, false>(a, tile, s_ti, M, q, T(0), hist, xdz, xdy, xdx, fe2,
+                                              fdz);
+        }
+        __syncthreads();  // the tile buffer and s_ti are reused
+      }
+    } else {
+      uint32_t nR[7] = {0, 0, 0, 0, 0, 0, 0};
+      const int64_t i = k * kLevelThreads + tid;
+      shell_cell<T, false>(a, qa.shs[g], i, i < G.nshell, q, hist, nR);
+#pragma unroll
+      for (int K = 0; K < 7; K++) {
+        const uint32_t n = __reduce_add_sync(0xffffffffu, nR[K]);
+        if (lane == 0 && n) atomicAdd(&hist[K * kHistWords + kRadius], n);
+      }
+      __syncthreads();
+    }
+    // the item's grid points, codes and outlier counts, then its completion
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(qa.done + g, 1u);
+    }
+  }
+  __syncthreads();
+  if (cur >= 0) flush_hist<T>(hist, qa.args[cur].hist, qa.args[cur].level);
+}
+
+// A group of the queue: the level stage of one field, its interior tiles and
+// boundary cells.  False when the group does not suit the fast kernels.
+bool level_queue_ok(const LevelArgs& a) { return level_multi_ok(a) && a.geo.ndim == 3; }
+
+static size_t queue_layout(int n, int nseg, size_t off[8]) {
+  size_t o = 0;
+  off[0] = o;  // LevelArgs[n]
+  o += al256l(sizeof(LevelArgs) * (size_t)n);
+  off[1] = o;  // ShellGeo[n]
+  o += al256l(sizeof(ShellGeo) * (size_t)n);
+  off[2] = o;  // QueueGroup[n]
+  o += al256l(sizeof(QueueGroup) * (size_t)n);
+  off[3] = o;  // QueueSeg[nseg]
+  o += al256l(sizeof(QueueSeg) * (size_t)nseg);
+  off[4] = o;  // done[n], claim, abort: the words the host zeroes
+  o += al256l(sizeof(uint32_t) * (size_t)n + 16);
+  return o;
+}
+
+size_t level_queue_arena_bytes(int n) {
+  size_t off[8];
+  return queue_layout(n, 2 * n, off);
+}
+
+template <typename T>
+static int plan_queue(const LevelArgs* h, int n, int schedule, int gran, int blocks_per_sm,
+                      uint8_t* arena, LevelQueuePlan* P) {
+  // the groups' order: level-major (every field's level 2, then level 3, ...)
+  // or field-major (the caller's order: a field's levels ascending); a
+  // group's dependency is its own field's previous level
+  std::vector<int> order((size_t)n);
+  for (int r = 0; r < n; r++) order[(size_t)r] = r;
+  if (schedule == 0)
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return h[x].level < h[y].level; });
+  size_t off[8];
+  const size_t bytes = queue_layout(n, 2 * n, off);
+  P->buf.assign(bytes, 0);
+  memcpy(P->buf.data() + off[0], h, sizeof(LevelArgs) * (size_t)n);
+  ShellGeo* shs = (ShellGeo*)(P->buf.data() + off[1]);
+  QueueGroup* grp = (QueueGroup*)(P->buf.data() + off[2]);
+  QueueSeg* seg = (QueueSeg*)(P->buf.data() + off[3]);
+  constexpr int epc = 16 / sizeof(T);
+  double fast_bytes = 0.0, shell_bytes = 0.0;
+  for (int r = 0; r < n; r++) {
+    const LevelArgs& a = h[r];
+    int64_t M[3];
+    grid_extent(a.geo.n, a.geo.L, a.level - 1, M);
+    const int64_t cells = shell_geo(a, M, &shs[r]);
+    const int64_t nshell = shs[r].nA + shs[r].nB + shs[r].nC;
+    const bool interior = M[0] >= 4 && M[1] >= 4 && M[2] >= 4 && cells > 0;
+    QueueGroup& G = grp[r];
+    G.ntile = interior ? a.tcnt[0] * a.tcnt[1] * a.tcnt[2] : 0;
+    G.nshell = nshell;
+    const int64_t items = cdiv(G.ntile, gran) + cdiv(nshell, kLevelThreads);
+    if (items >= ((int64_t)1 << 31)) return STZ_ERR_ARG;
+    G.items = (uint32_t)items;
+    G.dep = -1;  // level 2 follows level 1, which precedes the launch
+    for (int p = 0; p < n; p++)
+      if (p != r && h[p].codes == a.codes && h[p].level == a.level - 1) G.dep = p;
+    if (a.level > 2 && G.dep < 0) return STZ_ERR_ARG;  // its level below is not queued
+    const uintptr_t a2 = 2 * sizeof(T);
+    bool pair = a.fine == nullptr || ((uintptr_t)a.fine % a2 == 0 &&
+                                      (a.fhi[2] - a.flo[2]) % 2 == 0 && a.flo[2] % 2 == 0);
+    if (level_stride(a.geo.L, a.level) == 1)
+      pair = pair && (uintptr_t)a.field % a2 == 0 && a.geo.n[2] % 2 == 0;
+    G.pair = pair ? 1 : 0;
+    G.vec = ((uintptr_t)a.coarse & 15) == 0 && (a.chi[2] - a.clo[2]) % epc == 0 &&
+            a.clo[2] % epc == 0;
+    const double bpc = cell_bytes<T, false>(a);
+    fast_bytes += (double)(cells - nshell) * bpc;
+    shell_bytes += (double)nshell * bpc;
+  }
+  // a group's level below must come earlier in the order
+  std::vector<int> pos((size_t)n);
+  for (int i = 0; i < n; i++) pos[(size_t)order[(size_t)i]] = i;
+  for (int r = 0; r < n; r++)
+    if (grp[r].dep >= 0 && pos[(size_t)grp[r].dep] > pos[(size_t)r]) return STZ_ERR_ARG;
+  int nseg = 0;
+  int64_t total = 0;
+  for (int r : order) {
+    const QueueGroup& G = grp[r];
+    if (G.ntile > 0) {
+      seg[nseg] = QueueSeg{total, r, 0};
+      total += cdiv(G.ntile, gran);
+      nseg++;
+    }
+    if (G.nshell > 0) {
+      seg[nseg] = QueueSeg{total, r, 1};
+      total += cdiv(G.nshell, kLevelThreads);
+      nseg++;
+    }
+  }
+  LevelQueue& qa = P->qa;
+  qa.args = (const LevelArgs*)(arena + off[0]);
+  qa.shs = (const ShellGeo*)(arena + off[1]);
+  qa.groups = (const QueueGroup*)(arena + off[2]);
+  qa.segs = (const QueueSeg*)(arena + off[3]);
+  qa.nseg = nseg;
+  qa.done = (uint32_t*)(arena + off[4]);
+  qa.claim =
+      (unsigned long long*)(arena + off[4] + ((sizeof(uint32_t) * (size_t)n + 7) & ~(size_t)7));
+  qa.abort = (uint32_t*)(qa.claim + 1);
+  qa.total = total;
+  qa.gran = gran;
+  P->arena = arena;
+  P->counters = arena + off[4];
+  P->counter_words = (int64_t)((bytes - off[4]) / 4);
+  P->f64 = sizeof(T) == 8;
+  P->bytes = fast_bytes + shell_bytes;
+  P->smem = fast_tile_bytes<T, false>() + sizeof(uint32_t) * 7 * kHistWords;
+  auto kern = k_level_queue<T>;
+  if (allow_smem((const void*)kern, P->smem) != STZ_OK) return STZ_ERR_CUDA;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLevelThreads, P->smem);
+  if (per_sm < 1) per_sm = 1;
+  if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+  P->grid = imin(total, (int64_t)sm_count() * per_sm);
+  return STZ_OK;
+}
+
+int plan_level_queue(const LevelArgs* h, int n, int schedule, int gran, int blocks_per_sm,
+                     uint8_t* arena_dev, LevelQueuePlan* P) {
+  P->buf.clear();
+  P->grid = 0;
+  if (n <= 0) return STZ_OK;
+  if (gran < 1 || gran > 64 || (schedule != 0 && schedule != 1) || ((uintptr_t)arena_dev & 255))
+    return STZ_ERR_ARG;
+  for (int r = 0; r < n; r++)
+    if (!level_queue_ok(h[r]) || h[r].geo.dtype != h[0].geo.dtype) return STZ_ERR_ARG;
+  return h[0].geo.dtype == STZ_F32
+             ? plan_queue<float>(h, n, schedule, gran, blocks_per_sm, arena_dev, P)
+             : plan_queue<double>(h, n, schedule, gran, blocks_per_sm, arena_dev, P);
+}
+
+int write_level_queue(const LevelQueuePlan& P, cudaStream_t s) {
+  if (P.grid == 0) return STZ_OK;
+  // from pageable memory: staged before the call returns
+  return cuda_ok(cudaMemcpyAsync(P.arena, P.buf.data(), P.buf.size(), cudaMemcpyHostToDevice, s));
+}
+
+int run_level_queue(const LevelQueuePlan& P, cudaStream_t s) {
+  if (P.grid == 0) return STZ_OK;
+  int rc = launch_zero_words((uint32_t*)P.counters, P.counter_words, s);
+  if (rc != STZ_OK) return rc;
+  ProfScope ps_(P.f64 ? "k_level_queue_f64" : "k_level_queue_f32", s, P.bytes);
+  if (P.f64)
+    k_level_queue<double><<<(unsigned)P.grid, kLevelThreads, P.smem, s>>>(P.qa);
+  else
+    k_level_queue<float><<<(unsigned)P.grid, kLevelThreads, P.smem, s>>>(P.qa);
+  return cuda_ok(cudaGetLastError());
 }
 
 int launch_level(const LevelArgs& a, bool decode, cudaStream_t s) {

@@ -70,9 +70,15 @@ PREDICTORS = {"cubic": 0, "linear": 1, "direct": 2}
 
 
 class BatchOpts(ctypes.Structure):
-    """stz_batch_opts: launch arrangement of a batch (never changes bytes)."""
+    """stz_batch_opts: launch arrangement of a batch (never changes bytes).
+    persistent = 1 runs the level stages of the 3D fields in one work-queue
+    launch per dtype (schedule, tiles_per_item, blocks_per_sm), with the
+    batch workspace ws_dev / ws_bytes."""
     _fields_ = [("lanes", ctypes.c_int), ("sm_share_den", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("schedule", ctypes.c_int), ("tiles_per_item", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("ws_dev", ctypes.c_void_p),
+                ("ws_bytes", ctypes.c_size_t)]
 
 
 class ServedField(ctypes.Structure):
@@ -133,6 +139,8 @@ def lib() -> ctypes.CDLL:
                                                     i64p, vp]
         L.stz_compress_batch.argtypes = [ctypes.c_int, ctypes.POINTER(FieldJob), vp,
                                          ctypes.POINTER(BatchOpts), vp]
+        L.stz_compress_batch_workspace_size.restype = sz
+        L.stz_compress_batch_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(FieldJob)]
         L.stz_region_workspace_size.restype = sz
         L.stz_region_workspace_size.argtypes = [vp, sz, sz, i64p, i64p, ctypes.c_int,
                                                 ctypes.c_int]
@@ -250,6 +258,12 @@ def compress_batch(jobs, sizes_dev: torch.Tensor, opts: BatchOpts | None = None,
                                   ctypes.byref(opts) if opts is not None else None,
                                   _stream(stream))
     _check(rc, "stz_compress_batch")
+
+
+def compress_batch_workspace_size(jobs) -> int:
+    """stz_compress_batch_workspace_size: bytes of the work-queue
+    arrangement's batch workspace for these jobs."""
+    return int(lib().stz_compress_batch_workspace_size(len(jobs), jobs))
 
 
 def info(comp: torch.Tensor) -> dict:

@@ -1,8 +1,10 @@
 """Batched form (stz_compress_batch): every field's container equals the
 single-field path's and the oracle's, bit for bit, under every launch
 arrangement the autotuner may pick (lanes, SM share, captured graph or plain
-launches); a replayed graph reads the fields' current contents; a field whose
-output buffer is too small is reported without disturbing the others."""
+launches, the work queue with either level schedule and several tile
+granularities and grid sizes); a replayed graph reads the fields' current
+contents; a field whose output buffer is too small is reported without
+disturbing the others."""
 import numpy as np
 import pytest
 
@@ -104,3 +106,53 @@ def test_capacity_reported_per_field(mods, ora):
     for i in (0, 2, 3, 4, 5, 6, 7):
         got = bc.outs[i][: v[i]].cpu().numpy()
         assert np.array_equal(got, ora.compress(xs[i], ebs[i], modes[i])), i
+
+
+def test_work_queue_matches_oracle_under_every_schedule(mods, ora):
+    """The level stages of the 3D fields in one persistent launch per dtype
+    over (field, level, tile) items: containers equal the oracle's whatever
+    the schedule, tiles per item, blocks per SM, lanes and graph; the 2D and
+    tiny fields take the per-field path beside it."""
+    stz, batch = mods
+    xs, ebs, modes = small_batch()
+    xs = xs + [synth.sinusoids((70, 90, 110), synth.seed_for(3, 5)),
+               synth.sinusoids((48, 40, 64), 11, dtype=np.float64, noise=0.0)]
+    ebs = ebs + [1e-3, 1e-4]
+    modes = modes + ["rel", "rel"]
+    fields = [torch.from_numpy(x).cuda() for x in xs]
+    refs = [ora.compress(x, eb, m) for x, eb, m in zip(xs, ebs, modes)]
+    bc = batch.BatchCompressor(fields, ebs, modes)
+    assert bc.bws.numel() > 1  # some fields are queued
+    for lanes, den, graph, queue in [(1, 1, 0, (0, 1, 0)), (4, 1, 0, (1, 1, 0)),
+                                     (4, 2, 1, (0, 4, 0)), (8, 1, 1, (1, 2, 1)),
+                                     (16, 4, 1, (0, 64, 2)), (2, 1, 0, (1, 3, 1))]:
+        for o in bc.outs:
+            o.fill_(0xA5)
+        bc.sizes_dev.fill_(-1)
+        bc.run(bc.opts_for(lanes, den, graph, queue))
+        got = [c.cpu().numpy() for c in bc.containers()]
+        for i, (g, r) in enumerate(zip(got, refs)):
+            assert g.size == r.size and np.array_equal(g, r), (lanes, den, graph, queue, i)
+    # a replayed work-queue graph compresses the fields' current contents
+    o = bc.opts_for(4, 1, 1, (0, 2, 0))
+    bc.run(o)
+    xs2 = [np.ascontiguousarray(x * 0.75 - 1.0).astype(x.dtype) for x in xs]
+    for f, x2 in zip(fields, xs2):
+        f.copy_(torch.from_numpy(x2))
+    bc.run(o)
+    for c, x2, eb, m in zip(bc.containers(), xs2, ebs, modes):
+        assert np.array_equal(c.cpu().numpy(), ora.compress(x2, eb, m))
+
+
+def test_work_queue_rejects_missing_workspace(mods):
+    stz, batch = mods
+    xs, ebs, modes = small_batch()
+    fields = [torch.from_numpy(x).cuda() for x in xs]
+    bc = batch.BatchCompressor(fields, ebs, modes)
+    o = bc.opts_for(4, 1, 0, (0, 1, 0))
+    o.ws_bytes = 0
+    with pytest.raises(stz.StzError):
+        bc.run(o)
+    o = bc.opts_for(4, 1, 0, (2, 1, 0))  # no such schedule
+    with pytest.raises(stz.StzError):
+        bc.run(o)

@@ -116,6 +116,36 @@ def test_batch_argument_errors_need_no_gpu(stzmod):
     # zeroed jobs (no dims, null pointers) are rejected before any CUDA call
     o.lanes = 2
     assert L.stz_compress_batch(2, jobs, sizes, ctypes.byref(o), None) == stzmod.ERR_ARG
+    # the work queue: an unknown schedule or tile count is rejected up front
+    o.persistent, o.schedule = 1, 5
+    assert L.stz_compress_batch(2, jobs, sizes, ctypes.byref(o), None) == stzmod.ERR_ARG
+    o.schedule, o.tiles_per_item = 0, 65
+    assert L.stz_compress_batch(2, jobs, sizes, ctypes.byref(o), None) == stzmod.ERR_ARG
+    assert L.stz_compress_batch_workspace_size(2, jobs) == 0  # invalid jobs
+
+
+def test_batch_queue_workspace_needs_no_gpu(stzmod):
+    """The work queue's batch workspace holds the level groups of the 3D
+    fields only (sizing reads no device memory)."""
+    L = stzmod.lib()
+
+    def job(j, dims, dtype=0):
+        j.field_dev, j.out_dev, j.ws_dev = 1 << 12, 1 << 13, 1 << 20
+        for a, v in enumerate(dims + (0,) * (3 - len(dims))):
+            j.dims[a] = v
+        j.ndim, j.dtype, j.eb_mode, j.eb = len(dims), dtype, 1, 1e-3
+        j.out_cap, j.ws_bytes = 1 << 40, 1 << 40
+
+    jobs = (stzmod.FieldJob * 3)()
+    job(jobs[0], (64, 64, 64))
+    job(jobs[1], (180, 360))
+    job(jobs[2], (40, 33, 27), 1)
+    both = L.stz_compress_batch_workspace_size(3, jobs)
+    first = L.stz_compress_batch_workspace_size(1, jobs)
+    assert both > first > 0 and both % 256 == 0
+    only2d = (stzmod.FieldJob * 1)()
+    job(only2d[0], (180, 360))
+    assert L.stz_compress_batch_workspace_size(1, only2d) == 0
 
 
 def test_region_sizes_and_async_errors_need_no_gpu(stzmod):
