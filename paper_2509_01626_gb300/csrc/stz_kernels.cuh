@@ -1,6 +1,8 @@
 // stz_kernels.cuh -- host-side launchers of the STZ kernels (one .cu each).
 #pragma once
 
+#include <cuda.h>
+
 #include <vector>
 
 #include "stz_common.cuh"
@@ -101,6 +103,7 @@ struct QueueGroup {
   uint32_t items;  // work items: ceil(ntile / gran) + ceil(nshell / 256)
   int dep;         // the group whose items must all be done first (-1: none)
   int pair, vec;   // fast_tile's paired accesses; 16-byte tile copies
+  int tma;         // the coarse tile by one TMA copy (tensor map tmaps[group])
 };
 struct QueueSeg {
   int64_t first;  // first work item
@@ -112,6 +115,7 @@ struct LevelQueue {
   const ShellGeo* shs;
   const QueueGroup* groups;
   const QueueSeg* segs;
+  const CUtensorMap* tmaps;   // per group (used where groups[g].tma)
   int nseg;
   uint32_t* done;             // completed items per group
   unsigned long long* claim;  // next item to claim

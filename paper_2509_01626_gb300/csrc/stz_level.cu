@@ -1472,20 +1472,43 @@ __device__ bool queue_wait(const uint32_t* done, uint32_t need, const uint32_t* 
   return false;
 }
 
+// Tile buffers of the queue kernel: two for f32 (the next tile of an item
+// loads while the current one is computed), one for f64 (two would leave
+// room for one block per SM beside the histograms).
+template <typename T>
+__host__ __device__ constexpr int queue_bufs() { return sizeof(T) == 4 ? 2 : 1; }
+template <typename T>
+__host__ __device__ constexpr size_t queue_smem() {
+  return 128 + queue_bufs<T>() * fast_tile_bytes<T, true>() + sizeof(uint32_t) * 7 * kHistWords;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kLevelThreads, 2) k_level_queue(const __grid_constant__ LevelQueue qa) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ TileInfo s_ti;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ TileInfo s_ti[2];
+  __shared__ __align__(8) unsigned long long s_bar[2];
   __shared__ long long s_item;
   __shared__ int s_ok;
-  constexpr size_t tbytes = fast_tile_bytes<T, false>();
-  T* tile = (T*)smem;
-  uint32_t* hist = (uint32_t*)(smem + tbytes);
+  constexpr int NB = queue_bufs<T>();
+  constexpr size_t tbytes = fast_tile_bytes<T, true>();
+  // TMA destinations are 128-byte aligned (the launch adds 128 bytes of slack)
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  T* tiles[2] = {(T*)smem, (T*)(smem + (NB - 1) * tbytes)};
+  uint32_t* hist = (uint32_t*)(smem + NB * tbytes);
   const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(&s_bar[0]);
+    mbar_init(&s_bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
   for (int w = tid; w < 7 * kHistWords; w += blockDim.x) hist[w] = 0;
-  int cur = -1;  // the group whose counts are in the shared histograms
+  __syncthreads();
+  uint32_t phase = 0u;  // bit b: parity of buffer b's next completion
+  int b = 0;            // the buffer of the next tile
+  int cur = -1;         // the group whose counts are in the shared histograms
+  bool stop = false;
   QConst<T> q;
-  for (;;) {
+  while (!stop) {
     if (tid == 0) s_item = (long long)atomicAdd(qa.claim, 1ull);
     __syncthreads();
     const int64_t item = s_item;
@@ -1529,30 +1552,65 @@ __global__ void __launch_bounds__(kLevelThreads, 2) k_level_queue(const __grid_c
                 xdx = (int)sl;
       const int fe2 = (int)(a.fhi[2] - a.flo[2]);
       const int fdz = (int)((a.fhi[1] - a.flo[1]) * fe2);
-      const int64_t t1 = min((k + 1) * (int64_t)qa.gran, G.ntile);
-      for (int64_t t = k * qa.gran; t < t1; t++) {
-        tile_info(a, t, s_ti);
-        if (G.vec) tile_prefetch<T, true>(a, t, tile);
-        else tile_prefetch<T, false>(a, t, tile);
-        cp_async_wait_all();
-        __syncthreads();
-        const bool full = tile_full(a, s_ti, false);
+      const bool tma = G.tma != 0;
+      const CUtensorMap* tm = qa.tmaps + g;
+      // tile t of the item into buffer bb: its stream information, and its
+      // coarse grid with halo by one TMA copy or per-thread copies
+      auto issue = [&](int64_t t, int bb) {
+        tile_info(a, t, s_ti[bb]);
+        if (tma) {
+          if (tid == 0) tma_tile<T>(*tm, a, t, tiles[bb], &s_bar[bb]);
+        } else if (G.vec) {
+          tile_prefetch<T, true>(a, t, tiles[bb]);
+        } else {
+          tile_prefetch<T, false>(a, t, tiles[bb]);
+        }
+      };
+      const int64_t t0 = k * (int64_t)qa.gran, t1 = min(t0 + (int64_t)qa.gran, G.ntile);
+      issue(t0, b);
+      for (int64_t t = t0; t < t1; t++) {
+        if (tma) {
+          const bool ok = mbar_wait(&s_bar[b], (phase >> b) & 1u);
+          phase ^= 1u << b;
+          if (__syncthreads_or(!ok)) {
+            // the copy did not complete in time: report it, give it one more
+            // bounded wait so that no copy is in flight at exit, and stop
+            if (tid == 0) {
+              atomicOr(a.status, kStatTimeout);
+              atomicExch(qa.abort, 1u);
+            }
+            mbar_wait(&s_bar[b], ((phase >> b) & 1u) ^ 1u);
+            stop = true;
+            break;
+          }
+        } else {
+          cp_async_wait_all();
+          __syncthreads();
+        }
+        const int nb = NB == 2 ? b ^ 1 : b;
+        if (NB == 2 && t + 1 < t1) issue(t + 1, nb);
+        const TileInfo& ti = s_ti[b];
+        const bool full = tile_full(a, ti, false);
         if (G.pair) {
           if (full)
-            fast_tile<T, false, true, true>(a, tile, s_ti, M, q, T(0), hist, xdz, xdy, xdx, fe2, fdz);
+            fast_tile<T, false, true, true>(a, tiles[b], ti, M, q, T(0), hist, xdz, xdy, xdx, fe2,
+                                            fdz);
           else
-            fast_tile<T, false, false, true>(a, tile, s_ti, M, q, T(0), hist, xdz, xdy, xdx, fe2,
-                                             fdz);
+            fast_tile<T, false, false, true>(a, tiles[b], ti, M, q, T(0), hist, xdz, xdy, xdx,
+                                             fe2, fdz);
         } else {
           if (full)
-            fast_tile<T, false, true, false>(a, tile, s_ti, M, q, T(0), hist, xdz, xdy, xdx, fe2,
-                                             fdz);
+            fast_tile<T, false, true, false>(a, tiles[b], ti, M, q, T(0), hist, xdz, xdy, xdx,
+                                             fe2, fdz);
           else
-            fast_tile<T, false, false, false>(a, tile, s_ti, M, q, T(0), hist, xdz, xdy, xdx, fe2,
-                                              fdz);
+            fast_tile<T, false, false, false>(a, tiles[b], ti, M, q, T(0), hist, xdz, xdy, xdx,
+                                              fe2, fdz);
         }
-        __syncthreads();  // the tile buffer and s_ti are reused
+        __syncthreads();  // the buffer and its tile information are reused
+        if (NB == 1 && t + 1 < t1) issue(t + 1, b);
+        b = nb;
       }
+      if (stop) break;
     } else {
       uint32_t nR[7] = {0, 0, 0, 0, 0, 0, 0};
       const int64_t i = k * kLevelThreads + tid;
@@ -1588,6 +1646,8 @@ static size_t queue_layout(int n, int nseg, size_t off[8]) {
   o += al256l(sizeof(QueueGroup) * (size_t)n);
   off[3] = o;  // QueueSeg[nseg]
   o += al256l(sizeof(QueueSeg) * (size_t)nseg);
+  off[5] = o;  // CUtensorMap[n] (64-byte aligned)
+  o += al256l(sizeof(CUtensorMap) * (size_t)n);
   off[4] = o;  // done[n], claim, abort: the words the host zeroes
   o += al256l(sizeof(uint32_t) * (size_t)n + 16);
   return o;
@@ -1643,6 +1703,10 @@ static int plan_queue(const LevelArgs* h, int n, int schedule, int gran, int blo
     G.pair = pair ? 1 : 0;
     G.vec = ((uintptr_t)a.coarse & 15) == 0 && (a.chi[2] - a.clo[2]) % epc == 0 &&
             a.clo[2] % epc == 0;
+    // the coarse tile by one TMA copy where the coarse box allows a tensor map
+    CUtensorMap* tm = (CUtensorMap*)(P->buf.data() + off[5]) + r;
+    G.tma = coarse_tensor_map<T>(a, tm) ? 1 : 0;
+    if (!G.tma) memset(tm, 0, sizeof(*tm));
     const double bpc = cell_bytes<T, false>(a);
     fast_bytes += (double)(cells - nshell) * bpc;
     shell_bytes += (double)nshell * bpc;
@@ -1672,6 +1736,7 @@ static int plan_queue(const LevelArgs* h, int n, int schedule, int gran, int blo
   qa.shs = (const ShellGeo*)(arena + off[1]);
   qa.groups = (const QueueGroup*)(arena + off[2]);
   qa.segs = (const QueueSeg*)(arena + off[3]);
+  qa.tmaps = (const CUtensorMap*)(arena + off[5]);
   qa.nseg = nseg;
   qa.done = (uint32_t*)(arena + off[4]);
   qa.claim =
@@ -1684,7 +1749,7 @@ static int plan_queue(const LevelArgs* h, int n, int schedule, int gran, int blo
   P->counter_words = (int64_t)((bytes - off[4]) / 4);
   P->f64 = sizeof(T) == 8;
   P->bytes = fast_bytes + shell_bytes;
-  P->smem = fast_tile_bytes<T, false>() + sizeof(uint32_t) * 7 * kHistWords;
+  P->smem = queue_smem<T>();
   auto kern = k_level_queue<T>;
   if (allow_smem((const void*)kern, P->smem) != STZ_OK) return STZ_ERR_CUDA;
   int per_sm = 0;
