@@ -406,11 +406,14 @@ template <> struct Pair2<double> { using type = double2; };
 // issued one cell ahead of their use.  PAIR: the fine box and (at stride 1)
 // the field have even, aligned rows, so the x-neighbour points of a cell
 // (ox = 0, 1) are read and written as pairs.
-template <typename T, bool DEC, bool FULL, bool PAIR>
+// SC (decoding): the tile's codes were staged in shared memory, stream K's
+// chunk at scodes + (K - 1) * kTileSlot, and are read from there.
+constexpr int kTileSlot = kFBZ * kFBY * kFBX;  // symbols of a brick (one chunk)
+template <typename T, bool DEC, bool FULL, bool PAIR, bool SC = false>
 __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restrict__ tile,
                                           const TileInfo& ti, const int M[3], const QConst<T>& q,
                                           T two_eb, uint32_t* hist, int xdz, int xdy, int xdx,
-                                          int fe2, int fdz) {
+                                          int fe2, int fdz, const uint16_t* scodes = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int ly = tid >> 4, lx = tid & 15;
   const int c0z = ti.c0[0], cy = ti.c0[1] + ly, cx = ti.c0[2] + lx;
@@ -426,7 +429,8 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
 #pragma unroll
   for (int K = 1; K <= 7; K++) {
     const int l1 = FULL ? kFBY : ti.l[K][1], l2 = FULL ? kFBX : ti.l[K][2];
-    cp[K - 1] = a.codes + ti.slot[K] + (FULL ? tid : ly * l2 + lx);
+    uint16_t* base = SC ? (uint16_t*)scodes + (K - 1) * kTileSlot : a.codes + ti.slot[K];
+    cp[K - 1] = base + (FULL ? tid : ly * l2 + lx);
     cstep[K - 1] = l1 * l2;
   }
   const T* xp = DEC ? nullptr
@@ -617,7 +621,8 @@ __device__ __forceinline__ void fast_tile(const LevelArgs& a, const T* __restric
 #pragma unroll
         for (int K = 1; K <= 7; K++) {
           if (on[K - 1] && cv[K - 1] == 0) {  // outlier: its value from the list
-            const int64_t local = cp[K - 1] - (a.codes + ti.slot[K]);
+            const int64_t local =
+                cp[K - 1] - (SC ? (uint16_t*)scodes + (K - 1) * kTileSlot : a.codes + ti.slot[K]);
             if (!outlier_value(a.sub_olo, a.dense[K] != 0, ti.slot[K] / a.geo.bvol, (int)local,
                                ti.l[K][0] * ti.l[K][1] * ti.l[K][2], a.nsub, a.opos[K],
                                (const T*)a.oval[K], a.nout[K], ti.pos[K] + local, val[K - 1])) {
@@ -710,6 +715,29 @@ __device__ __forceinline__ void tma_tile(const CUtensorMap& m, const LevelArgs& 
       : "memory");
 }
 
+// Decoding f32, the interior kernel also stages a tile's codes in shared
+// memory: the 7 chunks (one per stream) of the tile's brick, copied with the
+// coarse tile one tile ahead, so that a cell's 7 code reads wait on shared
+// memory instead of global memory (2 x 28 KiB beside the 2 x 20 KiB tiles).
+template <typename T, bool DEC>
+__host__ __device__ constexpr bool stage_codes() { return DEC && sizeof(T) == 4; }
+constexpr size_t kTileCodeBytes = 7 * (size_t)kTileSlot * sizeof(uint16_t);
+
+// the chunks of tile ti's 7 streams into dst (stream K at (K - 1) * kTileSlot):
+// each brick's symbols, rounded up to whole 16-byte units (a slot holds a
+// whole brick's worth of symbols, so the rounding stays inside it)
+__device__ __forceinline__ void codes_prefetch(const LevelArgs& a, const TileInfo& ti,
+                                               uint16_t* dst) {
+  constexpr int kUnits = kTileSlot / 8;  // 16-byte units per chunk
+  for (int q = threadIdx.x; q < 7 * kUnits; q += blockDim.x) {
+    const int K = q / kUnits + 1, j = q - (K - 1) * kUnits;
+    const int cnt = ti.l[K][0] * ti.l[K][1] * ti.l[K][2];
+    if (j * 8 < cnt)
+      cp_async<16>(dst + (K - 1) * kTileSlot + j * 8, a.codes + ti.slot[K] + j * 8, true);
+  }
+  cp_async_commit();
+}
+
 template <typename T, bool TMA>
 __host__ __device__ constexpr size_t fast_tile_bytes() {
   return TMA ? (((size_t)(kFBZ + 3) * kFEZY * sizeof(T) + 127) & ~(size_t)127)
@@ -733,6 +761,9 @@ __global__ void __launch_bounds__(kLevelThreads, 2)
   constexpr size_t tbytes = fast_tile_bytes<T, TMA>();
   T* tiles[2] = {(T*)smem, (T*)(smem + tbytes)};
   uint32_t* hist = (uint32_t*)(smem + 2 * tbytes);
+  constexpr bool SC = stage_codes<T, DEC>() && !TMA;
+  uint16_t* scodes[2] = {(uint16_t*)(smem + 2 * tbytes),
+                         (uint16_t*)(smem + 2 * tbytes + kTileCodeBytes)};
   const int tid = threadIdx.x;
   if (TMA) {
     if (tid == 0) {
@@ -771,6 +802,10 @@ __global__ void __launch_bounds__(kLevelThreads, 2)
   if (tt < ntiles) {
     tile_info(a, tt, s_ti[0]);
     prefetch(tt, 0);
+    if (SC) {
+      __syncthreads();  // the tile's slots, from threads 0..6
+      codes_prefetch(a, s_ti[0], scodes[0]);
+    }
   }
   for (; tt < ntiles; tt += gridDim.x, b ^= 1) {
     if (TMA) {
@@ -791,13 +826,18 @@ __global__ void __launch_bounds__(kLevelThreads, 2)
     if (nt < ntiles) {
       tile_info(a, nt, s_ti[b ^ 1]);
       prefetch(nt, b ^ 1);
+      if (SC) {
+        __syncthreads();  // the next tile's slots, from threads 0..6
+        codes_prefetch(a, s_ti[b ^ 1], scodes[b ^ 1]);
+      }
     }
     const TileInfo& ti = s_ti[b];
     if (tile_full(a, ti, DEC))
-      fast_tile<T, DEC, true, PAIR>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2, fdz);
+      fast_tile<T, DEC, true, PAIR, SC>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2,
+                                        fdz, scodes[b]);
     else
-      fast_tile<T, DEC, false, PAIR>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2,
-                                     fdz);
+      fast_tile<T, DEC, false, PAIR, SC>(a, tiles[b], ti, M, q, two_eb, hist, xdz, xdy, xdx, fe2,
+                                         fdz, scodes[b]);
   }
   if (!TMA) cp_async_wait_all();
   if (!DEC) {
@@ -1243,6 +1283,7 @@ static int run_level_fast(const LevelArgs& a, const int64_t M[3], double bytes, 
   if (!tma) memset(&tmap, 0, sizeof(tmap));
   size_t smem = tma ? 2 * fast_tile_bytes<T, true>() + 128 : 2 * fast_tile_bytes<T, false>();
   if (!DEC) smem += sizeof(uint32_t) * 7 * kHistWords;
+  if (stage_codes<T, DEC>()) smem += 2 * kTileCodeBytes;
   // x-neighbour pairs as one access: the fine box's rows (and, reading the
   // field at stride 1, the field's rows) even and 2-element aligned
   const uintptr_t a2 = 2 * sizeof(T);
