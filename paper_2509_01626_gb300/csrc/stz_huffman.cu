@@ -1065,19 +1065,21 @@ __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecSt
         int k = (int)(b0 >> 5);
         int pos = (int)(b0 & 31);
         uint32_t cur = sp[k], nxt = sp[k + 1];
-        // the smallest low half of the entries met: below 1 << 11 once a
-        // window starts no code (the position then stops advancing)
-        uint32_t mn = 0xFFFFu;
-        // nbits <= 24 and pos < 32, so one word step brings pos below 32
+        // the smallest entry met: below 1 << 11 once a window starts no code
+        // (every valid entry has its first length, >= 1, at bit 11; an
+        // invalid window stops the position)
+        uint32_t mn = 0xFFFFFFFFu;
+        // nbits <= 24 and pos < 32, so at most one word is crossed; the step
+        // is written without a branch (the next word's load is predicated)
         auto advance = [&](uint32_t nbits) {
           pos += (int)nbits;
-          if (pos >= 32) {
-            pos -= 32;
-            cur = nxt;
-            bad |= k + 1 >= lim;  // past the chunk's payload and first pad word
-            k = min(k + 1, lim - 1);
-            nxt = sp[k + 1];
-          }
+          const int carry = pos >> 5;
+          pos &= 31;
+          cur = carry ? nxt : cur;
+          k += carry;
+          bad |= k >= lim;  // past the chunk's payload and first pad word
+          k = min(k, lim - 1);
+          if (carry) nxt = sp[k + 1];
         };
         // the next two symbols as a u16 pair: one lookup, and a second one
         // only when the second code does not end inside the first window
@@ -1087,7 +1089,7 @@ __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecSt
           const uint32_t L0 = (e >> 11) & 15u;
           uint32_t L1 = e >> 27;
           uint32_t pair = e & 0x07FF07FFu;
-          mn = min(mn, e & 0xFFFFu);
+          mn = min(mn, e);
           if (L1 == 0u) {
             const uint32_t e1 = t[(win << L0) >> (32 - kMaxCodeLen)];
             L1 = (e1 >> 11) & 15u;
