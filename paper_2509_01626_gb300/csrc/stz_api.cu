@@ -56,14 +56,28 @@ void make_geo(const int64_t n[3], int ndim, int dtype, int L, const int b[3], Ge
 // header) are written by a one-block kernel into mapped pinned host memory:
 // no copy engine is involved, so these reads never queue behind large
 // host<->device copies the caller has in flight on other streams.
+// Bytes [0, n) from src to dst by the block: in 16-byte pieces where both are
+// 16-byte aligned (each piece one write to the mapped host buffer, not 16),
+// the tail byte by byte.
+__device__ __forceinline__ void block_copy(const uint8_t* __restrict__ src,
+                                           uint8_t* __restrict__ dst, int n) {
+  int done = 0;
+  if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
+    const int n16 = n >> 4;
+    for (int i = threadIdx.x; i < n16; i += blockDim.x)
+      ((uint4*)dst)[i] = ((const uint4*)src)[i];
+    done = n16 << 4;
+  }
+  for (int i = done + threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
 __global__ void k_readback(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+  block_copy(src, dst, n);
 }
 // the same for two pieces at once
 __global__ void k_readback2(const uint8_t* __restrict__ s0, uint8_t* __restrict__ d0, int n0,
                             const uint8_t* __restrict__ s1, uint8_t* __restrict__ d1, int n1) {
-  for (int i = threadIdx.x; i < n0; i += blockDim.x) d0[i] = s0[i];
-  for (int i = threadIdx.x; i < n1; i += blockDim.x) d1[i] = s1[i];
+  block_copy(s0, d0, n0);
+  block_copy(s1, d1, n1);
 }
 
 // Zero fill of device words by a kernel (not cudaMemsetAsync, which may be

@@ -100,9 +100,28 @@ __device__ void bitonic_sort_u64(unsigned long long* k, int n /* power of 2 */) 
   }
 }
 
+// First index in [lo, hi) whose value v(index) exceeds m, values
+// non-decreasing; hi if none.  The whole warp searches: 32 probes a step.
+template <typename V>
+__device__ __forceinline__ int warp_upper(V v, int lo, int hi, uint32_t m, int lane) {
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) >> 5;
+    const int p = min(lo + (lane + 1) * step - 1, hi - 1);  // lane 31 probes hi - 1
+    const unsigned b = __ballot_sync(0xffffffffu, v(p) > m);
+    if (!b) return hi;
+    const int f = __ffs(b) - 1;
+    const int pf = min(lo + (f + 1) * step - 1, hi - 1);
+    lo = f == 0 ? lo : min(lo + f * step - 1, hi - 1) + 1;
+    hi = pf + 1;  // v(pf) > m: the answer is at most pf
+  }
+  const int p = lo + lane;
+  const unsigned b = __ballot_sync(0xffffffffu, p < hi && v(p) > m);
+  return b ? lo + __ffs(b) - 1 : hi;
+}
+
 __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __restrict__ hist,
                                                            uint16_t* __restrict__ enc,
-                                                           BookDev* __restrict__ books) {
+                                                           BookDev* __restrict__ books, int s0) {
   __shared__ unsigned long long key[kAlphabet];
   __shared__ uint32_t iw[kAlphabet];
   __shared__ uint16_t par_leaf[kAlphabet];
@@ -113,8 +132,9 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
   __shared__ uint32_t first_code[32];
   __shared__ int first_index[32];
   __shared__ int wcnt[2 * kBookThreads / 32][kMaxCodeLen + 1];  // per warp-group, per length
+  __shared__ uint16_t merged[kAlphabet];  // a merge round's picks: leaf, or 0x8000 | node
   __shared__ int s_n;
-  const int s = blockIdx.x;
+  const int s = s0 + blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint32_t* h = hist + (int64_t)s * kAlphabet;
   if (tid == 0) s_n = 0;
@@ -155,48 +175,83 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
     }
     return;
   }
-  // two-queue merge (sequential, one thread).  The heads of both queues are
-  // kept in registers three deep (the next weights are loaded two picks
-  // before they can be needed), so the loop carries no shared-memory latency.
-  if (tid == 0) {
-    // weights fit in 32 bits: a stream has fewer than 2^31 symbols
-    int i = 0, j = 0;
-    uint32_t lw = (uint32_t)(key[0] >> 11);
-    uint32_t lw1 = nl > 1 ? (uint32_t)(key[1] >> 11) : 0u;
-    uint32_t lw2 = nl > 2 ? (uint32_t)(key[2] >> 11) : 0u;
-    // internal nodes j, j+1, j+2 (those created so far; the rest are set
-    // when created)
-    uint32_t jw = 0, jw1 = 0, jw2 = 0;
-    for (int k = 0; k < nl - 1; k++) {
-      uint32_t wsum = 0;
+  // The two-queue merge: leaves in (frequency, symbol) order, internal nodes
+  // in creation order, always the two lightest heads, a leaf before an
+  // internal node of equal weight.  Its picks are the merge of the two
+  // sorted queues, so one warp takes them in rounds: with m the weight of the
+  // next node (the two lightest heads), every queued node of weight <= m is
+  // picked before any node created from here on (those weigh >= m and are
+  // newer), so the t nodes of weight <= m pair up in merge order into
+  // floor(t / 2) new nodes at once; an odd one waits for the next round.
+  // A stream's rounds are about the log of its weight (20-24 measured),
+  // instead of one dependent step per node.
+  if (w == 0) {
+    auto lwt = [&](int x) -> uint32_t { return (uint32_t)(key[x] >> 11); };
+    auto iwt = [&](int x) -> uint32_t { return iw[x]; };
+    int i = 0, j = 0, k = 0;
+    while (k < nl - 1) {
+      uint32_t m = 0;
+      {
+        int ii = i, jj = j;
 #pragma unroll
-      for (int pick = 0; pick < 2; pick++) {
-        const bool take_leaf = i < nl && (j >= k || lw <= jw);
-        if (take_leaf) {
-          wsum += lw;
-          par_leaf[i] = (uint16_t)k;
-          i++;
-          lw = lw1;
-          lw1 = lw2;
-          lw2 = i + 2 < nl ? (uint32_t)(key[i + 2] >> 11) : 0u;
-          if (i >= nl) lw = 0u;
-        } else {
-          wsum += jw;
-          par_int[j] = (uint16_t)k;
-          j++;
-          jw = jw1;
-          jw1 = jw2;
-          jw2 = j + 2 < k ? iw[j + 2] : 0u;
+        for (int p = 0; p < 2; p++) {
+          const uint32_t lv = ii < nl ? lwt(ii) : 0u, iv = jj < k ? iw[jj] : 0u;
+          const bool leaf = ii < nl && (jj >= k || lv <= iv);
+          m += leaf ? lv : iv;
+          ii += leaf ? 1 : 0;
+          jj += leaf ? 0 : 1;
         }
       }
-      iw[k] = wsum;
-      if (j == k) {
-        jw = wsum;  // the queue was empty: its head is the new node
-      } else if (j + 1 == k) {
-        jw1 = wsum;
-      } else if (j + 2 == k) {
-        jw2 = wsum;
+      const int tL = warp_upper(lwt, i, nl, m, lane) - i;
+      const int tI = warp_upper(iwt, j, k, m, lane) - j;
+      const int t = tL + tI, P = t >> 1;
+      // each of the t nodes' place in merge order: its index in its queue
+      // plus the nodes of the other queue that go before it
+      for (int r = lane; r < t; r += 32) {
+        if (r < tL) {
+          const uint32_t wv = lwt(i + r);
+          int lo = j, hi = j + tI;  // internal nodes lighter than the leaf
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (iw[mid] < wv) lo = mid + 1;
+            else hi = mid;
+          }
+          merged[r + lo - j] = (uint16_t)(i + r);
+        } else {
+          const int q = r - tL;
+          const uint32_t wv = iw[j + q];
+          int lo = i, hi = i + tL;  // leaves not heavier than the node
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (lwt(mid) <= wv) lo = mid + 1;
+            else hi = mid;
+          }
+          merged[q + lo - i] = (uint16_t)(0x8000 | (j + q));
+        }
       }
+      __syncwarp();
+      int cl = 0;  // leaves among the picked
+      for (int q = lane; q < P; q += 32) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int e = merged[2 * q + h];
+          if (e & 0x8000) {
+            sum += iw[e & 0x7FFF];
+            par_int[e & 0x7FFF] = (uint16_t)(k + q);
+          } else {
+            sum += lwt(e);
+            par_leaf[e] = (uint16_t)(k + q);
+            cl++;
+          }
+        }
+        iw[k + q] = sum;
+      }
+      cl = (int)__reduce_add_sync(0xffffffffu, (unsigned)cl);
+      __syncwarp();
+      i += cl;
+      j += 2 * P - cl;
+      k += P;
     }
   }
   __syncthreads();
@@ -327,9 +382,12 @@ __global__ void __launch_bounds__(kBookThreads) k_codebook(const uint32_t* __res
 }
 
 int launch_codebook(const Geo& g, const uint32_t* hist, uint16_t* enc, BookDev* books,
-                    cudaStream_t s) {
+                    cudaStream_t s, int s0, int ns) {
+  if (ns < 0) ns = g.nstreams - s0;
+  if (s0 < 0 || s0 + ns > g.nstreams) return STZ_ERR_ARG;
+  if (ns == 0) return STZ_OK;
   ProfScope ps_("k_codebook", s);
-  k_codebook<<<g.nstreams, kBookThreads, 0, s>>>(hist, enc, books);
+  k_codebook<<<ns, kBookThreads, 0, s>>>(hist, enc, books, s0);
   return cuda_ok(cudaGetLastError());
 }
 

@@ -151,8 +151,9 @@ struct BookDev {
   uint16_t sym[kAlphabet];
   uint8_t len[kAlphabet];
 };
+// the codebooks of streams s0 .. s0 + ns - 1 (ns < 0: through the last)
 int launch_codebook(const Geo& g, const uint32_t* hist, uint16_t* enc, BookDev* books,
-                    cudaStream_t s);
+                    cudaStream_t s, int s0 = 0, int ns = -1);
 // payload words per chunk, and the bits of each 64-symbol lane run of a chunk
 // (32 u16 per chunk) for the packing pass
 int launch_chunk_words(const Geo& g, const uint16_t* codes, const uint16_t* enc,
