@@ -1147,6 +1147,39 @@ unsigned long long g_dg_tick = 0;
 }  // namespace
 
 extern "C++" {
+// This thread's side stream on the current device, with two events: a
+// decode runs its finer streams' chunk decoding there beside level 1's
+// passes.  Null when it cannot be created.
+namespace {
+struct Side {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+thread_local Side tl_side[64];
+}  // namespace
+
+static Side* side_stream() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  Side& sd = tl_side[dev];
+  if (!sd.s) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+      if (st) cudaStreamDestroy(st);
+      if (a) cudaEventDestroy(a);
+      cudaGetLastError();
+      return nullptr;
+    }
+    sd.s = st;
+    sd.fork = a;
+    sd.join = b;
+  }
+  return &sd;
+}
+
 template <typename F>
 static int decode_graph_run(const DecKey& key, F& launch_all, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_dg_mu);
@@ -1351,6 +1384,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
   const int ns_needed = 1 + 7 * (level - 1);
   int64_t nblocks = 0;
   double dec_bytes = 0.0;
+  double job_bytes[kMaxStreams] = {};
   for (int s = have_l1 ? 1 : 0; s < ns_needed; s++) {
     if (g.s[s].nsym == 0) continue;
     const SlotMap& sm = P.sm[s];
@@ -1367,8 +1401,9 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
     jb.nchunks_job = c;
     // the job's share of the stream's codes (written) and payload (read)
     if (H.d[s].nch > 0)
-      dec_bytes += (2.0 * (double)H.d[s].nsym + 4.0 * (double)H.d[s].pw) * (double)c /
-                   (double)H.d[s].nch;
+      job_bytes[tb.njobs - 1] = (2.0 * (double)H.d[s].nsym + 4.0 * (double)H.d[s].pw) *
+                                (double)c / (double)H.d[s].nch;
+    dec_bytes += job_bytes[tb.njobs - 1];
     jb.block0 = nblocks;
     nblocks += cdiv(c * H.nsub, kDecThreads);
   }
@@ -1387,7 +1422,43 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
       STZ_TRY(launch_lut(tb, lut, (uint32_t*)dp, (int)(sizeof(DevParams) / 4), st));
     else
       STZ_TRY(zero_words(dp, (int64_t)(sizeof(DevParams) / 4), st));
-    STZ_TRY(launch_decode_chunks(g, tb, lut, codes, sub_olo, status, dec_bytes, st));
+    // Level 1's passes are a latency chain on a few SMs.  When the finer
+    // streams' chunks make at least a full wave of the decoder, level 1's
+    // chunks are decoded first and the finer ones on the side stream beside
+    // level 1's passes, on a grid that leaves two SMs to them; the levels
+    // above wait for both.
+    Side* sd = nullptr;
+    DecTables tb1, tbf;
+    double b1 = 0.0, bf = 0.0;
+    const int sms = launch_sms();
+    if (!have_l1 && level >= 2) {
+      tb1 = tb;
+      tbf = tb;
+      tb1.njobs = tbf.njobs = 0;
+      tb1.nblocks = tbf.nblocks = 0;
+      for (int q = 0; q < tb.njobs; q++) {
+        DecTables& t = tb.jobs[q].sid == 0 ? tb1 : tbf;
+        DecChunkJob jb = tb.jobs[q];
+        jb.block0 = t.nblocks;
+        t.nblocks += cdiv(jb.nchunks_job * H.nsub, kDecThreads);
+        t.jobs[t.njobs++] = jb;
+        (tb.jobs[q].sid == 0 ? b1 : bf) += job_bytes[q];
+      }
+      // (not for the no-allocation entry, which creates no stream)
+      if (tb1.njobs > 0 && tbf.nblocks >= (int64_t)sms * decode_blocks_per_sm() && sms > 4 &&
+          !o.no_alloc)
+        sd = side_stream();
+    }
+    if (sd) {
+      STZ_TRY(cuda_ok(cudaEventRecord(sd->fork, st)));
+      STZ_TRY(launch_decode_chunks(g, tb1, lut, codes, sub_olo, status, b1, st));
+      STZ_TRY(cuda_ok(cudaStreamWaitEvent(sd->s, sd->fork, 0)));
+      STZ_TRY(launch_decode_chunks(g, tbf, lut, codes, sub_olo, status, bf, sd->s,
+                                   (int64_t)(sms - 2) * decode_blocks_per_sm()));
+      STZ_TRY(cuda_ok(cudaEventRecord(sd->join, sd->s)));
+    } else {
+      STZ_TRY(launch_decode_chunks(g, tb, lut, codes, sub_olo, status, dec_bytes, st));
+    }
     const uint8_t* sec0 = comp + H.d[0].sect_off;
     SectHost sh0 = sect_host(H.d[0].nlive, H.d[0].nch, H.d[0].pw, H.d[0].nout, ps, H.nsub);
     uint8_t* g1buf = have_l1 ? (uint8_t*)o.l1 : ws + P.grid[1];
@@ -1435,6 +1506,7 @@ static int decode_core(const void* comp_dev, size_t comp_bytes, const int64_t* l
                                                    m1[2]);
       STZ_TRY(cuda_ok(cudaGetLastError()));
     }
+    if (sd) STZ_TRY(cuda_ok(cudaStreamWaitEvent(st, sd->join, 0)));
     for (int j = 2; j <= level; j++) {
       LevelArgs a;
       memset(&a, 0, sizeof(a));

@@ -1210,13 +1210,18 @@ __global__ void __launch_bounds__(kDecThreads, kDecBlocks) k_decode_chunks(
     const __grid_constant__ Geo g, const __grid_constant__ DecTables tb,
     const uint32_t* __restrict__ lut, uint16_t* __restrict__ codes,
     uint32_t* __restrict__ sub_olo, uint32_t* __restrict__ status) {
-  int jb = 0;
-  for (int k = 1; k < tb.njobs; k++)
-    if (tb.jobs[k].block0 <= (int64_t)blockIdx.x) jb = k;
-  const DecChunkJob& job = tb.jobs[jb];
-  const int sid = job.sid;
-  decode_block(job, tb.ds[sid], g.s[sid], g.b, g.bvol, lut + (int64_t)sid * kLutSize, codes,
-               sub_olo, status, (int64_t)blockIdx.x - job.block0);
+  // virtual blocks of 32 chunks, the grid striding over them (a grid smaller
+  // than the work leaves SMs to kernels running beside it)
+  for (int64_t vb = blockIdx.x; vb < tb.nblocks; vb += gridDim.x) {
+    if (vb != (int64_t)blockIdx.x) __syncthreads();  // the shared stage and table are reused
+    int jb = 0;
+    for (int k = 1; k < tb.njobs; k++)
+      if (tb.jobs[k].block0 <= vb) jb = k;
+    const DecChunkJob& job = tb.jobs[jb];
+    const int sid = job.sid;
+    decode_block(job, tb.ds[sid], g.s[sid], g.b, g.bvol, lut + (int64_t)sid * kLutSize, codes,
+                 sub_olo, status, vb - job.block0);
+  }
 }
 
 // The chunk jobs of many region decodes in one launch (the batched served
@@ -1246,15 +1251,18 @@ int launch_decode_chunks_multi(const DecJobMulti* jobs_dev, int njobs, int64_t n
 
 int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,
                          uint16_t* codes, uint32_t* sub_olo, uint32_t* status, double bytes,
-                         cudaStream_t s) {
+                         cudaStream_t s, int64_t max_grid) {
   if (tb.nblocks == 0) return STZ_OK;
   static_assert(kDecThreads == 256, "block_scan_256 assumes 256 threads");
   if (allow_smem((const void*)k_decode_chunks, kDecSmem) != STZ_OK)
     return STZ_ERR_CUDA;
+  const int64_t grid = max_grid > 0 ? imin(tb.nblocks, max_grid) : tb.nblocks;
   ProfScope ps_("k_decode_chunks", s, bytes);
-  k_decode_chunks<<<(unsigned)tb.nblocks, kDecThreads, kDecSmem, s>>>(g, tb, lut, codes, sub_olo,
-                                                                      status);
+  k_decode_chunks<<<(unsigned)grid, kDecThreads, kDecSmem, s>>>(g, tb, lut, codes, sub_olo,
+                                                                status);
   return cuda_ok(cudaGetLastError());
 }
+
+int decode_blocks_per_sm() { return kDecBlocks; }
 
 }  // namespace stz

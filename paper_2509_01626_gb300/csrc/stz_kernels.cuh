@@ -203,9 +203,12 @@ int launch_lut(const DecTables& tb, uint32_t* lut, uint32_t* clear, int nclear,
 // For streams with outliers, sub_olo[slot * (kNSub + 1) + u] receives where
 // sub-chunk u of each decoded chunk starts in the stream's outlier list
 // (u = nsub: where the chunk ends).
+// max_grid > 0: at most that many thread blocks, striding over the work
 int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,
                          uint16_t* codes, uint32_t* sub_olo, uint32_t* status, double bytes,
-                         cudaStream_t s);
+                         cudaStream_t s, int64_t max_grid = 0);
+// blocks of the chunk decoder resident per SM
+int decode_blocks_per_sm();
 
 // Chunk jobs of many decodes in one launch (the batched served form); jobs
 // in device memory, ascending block0, each with its own table and outputs.

@@ -864,8 +864,7 @@ struct ShellGeo {
 // is the coarse value at cell + (dz, dy, dx), d in -1..2, clamped into the
 // coarse box (a clamped tap is never one a chosen rule uses).  cub[a]: the
 // cubic stencil fits along axis a at the odd point; rule[a]: the one-axis
-// rule there otherwise.  Unused slots of the low-order rules are computed and
-// discarded, so every used value has the operation order of level_predict.
+// rule there otherwise; every value has the operation order of level_predict.
 template <typename T>
 struct ShellTaps {
   const T* __restrict__ cb;  // coarse value of the cell
@@ -875,17 +874,29 @@ struct ShellTaps {
   }
 };
 
-template <typename T>
-__device__ __forceinline__ T rule_sel(int r, T w0, T w1, T w2) {
-  const T mid = op_mul(op_add(w0, w1), T(0.5));
-  const T ext = op_add(w0, op_mul(op_sub(w0, w2), T(0.5)));
+// One one-axis rule r over the slots w(q) of its axis (q = 0: the -1 point,
+// 1: the +1 point, 2: the -3 point): the midpoint, the extrapolation or the
+// copy; only the slots the rule uses are read.
+// LAZY (decoding, where the kernel waits on these loads): branch on the
+// rule and read only its slots; otherwise (compressing, bound by issue) read
+// all three and select, without branches.
+template <typename T, bool LAZY, typename W>
+__device__ __forceinline__ T rule_apply(int r, const W& w) {
+  const T w0 = w(0);
+  if (LAZY) {
+    if (r == kMid) return op_mul(op_add(w0, w(1)), T(0.5));
+    if (r == kExt) return op_add(w0, op_mul(op_sub(w0, w(2)), T(0.5)));
+    return w0;
+  }
+  const T mid = op_mul(op_add(w0, w(1)), T(0.5));
+  const T ext = op_add(w0, op_mul(op_sub(w0, w(2)), T(0.5)));
   return r == kMid ? mid : (r == kExt ? ext : w0);
 }
 
 // coarse offset of slot q of a one-axis rule: 0 -> 0, 1 -> +1, 2 -> -1
 __device__ __forceinline__ constexpr int sd(int q) { return q == 0 ? 0 : (q == 1 ? 1 : -1); }
 
-template <int K, typename T>
+template <int K, typename T, bool LAZY>
 __device__ __forceinline__ T shell_predict(const ShellTaps<T>& t, const bool cub[3],
                                            const int rule[3]) {
   constexpr int oz = (K >> 2) & 1, oy = (K >> 1) & 1, ox = K & 1;
@@ -918,26 +929,19 @@ __device__ __forceinline__ T shell_predict(const ShellTaps<T>& t, const bool cub
     return op_add(op_mul(si, T(0.125)), op_mul(op_sub(si, so), T(0.015625)));
   }
   const int r0 = rule[a0], r1 = rule[a1], r2 = rule[2];
+  // the separable rules, innermost along a0: each rule reads only its slots
   if constexpr (nodd == 1) {
-    return rule_sel(r0, at(sd(0), 0, 0), at(sd(1), 0, 0), at(sd(2), 0, 0));
+    return rule_apply<T, LAZY>(r0, [&](int q0) { return at(sd(q0), 0, 0); });
   } else if constexpr (nodd == 2) {
-    T w1[3];
-#pragma unroll
-    for (int q1 = 0; q1 < 3; q1++)
-      w1[q1] = rule_sel(r0, at(sd(0), sd(q1), 0), at(sd(1), sd(q1), 0), at(sd(2), sd(q1), 0));
-    return rule_sel(r1, w1[0], w1[1], w1[2]);
+    return rule_apply<T, LAZY>(r1, [&](int q1) {
+      return rule_apply<T, LAZY>(r0, [&](int q0) { return at(sd(q0), sd(q1), 0); });
+    });
   } else {
-    T w2[3];
-#pragma unroll
-    for (int q2 = 0; q2 < 3; q2++) {
-      T w1[3];
-#pragma unroll
-      for (int q1 = 0; q1 < 3; q1++)
-        w1[q1] = rule_sel(r0, at(sd(0), sd(q1), sd(q2)), at(sd(1), sd(q1), sd(q2)),
-                          at(sd(2), sd(q1), sd(q2)));
-      w2[q2] = rule_sel(r1, w1[0], w1[1], w1[2]);
-    }
-    return rule_sel(r2, w2[0], w2[1], w2[2]);
+    return rule_apply<T, LAZY>(r2, [&](int q2) {
+      return rule_apply<T, LAZY>(r1, [&](int q1) {
+        return rule_apply<T, LAZY>(r0, [&](int q0) { return at(sd(q0), sd(q1), sd(q2)); });
+      });
+    });
   }
 }
 
@@ -963,22 +967,28 @@ __device__ __forceinline__ void shell_cell(const LevelArgs& a, const ShellGeo& s
   const int64_t fst[3] = {fe1 * fe2, fe2, 1};                        // fine box strides
   int c[3] = {0, 0, 0};
   if (cv) {
-    const int64_t nx = sh.hi[2] - sh.lo[2], ny = sh.hi[1] - sh.lo[1];
-    if (i < sh.nA) {
-      const int64_t r = i / (ny * nx);
-      c[0] = (int)sh.bv[0][r];
-      c[1] = (int)(sh.lo[1] + (i / nx) % ny);
-      c[2] = (int)(sh.lo[2] + i % nx);
-    } else if (i < sh.nA + sh.nB) {
-      const int64_t k = i - sh.nA, nbyx = sh.nb[1] * nx;
-      c[0] = (int)(sh.ilo[0] + k / nbyx);
-      c[1] = (int)sh.bv[1][(k / nx) % sh.nb[1]];
-      c[2] = (int)(sh.lo[2] + k % nx);
+    // 32-bit index arithmetic: a shell has fewer than 2^31 cells (checked at
+    // launch), and 32-bit divisions cost a fraction of 64-bit ones
+    const uint32_t nx = (uint32_t)(sh.hi[2] - sh.lo[2]), ny = (uint32_t)(sh.hi[1] - sh.lo[1]);
+    const uint32_t nA = (uint32_t)sh.nA, nB = (uint32_t)sh.nB, ii = (uint32_t)i;
+    if (ii < nA) {
+      const uint32_t r = ii / nx, p = r / ny;
+      c[0] = (int)sh.bv[0][p];
+      c[1] = (int)sh.lo[1] + (int)(r - p * ny);
+      c[2] = (int)sh.lo[2] + (int)(ii - r * nx);
+    } else if (ii < nA + nB) {
+      const uint32_t k = ii - nA, nb1 = (uint32_t)sh.nb[1];
+      const uint32_t r = k / nx, p = r / nb1;
+      c[0] = (int)sh.ilo[0] + (int)p;
+      c[1] = (int)sh.bv[1][r - p * nb1];
+      c[2] = (int)sh.lo[2] + (int)(k - r * nx);
     } else {
-      const int64_t k = i - sh.nA - sh.nB, iyn = sh.ihi[1] - sh.ilo[1];
-      c[0] = (int)(sh.ilo[0] + k / (iyn * sh.nb[2]));
-      c[1] = (int)(sh.ilo[1] + (k / sh.nb[2]) % iyn);
-      c[2] = (int)sh.bv[2][k % sh.nb[2]];
+      const uint32_t k = ii - nA - nB, iyn = (uint32_t)(sh.ihi[1] - sh.ilo[1]);
+      const uint32_t nb2 = (uint32_t)sh.nb[2];
+      const uint32_t r = k / nb2, p = r / iyn;
+      c[0] = (int)sh.ilo[0] + (int)p;
+      c[1] = (int)sh.ilo[1] + (int)(r - p * iyn);
+      c[2] = (int)sh.bv[2][k - r * nb2];
     }
   }
   // per axis: the odd point's existence, stencil and rule; clamped taps
@@ -1005,9 +1015,11 @@ __device__ __forceinline__ void shell_cell(const LevelArgs& a, const ShellGeo& s
   for (int ax = 0; ax < 3; ax++) ev_box = ev_box && g0[ax] >= a.flo[ax] && g0[ax] < a.fhi[ax];
   const int64_t fidx0 = ((g0[0] - a.flo[0]) * fe1 + (g0[1] - a.flo[1])) * fe2 + (g0[2] - a.flo[2]);
   if (cv && a.fine && ev_box) ((T*)a.fine)[fidx0] = tp(0, 0, 0);
-  // the cell's brick and place in it (the same for the 7 sub-blocks)
-  const int Bc[3] = {c[0] / geo.b[0], c[1] / geo.b[1], c[2] / geo.b[2]};
-  const int rc[3] = {c[0] - Bc[0] * geo.b[0], c[1] - Bc[1] * geo.b[1], c[2] - Bc[2] * geo.b[2]};
+  // the cell's brick and place in it (the same for the 7 sub-blocks); the
+  // shell runs only beside the interior kernel, with its brick
+  constexpr int kB[3] = {kFBZ, kFBY, kFBX};
+  const int Bc[3] = {c[0] / kB[0], c[1] / kB[1], c[2] / kB[2]};
+  const int rc[3] = {c[0] - Bc[0] * kB[0], c[1] - Bc[1] * kB[1], c[2] - Bc[2] * kB[2]};
   const int64_t xbase = DEC ? 0 : g0[0] * xst[0] + g0[1] * xst[1] + g0[2] * xst[2];
 #pragma unroll
   for (int K = 1; K <= 7; K++) {
@@ -1026,23 +1038,23 @@ __device__ __forceinline__ void shell_cell(const LevelArgs& a, const ShellGeo& s
     if (v) {
       const StreamGeo& sg = geo.s[sid];
       const SlotMap& sm = a.sm[K];
-      const int l0 = min(geo.b[0], (int)sg.e[0] - Bc[0] * geo.b[0]);
-      const int l1 = min(geo.b[1], (int)sg.e[1] - Bc[1] * geo.b[1]);
-      const int l2 = min(geo.b[2], (int)sg.e[2] - Bc[2] * geo.b[2]);
+      const int l0 = min(kB[0], (int)sg.e[0] - Bc[0] * kB[0]);
+      const int l1 = min(kB[1], (int)sg.e[1] - Bc[1] * kB[1]);
+      const int l2 = min(kB[2], (int)sg.e[2] - Bc[2] * kB[2]);
       const int local = (rc[0] * l1 + rc[1]) * l2 + rc[2];
       const int64_t ord = ((Bc[0] - sm.lo[0]) * sm.cnt[1] + (Bc[1] - sm.lo[1])) * sm.cnt[2] +
                           (Bc[2] - sm.lo[2]);
-      const int64_t slot = (sm.base + ord) * geo.bvol + local;
+      const int64_t slot = (sm.base + ord) * (int64_t)kTileSlot + local;
       const int64_t fidx = fidx0 + o[0] * fst[0] + o[1] * fst[1] + o[2] * fst[2];
       T pred;
       switch (K) {
-        case 1: pred = shell_predict<1>(tp, cub, rule); break;
-        case 2: pred = shell_predict<2>(tp, cub, rule); break;
-        case 3: pred = shell_predict<3>(tp, cub, rule); break;
-        case 4: pred = shell_predict<4>(tp, cub, rule); break;
-        case 5: pred = shell_predict<5>(tp, cub, rule); break;
-        case 6: pred = shell_predict<6>(tp, cub, rule); break;
-        default: pred = shell_predict<7>(tp, cub, rule); break;
+        case 1: pred = shell_predict<1, T, DEC>(tp, cub, rule); break;
+        case 2: pred = shell_predict<2, T, DEC>(tp, cub, rule); break;
+        case 3: pred = shell_predict<3, T, DEC>(tp, cub, rule); break;
+        case 4: pred = shell_predict<4, T, DEC>(tp, cub, rule); break;
+        case 5: pred = shell_predict<5, T, DEC>(tp, cub, rule); break;
+        case 6: pred = shell_predict<6, T, DEC>(tp, cub, rule); break;
+        default: pred = shell_predict<7, T, DEC>(tp, cub, rule); break;
       }
       if (!DEC) {
         const T x = __ldg((const T*)a.field + xbase + o[0] * xst[0] + o[1] * xst[1] +
@@ -1059,9 +1071,9 @@ __device__ __forceinline__ void shell_cell(const LevelArgs& a, const ShellGeo& s
         const int sy = a.codes[slot];
         T val = dequantize(sy, pred, two_eb, kRadius);
         if (sy == 0) {
-          const int64_t pos = (int64_t)Bc[0] * geo.b[0] * sg.e[1] * sg.e[2] +
-                              (int64_t)Bc[1] * geo.b[1] * l0 * sg.e[2] +
-                              (int64_t)Bc[2] * geo.b[2] * l0 * l1 + local;
+          const int64_t pos = (int64_t)Bc[0] * kB[0] * sg.e[1] * sg.e[2] +
+                              (int64_t)Bc[1] * kB[1] * l0 * sg.e[2] +
+                              (int64_t)Bc[2] * kB[2] * l0 * l1 + local;
           if (!outlier_value(a.sub_olo, a.dense[K] != 0, sm.base + ord, local, l0 * l1 * l2,
                              a.nsub, a.opos[K], (const T*)a.oval[K], a.nout[K], pos, val)) {
             val = T(0);
@@ -1343,6 +1355,11 @@ static int64_t shell_geo(const LevelArgs& a, const int64_t M[3], ShellGeo* sh) {
   return cells;
 }
 
+// shell_cell's index arithmetic is 32-bit
+static bool shell_fits(const ShellGeo& sh) {
+  return sh.nA + sh.nB + sh.nC < ((int64_t)1 << 31);
+}
+
 template <typename T, bool DEC>
 static int run_level_shell(const LevelArgs& a, const ShellGeo& sh, double bytes, cudaStream_t s) {
   const int64_t total = sh.nA + sh.nB + sh.nC;
@@ -1385,6 +1402,7 @@ static int run_level(const LevelArgs& a, cudaStream_t s) {
                     2 * kFBZ * fe < ((int64_t)1 << 31);
   ShellGeo sh;
   const int64_t cells = shell_geo(a, M, &sh);
+  if (!shell_fits(sh)) return STZ_ERR_ARG;
   const double bpc = cell_bytes<T, DEC>(a);
   if (!fast) return run_level_generic<T, DEC>(a, (double)cells * bpc, s);
   const int64_t nshell = sh.nA + sh.nB + sh.nC;
@@ -1427,6 +1445,7 @@ static int run_level_multi(const LevelArgs* h, int n, uint8_t* arena, cudaStream
     int64_t M[3];
     grid_extent(a.geo.n, a.geo.L, a.level - 1, M);
     const int64_t cells = shell_geo(a, M, &shs[r]);
+    if (!shell_fits(shs[r])) return STZ_ERR_ARG;
     const int64_t nshell = shs[r].nA + shs[r].nB + shs[r].nC;
     // interior cells exist only with M >= 4 on every axis
     const bool interior = M[0] >= 4 && M[1] >= 4 && M[2] >= 4 && cells > 0;
@@ -1724,6 +1743,7 @@ static int plan_queue(const LevelArgs* h, int n, int schedule, int gran, int blo
     int64_t M[3];
     grid_extent(a.geo.n, a.geo.L, a.level - 1, M);
     const int64_t cells = shell_geo(a, M, &shs[r]);
+    if (!shell_fits(shs[r])) return STZ_ERR_ARG;
     const int64_t nshell = shs[r].nA + shs[r].nB + shs[r].nC;
     const bool interior = M[0] >= 4 && M[1] >= 4 && M[2] >= 4 && cells > 0;
     QueueGroup& G = grp[r];
