@@ -975,7 +975,7 @@ def main():
         "compression_ratio": round(fb / r["comp_bytes"], 3),
         "roi": r["roi"],
         "roofline": roofline, "cpu_baseline": cpu, "e2e": r["e2e"],
-        "gpu_launches": int(r["launches"]), "clocks": r["clk"], "kernels": breakdown[:12],
+        "gpu_launches": int(r["launches"]), "clocks": r["clk"], "kernels": breakdown[:24],
         "bounds": bounds, "large": large, "ablation": ablation,
         "batched": batched, "served": served,
     }
