@@ -192,9 +192,13 @@ def traffic_ratio(kernel):
     return float(e["dram_bytes"]) / float(e["algo_bytes"])
 
 
-# sources whose hash keys a recorded traffic ratio (any change voids it)
+# sources whose hash keys a recorded traffic ratio (any change voids it), by
+# kernel name prefix
 TRAFFIC_SOURCES = {
     "k_decode_chunks": ["paper_2509_01626_gb300/csrc/stz_huffman.cu"],
+    "k_chunk_words": ["paper_2509_01626_gb300/csrc/stz_huffman.cu"],
+    "k_pack": ["paper_2509_01626_gb300/csrc/stz_huffman.cu"],
+    "k_range": ["paper_2509_01626_gb300/csrc/stz_range.cu"],
     "k_level": ["paper_2509_01626_gb300/csrc/stz_level.cu",
                 "paper_2509_01626_gb300/csrc/stz_predict.cuh"],
 }
@@ -228,7 +232,7 @@ def write_traffic(kernel, ncu_csv, bench_json, capture):
     algo = k["achieved_gbs"] * 1e9 * k["ms_per_step"] * 1e-3  # bytes of one step
     if abs(k["launches_per_step"] - n) > 1e-6:
         raise SystemExit(f"captured {n} launches, the step has {k['launches_per_step']}")
-    key = "k_decode_chunks" if kernel.startswith("k_decode") else "k_level"
+    key = [k for k in TRAFFIC_SOURCES if kernel.startswith(k)][0]
     srcs = TRAFFIC_SOURCES[key] + COMMON_SOURCES
     h = hashlib.sha256()
     for src in srcs:
