@@ -1010,10 +1010,18 @@ constexpr int kDecBlocks = STZ_DEC_BLOCKS;
 constexpr int kStageWords = kDecBlocks >= 6 ? 4320 : 6144;
 constexpr int kMaxChunkWords = (4096 * kMaxCodeLen + 31) / 32;  // bricks hold <= 4096 cells
 static_assert(kMaxChunkWords + 2 <= kStageWords, "a chunk must fit the stage");
-constexpr size_t kDecSmem = sizeof(uint32_t) * kStageWords + sizeof(uint32_t) * kLutSize +
-                            sizeof(uint32_t) * kDecThreads +
-                            sizeof(uint32_t) * (kDecThreads + 1) + sizeof(uint32_t) * kDecThreads +
-                            sizeof(int) * kDecThreads;
+// A launch of at most one block per SM (a level-1 stream, a small region)
+// has the SM's shared memory to itself: its blocks stage 64 KiB of payload,
+// so that a level-1 block's 32 chunks (about 3.6 bits per symbol) arrive in
+// one round instead of two, halving the serial decode chains that round
+// after round would otherwise run one after the other.
+constexpr int kBigStageWords = 16384;
+__host__ __device__ constexpr size_t dec_smem(int stage_words) {
+  return sizeof(uint32_t) * stage_words + sizeof(uint32_t) * kLutSize +
+         sizeof(uint32_t) * kDecThreads + sizeof(uint32_t) * (kDecThreads + 1) +
+         sizeof(uint32_t) * kDecThreads + sizeof(int) * kDecThreads;
+}
+constexpr size_t kDecSmem = dec_smem(kStageWords);
 static_assert((sizeof(uint32_t) * kStageWords) % 16 == 0 &&
                   (sizeof(uint32_t) * kStageWords + sizeof(uint32_t) * kLutSize) % 16 == 0,
               "shared arrays of the chunk decoder must stay aligned");
@@ -1037,11 +1045,12 @@ __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecSt
                                              int64_t bvol, const uint32_t* __restrict__ lutg,
                                              uint16_t* __restrict__ codes,
                                              uint32_t* __restrict__ sub_olo,
-                                             uint32_t* __restrict__ status, int64_t bidx) {
+                                             uint32_t* __restrict__ status, int64_t bidx,
+                                             int stage_words) {
   extern __shared__ __align__(16) unsigned char dsm[];
   // arrays in order of alignment: the 16-byte-loaded table first, then 4-byte
   uint32_t* stage = (uint32_t*)dsm;
-  uint32_t* t = stage + kStageWords;
+  uint32_t* t = stage + stage_words;
   uint32_t* cw0 = (uint32_t*)(t + kLutSize);     // chunk's first word in the stream payload
   uint32_t* S = cw0 + kDecThreads;               // padded-size prefix sums
   uint32_t* cjl = S + kDecThreads + 1;                            // chunk index in stream
@@ -1087,7 +1096,7 @@ __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecSt
   while (a < nch) {
     __syncthreads();
     const uint32_t base = S[a];
-    const int b = a + __syncthreads_count(tid >= a && tid < nch && S[tid + 1] - base <= kStageWords);
+    const int b = a + __syncthreads_count(tid >= a && tid < nch && S[tid + 1] - base <= (uint32_t)stage_words);
     {
       // copy chunks [a, b): one warp per chunk, lanes over its words, every
       // copy asynchronous (none waits for the one before), then one wait
@@ -1209,7 +1218,7 @@ __device__ __forceinline__ void decode_block(const DecChunkJob& job, const DecSt
 __global__ void __launch_bounds__(kDecThreads, kDecBlocks) k_decode_chunks(
     const __grid_constant__ Geo g, const __grid_constant__ DecTables tb,
     const uint32_t* __restrict__ lut, uint16_t* __restrict__ codes,
-    uint32_t* __restrict__ sub_olo, uint32_t* __restrict__ status) {
+    uint32_t* __restrict__ sub_olo, uint32_t* __restrict__ status, int stage_words) {
   // virtual blocks of 32 chunks, the grid striding over them (a grid smaller
   // than the work leaves SMs to kernels running beside it)
   for (int64_t vb = blockIdx.x; vb < tb.nblocks; vb += gridDim.x) {
@@ -1220,7 +1229,7 @@ __global__ void __launch_bounds__(kDecThreads, kDecBlocks) k_decode_chunks(
     const DecChunkJob& job = tb.jobs[jb];
     const int sid = job.sid;
     decode_block(job, tb.ds[sid], g.s[sid], g.b, g.bvol, lut + (int64_t)sid * kLutSize, codes,
-                 sub_olo, status, vb - job.block0);
+                 sub_olo, status, vb - job.block0, stage_words);
   }
 }
 
@@ -1236,7 +1245,7 @@ __global__ void __launch_bounds__(kDecThreads, kDecBlocks) k_decode_chunks_multi
   }
   const DecJobMulti& m = jobs[lo];
   decode_block(m.job, m.ds, m.sg, m.b, m.bvol, m.lut, m.codes, m.sub_olo, m.status,
-               (int64_t)blockIdx.x - m.job.block0);
+               (int64_t)blockIdx.x - m.job.block0, kStageWords);
 }
 
 int launch_decode_chunks_multi(const DecJobMulti* jobs_dev, int njobs, int64_t nblocks,
@@ -1254,12 +1263,14 @@ int launch_decode_chunks(const Geo& g, const DecTables& tb, const uint32_t* lut,
                          cudaStream_t s, int64_t max_grid) {
   if (tb.nblocks == 0) return STZ_OK;
   static_assert(kDecThreads == 256, "block_scan_256 assumes 256 threads");
-  if (allow_smem((const void*)k_decode_chunks, kDecSmem) != STZ_OK)
-    return STZ_ERR_CUDA;
   const int64_t grid = max_grid > 0 ? imin(tb.nblocks, max_grid) : tb.nblocks;
+  // a launch of at most one block per SM takes the big stage
+  const int stage = grid <= (int64_t)launch_sms() ? kBigStageWords : kStageWords;
+  const size_t smem = dec_smem(stage);
+  if (allow_smem((const void*)k_decode_chunks, smem) != STZ_OK) return STZ_ERR_CUDA;
   ProfScope ps_("k_decode_chunks", s, bytes);
-  k_decode_chunks<<<(unsigned)grid, kDecThreads, kDecSmem, s>>>(g, tb, lut, codes, sub_olo,
-                                                                status);
+  k_decode_chunks<<<(unsigned)grid, kDecThreads, smem, s>>>(g, tb, lut, codes, sub_olo, status,
+                                                            stage);
   return cuda_ok(cudaGetLastError());
 }
 
