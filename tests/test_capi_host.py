@@ -173,3 +173,34 @@ def test_region_sizes_and_async_errors_need_no_gpu(stzmod):
     hi_bad = (ctypes.c_int64 * 3)(2, 2, 99)
     assert L.stz_decompress_region_async(dev, comp.size, hdr, len(hdr), None, lo, hi_bad, 3, dev,
                                          64, od, dev, 1 << 20, dev, None) == stzmod.ERR_ARG
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libstz.so every call raises: there is no CPU fallback."""
+    import torch
+
+    from paper_2509_01626_gb300 import stz
+
+    monkeypatch.setattr(stz, "_lib", None)
+    monkeypatch.setattr(stz, "LIB_PATH", str(tmp_path / "libstz.so"))
+    with pytest.raises(ImportError):
+        stz.lib()
+    # a host tensor is refused outright (there is no CPU path to fall back to)
+    with pytest.raises((ImportError, ValueError)):
+        stz.compress(torch.zeros(8, 8, 8), 1e-3)
+    with pytest.raises(ImportError):
+        stz.compress_bound((8, 8, 8), torch.float32)
+
+
+def test_product_code_never_reaches_the_oracle():
+    """The package (the product path) neither imports nor runs anything under
+    oracle/: only tests, the smoke check and the bench's CPU baseline may."""
+    pkg = os.path.join(ROOT, "paper_2509_01626_gb300")
+    pat = re.compile(r"^\s*(import|from)\s+oracle\b|stz_oracle|oracle[/\\]", re.M)
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not pat.search(src), os.path.join(dirpath, f)
