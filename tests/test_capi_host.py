@@ -204,3 +204,190 @@ def test_product_code_never_reaches_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not pat.search(src), os.path.join(dirpath, f)
+
+
+def _golden(name="sin3d_f32_22x19x27"):
+    return np.fromfile(os.path.join(GOLDEN, name + ".stz"), dtype=np.uint8)
+
+
+def _i64(*v):
+    return (ctypes.c_int64 * len(v))(*v)
+
+
+def test_sizes_for_other_level_counts(stzmod):
+    L = stzmod.lib()
+    d = _i64(64, 64, 64)
+    assert L.stz_compress_bound_ex(d, 3, 0, 0) == L.stz_compress_bound(d, 3, 0)
+    assert L.stz_workspace_size_ex(d, 3, 0, 0) == L.stz_workspace_size(d, 3, 0)
+    assert L.stz_compress_bound_ex(d, 3, 0, 3) == L.stz_compress_bound(d, 3, 0)
+    for lv in (1, 2, 4, 5, 6):
+        assert L.stz_compress_bound_ex(d, 3, 0, lv) > 64 ** 3 * 4
+        assert L.stz_workspace_size_ex(d, 3, 1, lv) > 0
+    for lv in (-1, 7):
+        assert L.stz_compress_bound_ex(d, 3, 0, lv) == 0
+        assert L.stz_workspace_size_ex(d, 3, 0, lv) == 0
+    assert L.stz_compress_bound_ex(d, 3, 2, 3) == 0  # no such dtype
+
+
+def test_compress_ex_rejects_bad_options_before_any_cuda_call(stzmod):
+    L = stzmod.lib()
+    d = _i64(8, 8, 8)
+    nb = ctypes.c_size_t(0)
+    vp = ctypes.c_void_p
+
+    def call(opts, field=vp(256), out_bytes=ctypes.byref(nb)):
+        o = ctypes.byref(opts) if opts is not None else None
+        return L.stz_compress_ex(field, d, 3, 0, 1, 1e-3, o, vp(256), 1 << 20, out_bytes,
+                                 vp(256), 1 << 30, None)
+
+    for lv, pred, ratio in ((7, 0, 2.5), (-1, 0, 2.5), (3, 3, 2.5), (3, -1, 2.5),
+                            (3, 0, 0.5), (3, 0, 65.0), (3, 0, float("nan"))):
+        assert call(stzmod.CompressOpts(lv, pred, ratio)) == stzmod.ERR_ARG, (lv, pred, ratio)
+    assert call(None, field=None) == stzmod.ERR_ARG
+    assert call(None, field=vp(8)) == stzmod.ERR_ARG  # field not 16-byte aligned
+    assert call(None, out_bytes=None) == stzmod.ERR_ARG
+
+
+def test_decode_calls_reject_bad_pointers_before_any_cuda_call(stzmod):
+    L = stzmod.lib()
+    vp = ctypes.c_void_p
+    od = _i64(0, 0, 0)
+    assert L.stz_decompress_progressive(None, 1000, 1, vp(256), 100, od, vp(256), 100,
+                                        None) == stzmod.ERR_ARG
+    assert L.stz_decompress_progressive(vp(256), 1000, 0, vp(256), 100, od, vp(256), 100,
+                                        None) == stzmod.ERR_ARG
+    assert L.stz_decompress_progressive(vp(260), 1000, 1, vp(256), 100, od, vp(256), 100,
+                                        None) == stzmod.ERR_ARG  # container not 8-byte aligned
+    comp = _golden()
+    hdr = comp[:1984].copy()
+    assert L.stz_decode_tables(None, comp.size, hdr.ctypes.data, hdr.size, vp(256), 1 << 20,
+                               None) == stzmod.ERR_ARG
+    assert L.stz_decode_tables(vp(256), comp.size, hdr.ctypes.data, hdr.size, vp(264), 1 << 20,
+                               None) == stzmod.ERR_ARG  # tables not 16-byte aligned
+    assert L.stz_decode_tables(vp(256), comp.size, hdr.ctypes.data, hdr.size, vp(256), 16,
+                               None) == stzmod.ERR_CAPACITY
+
+
+@pytest.mark.parametrize("name", ["sin3d_f32_22x19x27", "sin3d_f64_9x14x10", "sin2d_f32_37x50"])
+def test_sizes_read_from_a_host_header(stzmod, name):
+    """Decode-table and region-workspace sizes come from the host copy of a
+    container's first bytes alone."""
+    L = stzmod.lib()
+    comp = _golden(name)
+    hdr = comp[:1984].copy()
+    chunks = (ctypes.c_int64 * 64)()
+    inf = stzmod._Info()
+    assert L.stz_info(comp.ctypes.data, comp.size, 0, ctypes.byref(inf)) == 0
+    nd, lv = inf.ndim, inf.levels
+    dims = tuple(inf.dims)[:nd]
+    full_lo, full_hi = _i64(*([0] * nd)), _i64(*dims)
+    ns = L.stz_region_chunks(hdr.ctypes.data, hdr.size, comp.size, full_lo, full_hi, lv, 0,
+                             chunks, 64)
+    # 1 + 7 (L - 1) streams; a 2D field leaves 4 of each level's 7 empty
+    assert ns == 1 + 7 * (lv - 1)
+    if nd == 2:
+        assert sum(1 for k in range(1, ns) if chunks[k] > 0) == 3 * (lv - 1)
+    # one table of 4096 four-byte entries per stream
+    assert L.stz_decode_tables_size(hdr.ctypes.data, hdr.size, comp.size) == 16384 * ns
+    bad = hdr.copy()
+    bad[:4] = 0
+    assert L.stz_decode_tables_size(bad.ctypes.data, bad.size, comp.size) == 0
+    ws_full = L.stz_region_workspace_size(hdr.ctypes.data, hdr.size, comp.size, full_lo, full_hi,
+                                          lv, 0)
+    assert ws_full > 0
+    small_hi = _i64(*[min(2, n) for n in dims])
+    ws_small = L.stz_region_workspace_size(hdr.ctypes.data, hdr.size, comp.size, full_lo,
+                                           small_hi, lv, 0)
+    assert 0 < ws_small <= ws_full
+    # a supplied level-1 grid never needs more room
+    assert L.stz_region_workspace_size(hdr.ctypes.data, hdr.size, comp.size, full_lo, small_hi,
+                                       lv, 1) <= ws_small
+    for level in (0, lv + 1):
+        assert L.stz_region_workspace_size(hdr.ctypes.data, hdr.size, comp.size, full_lo,
+                                           full_hi, level, 0) == 0
+    empty_hi = _i64(*([0] * nd))
+    assert L.stz_region_workspace_size(hdr.ctypes.data, hdr.size, comp.size, full_lo, empty_hi,
+                                       lv, 0) == 0
+    past_hi = _i64(*[n + 1 for n in dims])
+    assert L.stz_region_workspace_size(hdr.ctypes.data, hdr.size, comp.size, full_lo, past_hi,
+                                       lv, 0) == 0
+
+
+def test_roi_geometry_and_argument_errors(stzmod):
+    L = stzmod.lib()
+    assert L.stz_roi_units(_i64(64, 64, 64), 3, _i64(4, 4, 4)) == 16 ** 3
+    assert L.stz_roi_units(_i64(37, 50), 2, _i64(4, 8)) == 10 * 7
+    assert L.stz_roi_units(_i64(30, 31, 33), 3, _i64(4, 8, 16)) == 8 * 4 * 3
+    assert L.stz_roi_units(_i64(64, 64, 64), 3, _i64(0, 4, 4)) == -1
+    assert L.stz_roi_units(_i64(64, 64, 64), 3, None) == -1
+    assert L.stz_roi_workspace_size(_i64(64, 64, 64), 3, _i64(0, 4, 4)) == 0
+    assert L.stz_roi_workspace_size(_i64(64, 64, 64), 3, _i64(4, 4, 4)) >= 3 * 8 * 16 ** 3
+    vp = ctypes.c_void_p
+    d, b = _i64(64, 64, 64), _i64(4, 4, 4)
+    ns = ctypes.c_int64(0)
+    ws = L.stz_roi_workspace_size(d, 3, b)
+
+    def sel(metric=0, mode=1, value=0.01, field=vp(256), cap=4096, wsb=ws, dtype=0):
+        return L.stz_roi_select(field, d, 3, dtype, b, metric, mode, value, vp(256), cap, None,
+                                ctypes.byref(ns), vp(256), wsb, None)
+
+    assert sel(metric=2) == stzmod.ERR_ARG
+    assert sel(mode=2) == stzmod.ERR_ARG
+    assert sel(value=0.0) == stzmod.ERR_ARG
+    assert sel(value=1.5) == stzmod.ERR_ARG
+    assert sel(dtype=2) == stzmod.ERR_ARG
+    assert sel(field=None) == stzmod.ERR_ARG
+    assert sel(field=vp(258)) == stzmod.ERR_ARG  # not aligned to the element
+    assert sel(cap=4095) == stzmod.ERR_CAPACITY
+    assert sel(wsb=ws - 1) == stzmod.ERR_CAPACITY
+
+
+def test_batched_requests_are_planned_on_the_host(stzmod):
+    """stz_decode_requests checks every request against its field's host
+    header before queuing anything; the workspace size is a host plan."""
+    L = stzmod.lib()
+    comp = _golden()
+    hdr = comp[:1984].copy()
+    vp = ctypes.c_void_p
+    f = (stzmod.ServedField * 1)()
+    f[0].comp_dev, f[0].comp_bytes = 256, comp.size
+    f[0].hdr_host, f[0].hdr_bytes = hdr.ctypes.data, hdr.size
+    f[0].level1_dev, f[0].tables_dev = 256, 256
+    r = (stzmod.RegionRequest * 2)()
+    for i in range(2):
+        r[i].field, r[i].level = 0, 3
+        r[i].lo[:] = [0, 0, 0]
+        r[i].hi[:] = [4 + i, 5, 6]
+        r[i].out_dev, r[i].out_cap = 256, 1 << 20
+    ws = L.stz_decode_requests_workspace(2, r, f, 1)
+    assert ws > 0
+    assert L.stz_decode_requests_workspace(1, r, f, 1) <= ws
+    assert L.stz_decode_requests_workspace(0, r, f, 1) == 0
+    assert L.stz_decode_requests_workspace(2, r, None, 0) == 0
+    st = vp(256)
+    assert L.stz_decode_requests(2, r, f, 1, None, ws, st, None) == stzmod.ERR_ARG
+    assert L.stz_decode_requests(2, r, f, 1, vp(256), ws, None, None) == stzmod.ERR_ARG
+    assert L.stz_decode_requests(2, r, f, 1, vp(256), ws - 1, st, None) == stzmod.ERR_CAPACITY
+    r[1].field = 1  # no such field
+    assert L.stz_decode_requests(2, r, f, 1, vp(256), ws, st, None) == stzmod.ERR_ARG
+    r[1].field, r[1].level = 0, 4  # past the container's levels
+    assert L.stz_decode_requests(2, r, f, 1, vp(256), ws, st, None) == stzmod.ERR_ARG
+    r[1].level = 3
+    f[0].tables_dev = None
+    assert L.stz_decode_requests(2, r, f, 1, vp(256), ws, st, None) == stzmod.ERR_ARG
+
+
+def test_launch_counter_and_timer_need_no_gpu(stzmod):
+    L = stzmod.lib()
+    c0 = L.stz_launch_count()
+    nb = ctypes.c_size_t(0)
+    # a rejected call launches nothing
+    assert L.stz_compress(None, _i64(8, 8, 8), 3, 0, 1, 1e-3, ctypes.c_void_p(256), 1 << 20,
+                          ctypes.byref(nb), ctypes.c_void_p(256), 1 << 20,
+                          None) == stzmod.ERR_ARG
+    assert L.stz_launch_count() == c0
+    L.stz_profile_enable(1)
+    L.stz_profile_reset()
+    buf = (stzmod._KernelTime * 4)()
+    assert L.stz_profile_read(buf, 4) == 0
+    L.stz_profile_enable(0)
